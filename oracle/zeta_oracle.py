@@ -1,0 +1,435 @@
+"""Plain FP64 CPU oracle for the in-situ multipole 3PCF of Ju et al. (2025),
+"An Optimal In-Situ Multipole Algorithm for the Isotropic Three-Point
+Correlation Function" (arXiv:2507.15209).
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports, calls, links
+or executes this module: only the test-suite, the smoke check and the
+benchmark's CPU-baseline leg do.  It shares no code with the CUDA library and
+takes every input (particles, grids, bin edges) as plain arrays.
+
+Each function restates one step of the method in the order of the paper's
+Sec. 2 and Fig. 1, with numpy / scipy library primitives (FFT, special
+functions, matmul, bincount) as the only building blocks.  Everything is
+float64.
+
+Readings taken where the paper is silent, ambiguous or garbled (each is also
+listed in the design notes):
+  R1  Eq. (double-e-expansion) drops a conjugate; we use real orthonormal
+      spherical harmonics R_lm with i^l in both vertex windows, so the pair
+      product is sum_m a_lm,b1 a_lm,b2 of real fields.
+  R2  DFT conventions: forward unnormalised e^{-2 pi i n.l/N}; inverse carries
+      1/N_g; k_n = 2 pi n / L_box with n_d in (-N/2, N/2).
+  R3  The basis window Phi-hat of Eq. (SFC-3PCF-vertex) is 1 (the translation
+      kernel is the lattice-sampled shell harmonic only).
+  R4  Radial binning: the vertex window is the r^2-weighted shell average
+      jbar_l(k; b) = int r^2 j_l(kr) dr / int r^2 dr over [r_lo, r_hi).
+  R5  Every Nyquist plane (any n_d = N/2) of the kernel is zero; at k = 0,
+      R_00 = 1/sqrt(4 pi) and R_{l>0} = 0.
+  R6  The SFCs are B-spline expansion coefficients assigned from the points,
+      eps_l = sum_p w_p beta(x_p/H - l); contrast delta = eps/eps_bar - 1 with
+      eps_bar = W/N_g (Sec. 3 uses the contrast in a periodic box).
+  R7  Particle form, Eq. (DDD-sum-privertex) with the primary vertex carried
+      by delta = n/n_bar - 1: zeta = (1/W) sum_p w_p sum_m f_b1 f_b2 - U, where
+      U = (1/V) int sum_m f_b1 f_b2 dx is the "-1" (uniform) term.
+  R8  No self-triplet or shot-noise subtraction (the paper's formulas have none).
+
+Parity pins of each function live in tests/test_oracle_pins.py; none of the
+functions below is unpinned.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import special
+
+__all__ = [
+    "bspline", "stencil_base", "assign", "contrast", "fft_integers", "nyquist_mask",
+    "jbar", "real_ylm", "window_kernel", "multipole_fields", "sum_node",
+    "gamma_1d", "mass_1d", "sum_gamma", "interpolate", "sum_particles",
+    "mass_term", "zeta_multipoles", "zeta_from_delta", "brute_force_raw",
+]
+
+FOUR_PI = 4.0 * math.pi
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1: multiresolution basis.  The scaling function is the centred
+# cardinal B-spline of order D (support D cells): D=2 linear hat, D=4 cubic.
+# ---------------------------------------------------------------------------
+def bspline(u, dsup: int):
+    """beta_D(u), the centred B-spline of order dsup (dsup in {2, 4})."""
+    a = np.abs(np.asarray(u, dtype=np.float64))
+    if dsup == 2:
+        return np.where(a < 1.0, 1.0 - a, 0.0)
+    if dsup == 4:
+        inner = 2.0 / 3.0 - a * a + 0.5 * a ** 3
+        outer = (2.0 - a) ** 3 / 6.0
+        return np.where(a < 1.0, inner, np.where(a < 2.0, outer, 0.0))
+    raise ValueError("dsup must be 2 or 4")
+
+
+def stencil_base(u, dsup: int):
+    """First node of the dsup-point stencil around grid coordinate u."""
+    return np.floor(u).astype(np.int64) - (dsup // 2 - 1)
+
+
+def assign(pos, w, n: int, box: float, dsup: int):
+    """SFCs of the point process, Sec. 2.1 and Fig. 1 step (2) (reading R6).
+
+    eps_l = sum_p w_p prod_d beta(u_pd - l_d), periodic in l; u = x / H.
+    Returns (eps[z, y, x], W = sum_p w_p).
+    """
+    pos = np.asarray(pos, np.float64)
+    w = np.asarray(w, np.float64)
+    u = pos / (box / n)
+    base = stencil_base(u, dsup)
+    eps = np.zeros(n ** 3)
+    for oz in range(dsup):
+        lz = base[:, 2] + oz
+        bz = bspline(u[:, 2] - lz, dsup)
+        for oy in range(dsup):
+            ly = base[:, 1] + oy
+            by = bspline(u[:, 1] - ly, dsup)
+            for ox in range(dsup):
+                lx = base[:, 0] + ox
+                bx = bspline(u[:, 0] - lx, dsup)
+                idx = ((lz % n) * n + (ly % n)) * n + (lx % n)
+                eps += np.bincount(idx, weights=w * bx * by * bz, minlength=n ** 3)
+    return eps.reshape(n, n, n), float(w.sum())
+
+
+def contrast(eps, wsum: float):
+    """delta = eps / eps_bar - 1 with eps_bar = W / N_g (Sec. 3, periodic box)."""
+    return eps / (wsum / eps.size) - 1.0
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1-2.2: DFT wavevectors and the multipole window of
+# Eq. (3PCF-multipole-window) with radial binning (Sec. 2.2, binning windows).
+# ---------------------------------------------------------------------------
+def fft_integers(n: int):
+    """Integer wavenumber of each DFT index: i for i < n/2, i - n otherwise."""
+    i = np.arange(n)
+    return np.where(i < n // 2, i, i - n)
+
+
+def nyquist_mask(n: int):
+    """True on every plane where some axis index equals n/2 (reading R5)."""
+    i = np.arange(n) == n // 2
+    return i[:, None, None] | i[None, :, None] | i[None, None, :]
+
+
+def jbar(ell: int, k, r_lo: float, r_hi: float, nq: int = 32):
+    """r^2-weighted shell average of j_l(k r) over [r_lo, r_hi) (reading R4).
+
+    Gauss-Legendre quadrature on sub-intervals short enough that the
+    integrand is resolved at the largest k supplied.
+    """
+    k = np.asarray(k, np.float64)
+    kmax = float(k.max()) if k.size else 0.0
+    nsub = max(1, int(math.ceil(kmax * (r_hi - r_lo) / 2.0)))
+    xg, wg = np.polynomial.legendre.leggauss(nq)
+    edges = np.linspace(r_lo, r_hi, nsub + 1)
+    num = np.zeros_like(k)
+    for a, b in zip(edges[:-1], edges[1:]):
+        half = 0.5 * (b - a)
+        r = 0.5 * (a + b) + half * xg
+        jl = special.spherical_jn(ell, k[..., None] * r)
+        num += half * np.sum(wg * r * r * jl, axis=-1)
+    den = (r_hi ** 3 - r_lo ** 3) / 3.0
+    return num / den
+
+
+def _sph_harm_complex(ell: int, m: int, theta, phi):
+    if hasattr(special, "sph_harm_y"):
+        return special.sph_harm_y(ell, m, theta, phi)
+    return special.sph_harm(m, ell, phi, theta)  # older scipy: (order, degree, azimuth, polar)
+
+
+def real_ylm(ell: int, m: int, vx, vy, vz):
+    """Real orthonormal spherical harmonic R_lm of the direction of (vx, vy, vz).
+
+    R_l0 = Y_l^0;  R_lm = sqrt2 (-1)^m Re Y_l^m (m > 0);  R_lm = sqrt2 (-1)^m Im Y_l^|m| (m < 0),
+    i.e. sqrt2 N_lm P_l^|m|(cos theta) {cos, sin}(|m| phi) without the Condon-Shortley
+    phase.  The zero vector gets R_00 = 1/sqrt(4 pi) and 0 otherwise (reading R5).
+    """
+    vx = np.asarray(vx, np.float64)
+    vy = np.asarray(vy, np.float64)
+    vz = np.asarray(vz, np.float64)
+    r = np.sqrt(vx * vx + vy * vy + vz * vz)
+    safe = np.where(r > 0, r, 1.0)
+    theta = np.arccos(np.clip(vz / safe, -1.0, 1.0))
+    phi = np.arctan2(vy, vx)
+    y = _sph_harm_complex(ell, abs(m), theta, phi)
+    if m > 0:
+        out = math.sqrt(2.0) * (-1.0) ** m * y.real
+    elif m < 0:
+        out = math.sqrt(2.0) * (-1.0) ** (-m) * y.imag
+    else:
+        out = y.real
+    zero_val = 1.0 / math.sqrt(FOUR_PI) if ell == 0 else 0.0
+    return np.where(r > 0, out, zero_val)
+
+
+def _grid_integers(n: int):
+    iv = fft_integers(n)
+    nz, ny, nx = np.meshgrid(iv, iv, iv, indexing="ij")
+    return nx, ny, nz
+
+
+def window_kernel(ell: int, m: int, n: int, box: float, edges):
+    """K_lm,b(n) = sqrt(4 pi) i^l jbar_l(|k_n|; b) R_lm(k_n-hat), Nyquist planes zero.
+
+    Eq. (3PCF-multipole-window) with the bin average of reading R4.
+    Returns complex array (nbins, n, n, n) over the full DFT grid [z, y, x].
+    """
+    nx, ny, nz = _grid_integers(n)
+    n2 = nx * nx + ny * ny + nz * nz
+    uniq, inv = np.unique(n2, return_inverse=True)
+    kmag = 2.0 * math.pi / box * np.sqrt(uniq.astype(np.float64))
+    ang = real_ylm(ell, m, nx, ny, nz)
+    ny_mask = nyquist_mask(n)
+    nb = len(edges) - 1
+    out = np.empty((nb, n, n, n), np.complex128)
+    for b in range(nb):
+        jb = jbar(ell, kmag, edges[b], edges[b + 1])[inv].reshape(n2.shape)
+        kern = math.sqrt(FOUR_PI) * (1j ** ell) * jb * ang
+        kern[ny_mask] = 0.0
+        out[b] = kern
+    return out
+
+
+def multipole_fields(delta_hat, ell: int, m: int, n: int, box: float, edges):
+    """a_lm,b(l) = IDFT[delta_hat * K_lm,b], Eq. (SFC-3PCF-vertex), Fig. 1 step (5).
+
+    The fields are real (readings R1, R5); returns float64 (nbins, n, n, n).
+    """
+    kern = window_kernel(ell, m, n, box, edges)
+    out = np.empty(kern.shape, np.float64)
+    for b in range(kern.shape[0]):
+        a = np.fft.ifftn(delta_hat * kern[b])
+        scale = max(1e-300, float(np.abs(a.real).max()))
+        if float(np.abs(a.imag).max()) > 1e-9 * scale:
+            raise AssertionError("multipole field is not real")
+        out[b] = a.real
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2: grid-based summation.
+# ---------------------------------------------------------------------------
+def sum_node(delta, a):
+    """Node form: (1/N_g) sum_l delta_l a_b1(l) a_b2(l), Eq. (3PCF-multipole-sum) at one m."""
+    nb = a.shape[0]
+    af = a.reshape(nb, -1)
+    return (af * delta.reshape(1, -1)) @ af.T / delta.size
+
+
+def _unit_interval_quadrature(func, lo: int, hi: int, nq: int = 8):
+    """int_lo^hi func(u) du for a function that is a polynomial on every unit interval."""
+    xg, wg = np.polynomial.legendre.leggauss(nq)
+    total = 0.0
+    for k in range(lo, hi):
+        u = k + 0.5 + 0.5 * xg
+        total += 0.5 * float(np.sum(wg * func(u)))
+    return total
+
+
+def gamma_1d(dsup: int):
+    """1-D connection coefficients gamma(a, b) = int beta(u) beta(u-a) beta(u-b) du.
+
+    Eq. (con-coeff) factorises over axes: Gamma_{l1,l2} = prod_d gamma(l1_d, l2_d).
+    Returns {(a, b): value} for |a|, |b| < dsup with a nonzero value.
+    """
+    half = dsup // 2
+    out = {}
+    for a in range(-(dsup - 1), dsup):
+        for b in range(-(dsup - 1), dsup):
+            v = _unit_interval_quadrature(
+                lambda u: bspline(u, dsup) * bspline(u - a, dsup) * bspline(u - b, dsup), -half, half)
+            if v != 0.0:
+                out[(a, b)] = v
+    return out
+
+
+def mass_1d(dsup: int):
+    """M(a) = int beta(u) beta(u - a) du for |a| < dsup."""
+    half = dsup // 2
+    return {a: _unit_interval_quadrature(lambda u: bspline(u, dsup) * bspline(u - a, dsup), -half, half)
+            for a in range(-(dsup - 1), dsup)}
+
+
+def _shift(a, off):
+    """Periodic shift: out[..., l] = a[..., l + off], off given as (z, y, x)."""
+    return np.roll(a, shift=(-off[0], -off[1], -off[2]), axis=(-3, -2, -1))
+
+
+def sum_gamma(delta, a, dsup: int):
+    """Connection-coefficient form, Eqs. (SFC-3PCF) and (3PCF-multipole-sum) at one m:
+
+    (1/N_g) sum_l delta_l sum_{l1, l2} Gamma_{l1,l2} a_b1(l + l1) a_b2(l + l2).
+    """
+    g1 = gamma_1d(dsup)
+    nb = a.shape[0]
+    ng = delta.size
+    cache = {}
+
+    def shifted(off):
+        if off not in cache:
+            cache[off] = _shift(a, off).reshape(nb, -1)
+        return cache[off]
+
+    dflat = delta.reshape(1, -1)
+    out = np.zeros((nb, nb))
+    items = list(g1.items())
+    for (pz, qz), vz in items:
+        for (py, qy), vy in items:
+            for (px, qx), vx in items:
+                a1 = shifted((pz, py, px)) * dflat
+                a2 = shifted((qz, qy, qx))
+                out += (vz * vy * vx) * (a1 @ a2.T)
+    return out / ng
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2: particle-based summation, Eq. (DDD-sum-privertex) and the
+# per-(L, M) densities n^LM(x, r) = sum_l eps~^LM_l phi_l(x).
+# ---------------------------------------------------------------------------
+def interpolate(a, pos, n: int, box: float, dsup: int):
+    """f_b(x_p) = sum_l beta(u_p - l) a_b(l) (B-spline expansion at each point)."""
+    pos = np.asarray(pos, np.float64)
+    u = pos / (box / n)
+    base = stencil_base(u, dsup)
+    nb = a.shape[0]
+    af = a.reshape(nb, -1)
+    f = np.zeros((nb, pos.shape[0]))
+    for oz in range(dsup):
+        lz = base[:, 2] + oz
+        bz = bspline(u[:, 2] - lz, dsup)
+        for oy in range(dsup):
+            ly = base[:, 1] + oy
+            by = bspline(u[:, 1] - ly, dsup)
+            for ox in range(dsup):
+                lx = base[:, 0] + ox
+                bx = bspline(u[:, 0] - lx, dsup)
+                idx = ((lz % n) * n + (ly % n)) * n + (lx % n)
+                f += (bx * by * bz)[None, :] * af[:, idx]
+    return f
+
+
+def sum_particles(a, pos, w, n: int, box: float, dsup: int):
+    """(1/W) sum_p w_p f_b1(x_p) f_b2(x_p) at one (l, m) (reading R7, first term)."""
+    w = np.asarray(w, np.float64)
+    f = interpolate(a, pos, n, box, dsup)
+    return (f * w[None, :]) @ f.T / float(w.sum())
+
+
+def mass_term(a, dsup: int):
+    """U = (1/V) int f_b1 f_b2 dx = (1/N_g) sum_{l,l'} a_b1(l) M3(l - l') a_b2(l') (reading R7)."""
+    m1 = mass_1d(dsup)
+    nb = a.shape[0]
+    ng = a[0].size
+    af = a.reshape(nb, -1)
+    out = np.zeros((nb, nb))
+    for dz, mz in m1.items():
+        for dy, my in m1.items():
+            for dx, mx in m1.items():
+                out += (mz * my * mx) * (af @ _shift(a, (dz, dy, dx)).reshape(nb, -1).T)
+    return out / ng
+
+
+# ---------------------------------------------------------------------------
+# Fig. 1 steps (2)-(7): the whole multipole measurement.
+# ---------------------------------------------------------------------------
+def _symmetrise(x):
+    return 0.5 * (x + np.swapaxes(x, -1, -2))
+
+
+def zeta_from_delta(delta, n: int, box: float, edges, lmax: int, dsup: int,
+                    forms=("node",), particles=None, raw_particle=False):
+    """zeta_l(b1, b2) for l <= lmax from a contrast grid (and particles for that form).
+
+    forms: any of "node", "gamma", "particle".  Returns (zeta, cond) dicts of
+    float64 arrays (lmax+1, nb, nb); cond holds the sum of absolute values of
+    the summed terms (the condition sum used to judge FP32 attainable error).
+    raw_particle drops the U term (the raw-DDD reading used against brute force).
+    """
+    nb = len(edges) - 1
+    delta = np.asarray(delta, np.float64)
+    delta_hat = np.fft.fftn(delta)
+    zeta = {f: np.zeros((lmax + 1, nb, nb)) for f in forms}
+    cond = {f: np.zeros((lmax + 1, nb, nb)) for f in forms}
+    if "particle" in forms:
+        pos = np.asarray(particles[:, :3], np.float64)
+        w = np.asarray(particles[:, 3], np.float64)
+    for ell in range(lmax + 1):
+        for m in range(-ell, ell + 1):
+            a = multipole_fields(delta_hat, ell, m, n, box, edges)
+            if "node" in forms:
+                zeta["node"][ell] += sum_node(delta, a)
+                cond["node"][ell] += sum_node(np.abs(delta), np.abs(a))
+            if "gamma" in forms:
+                zeta["gamma"][ell] += sum_gamma(delta, a, dsup)
+            if "particle" in forms:
+                f = interpolate(a, pos, n, box, dsup)
+                wsum = float(w.sum())
+                part = (f * w[None, :]) @ f.T / wsum
+                cond["particle"][ell] += (np.abs(f) * np.abs(w)[None, :]) @ np.abs(f).T / wsum
+                if not raw_particle:
+                    u = mass_term(a, dsup)
+                    part = part - u
+                    cond["particle"][ell] += np.abs(u)
+                zeta["particle"][ell] += part
+    return ({f: _symmetrise(v) for f, v in zeta.items()}, cond)
+
+
+def zeta_multipoles(particles, n: int, box: float, edges, lmax: int, dsup: int,
+                    forms=("node",), raw=False):
+    """Full pipeline from a catalogue: assign -> contrast -> DFT -> fields -> sums.
+
+    raw=True keeps the primary and the fields on n/n_bar (no -1) and drops U,
+    the reading compared with brute-force triplet enumeration.
+    """
+    particles = np.asarray(particles)
+    eps, wsum = assign(particles[:, :3], particles[:, 3], n, box, dsup)
+    delta = eps / (wsum / eps.size) if raw else contrast(eps, wsum)
+    return zeta_from_delta(delta, n, box, edges, lmax, dsup, forms=forms,
+                           particles=particles, raw_particle=raw)
+
+
+# ---------------------------------------------------------------------------
+# Continuum target of the raw-DDD reading: explicit pair/harmonic enumeration.
+# ---------------------------------------------------------------------------
+def brute_force_raw(particles, box: float, edges, lmax: int):
+    """D_l(b1,b2) = (4 pi / W) sum_i w_i sum_m Abar_lm(i;b1) Abar_lm(i;b2) with
+    Abar_lm(i;b) = V / (W V_b) sum_{j != i, r_ij in b} w_j R_lm(r_ij-hat), minimum image.
+
+    Loops over primaries in Python; meant for a few thousand points at most.
+    """
+    p = np.asarray(particles, np.float64)
+    pos, w = p[:, :3], p[:, 3]
+    wsum = float(w.sum())
+    vol = box ** 3
+    edges = np.asarray(edges, np.float64)
+    nb = len(edges) - 1
+    vb = 4.0 * math.pi / 3.0 * (edges[1:] ** 3 - edges[:-1] ** 3)
+    out = np.zeros((lmax + 1, nb, nb))
+    for i in range(len(p)):
+        d = pos - pos[i]
+        d -= box * np.round(d / box)
+        r = np.sqrt(np.sum(d * d, axis=1))
+        sel = np.arange(len(p)) != i
+        bidx = np.searchsorted(edges, r, side="right") - 1
+        ok = sel & (bidx >= 0) & (bidx < nb) & (r < edges[-1])
+        if not np.any(ok):
+            continue
+        dd, ww, bb = d[ok], w[ok], bidx[ok]
+        for ell in range(lmax + 1):
+            for m in range(-ell, ell + 1):
+                rl = real_ylm(ell, m, dd[:, 0], dd[:, 1], dd[:, 2])
+                abar = np.zeros(nb)
+                np.add.at(abar, bb, ww * rl)
+                abar *= vol / (wsum * vb)
+                out[ell] += w[i] * np.outer(abar, abar)
+    return out * FOUR_PI / wsum
