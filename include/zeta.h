@@ -1,0 +1,191 @@
+/*
+ * zeta.h -- C ABI of the GB300 (sm_103a) implementation of the in-situ multipole
+ * algorithm for the isotropic three-point correlation function of
+ * Ju et al. (2025), arXiv:2507.15209.
+ *
+ * The path, in the order of the paper's Fig. 1:
+ *   zeta_assign          step (2)  B-spline (MRA) assignment of the catalogue and the
+ *                                  contrast delta = eps/eps_bar - 1            (Sec. 2.1, Sec. 3)
+ *   zeta_fft_r2c         step (2)  3-D real-to-complex DFT of delta            (Eq. trans-field-FT)
+ *   zeta_reconstruct_alm steps (3)-(5)  multiply by sqrt(4 pi) i^l jbar_l(k;b) R_lm(k-hat) and
+ *                                  C2R to the real fields a_lm(x; b)           (Eqs. 3PCF-multipole-window,
+ *                                                                              SFC-3PCF-vertex)
+ *   zeta_sum_grid        step (6)  grid summation: node form or the connection-coefficient
+ *                                  (Gamma) form                               (Eqs. con-coeff, SFC-3PCF,
+ *                                                                              3PCF-multipole-sum)
+ *   zeta_sum_particles   step (6)  particle summation                         (Eq. DDD-sum-privertex)
+ *   zeta_mass_term       step (6)  the uniform ("-1") term of the particle form, per l
+ *   zeta_zeta_ell        steps (2)-(7)  the whole measurement of zeta_l(r1, r2), l <= lmax
+ *
+ * Conventions shared by every call
+ *   - Grids are float32, indexed [z][y][x] with x fastest, side n, N_g = n^3, cell H = box/n.
+ *   - A particle is four float32 (x, y, z, w) in box units; coordinates in [0, box).
+ *   - delta_hat, the half spectrum, is complex64 (re, im interleaved) laid out [nz][ny][nx]
+ *     with nx in [0, n/2): the x-Nyquist column is not stored, because every kernel of the
+ *     method is zero on all Nyquist planes.  Its size is n^3/2 complex = n^3 floats.
+ *     Forward DFT unnormalised, e^{-2 pi i n.l / n}; wavevector k = 2 pi n / box.
+ *   - A field a_lm(x; b) is a float32 grid; a stack of fields is [field][z][y][x].
+ *   - Real spherical harmonics without the Condon-Shortley phase:
+ *     R_l0 = Y_l^0, R_lm = sqrt2 N_lm P_l^m(cos t) cos(m p) (m > 0), sin(|m| p) (m < 0).
+ *   - Bins are [edges[b], edges[b+1]); the radial window of bin b is the r^2-weighted shell
+ *     average jbar_l(k; b) of j_l(k r).
+ *   - Gram outputs are float64 nbins x nbins row-major, ACCUMULATED into (+=), symmetric.
+ *
+ * Memory ownership
+ *   - Every pointer argument named as device memory is owned by the caller; the library never
+ *     frees it.  zeta_create allocates only small device tables (radial window table,
+ *     twiddles, constants) that zeta_destroy frees.
+ *   - Scratch memory comes from one caller-owned workspace (zeta_set_workspace); its size is
+ *     given by zeta_workspace_bytes.  Calls on one context must not overlap in time (one
+ *     stream per context, or external ordering), because they share the workspace.
+ *
+ * Errors
+ *   - Every call returns ZETA_OK (0) or a negative code.  Arguments are validated on the host
+ *     before anything is launched.  Launches are asynchronous on the given stream: a CUDA
+ *     error is reported by the call that observes it; a data error detected on the device
+ *     (non-finite particle) is latched in a device status word and returned by
+ *     zeta_get_status, which synchronises the stream.
+ *   - No call traps, asserts or spins without bound on the device.
+ */
+#ifndef ZETA_H
+#define ZETA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (NULL means the legacy default stream). */
+typedef struct CUstream_st* zeta_stream;
+typedef struct zeta_ctx zeta_ctx;
+
+enum {
+  ZETA_OK = 0,
+  ZETA_EINVAL = -1,     /* invalid argument (host-side validation)                  */
+  ZETA_ECUDA = -2,      /* a CUDA runtime call or kernel launch failed              */
+  ZETA_ENOMEM = -3,     /* device allocation of the context's tables failed         */
+  ZETA_ETIMEOUT = -4,   /* a bounded device wait gave up                            */
+  ZETA_ENOTSUP = -5,    /* configuration not supported by this build                */
+  ZETA_EWORKSPACE = -6, /* workspace missing or smaller than zeta_workspace_bytes   */
+  ZETA_EDATA = -7       /* device found invalid input data (non-finite particle)    */
+};
+
+/* Summation forms (bit mask). */
+enum { ZETA_SUM_NODE = 1, ZETA_SUM_GAMMA = 2, ZETA_SUM_PARTICLE = 4 };
+
+/* Arithmetic of the node-form Gram contraction (Sec. 2.2 grid sum). */
+enum {
+  ZETA_GRAM_FP32 = 0,   /* plain float32 FMA, the reference path                    */
+  ZETA_GRAM_TF32 = 1,   /* tensor cores, tf32 inputs, fp32 accumulation             */
+  ZETA_GRAM_BF16 = 2,   /* tensor cores, bf16 inputs, fp32 accumulation             */
+  ZETA_GRAM_BF16X3 = 3  /* tensor cores, split bf16 (hi*hi + hi*lo + lo*hi)          */
+};
+
+typedef struct {
+  int n;                /* grid side: power of two, 16 <= n <= 512                   */
+  double box;           /* periodic box side, same unit as positions and edges       */
+  int dsup;             /* B-spline support D: 2 (linear hat) or 4 (cubic)           */
+  int lmax;             /* highest multipole l, 0 <= lmax <= 14                      */
+  int nbins;            /* number of radial bins, 1 <= nbins <= 32                   */
+  const double* edges;  /* host, nbins+1 strictly increasing, edges[0] > 0,          */
+                        /* edges[nbins] < box/2; copied by zeta_create               */
+  int gram;             /* ZETA_GRAM_*                                               */
+} zeta_params;
+
+/* Library version (major*10000 + minor*100 + patch). Host only. */
+int zeta_version(void);
+
+/* Human-readable text of an error code. Host only; never NULL. */
+const char* zeta_strerror(int code);
+
+/* Build the FP64 host tables (radial window jbar_l by integer |n|^2, spherical-harmonic
+ * recurrence constants, twiddles, B-spline mass and connection values), upload them to the
+ * current device, and return a context.  Needs a CUDA device.  *out is NULL on error. */
+int zeta_create(const zeta_params* p, zeta_ctx** out);
+
+/* Free the context and its device tables.  NULL is accepted. */
+int zeta_destroy(zeta_ctx* ctx);
+
+/* Bytes of workspace that zeta_zeta_ell needs for up to np_max particles and the given
+ * summation forms; it also covers every single-step call.  0 on invalid arguments. */
+size_t zeta_workspace_bytes(const zeta_ctx* ctx, int64_t np_max, int forms);
+
+/* Hand the context a caller-owned device workspace (256-byte aligned, >= the size above).
+ * The library keeps the pointer, never frees it. */
+int zeta_set_workspace(zeta_ctx* ctx, void* dptr, size_t bytes);
+
+/* Number of 8x8x8-cell tiles that particle sorting uses: (n/8)^3. */
+int64_t zeta_tile_count(const zeta_ctx* ctx);
+
+/* Step (2): delta_l = eps_l / eps_bar - 1 with eps_l = sum_p w_p beta(u_p - l) (periodic)
+ * and eps_bar = W / N_g.  particles: device float4[np]; delta: device float[n^3] (output);
+ * wsum: device double[1] (output, W = sum_p w_p).  Deterministic: contributions are summed
+ * as 64-bit fixed point.  Uses the workspace. */
+int zeta_assign(zeta_ctx* ctx, const float* particles, int64_t np, float* delta, double* wsum,
+                zeta_stream stream);
+
+/* Step (2): delta_hat = DFT(delta), unnormalised, half spectrum without the x-Nyquist column.
+ * delta: device float[n^3]; delta_hat: device complex64[n^3/2] (as float[n^3]). */
+int zeta_fft_r2c(zeta_ctx* ctx, const float* delta, float* delta_hat, zeta_stream stream);
+
+/* Steps (3)-(5): for bins b0 <= b < b1, a_lm(.; b) = IDFT[delta_hat * K_lm,b] with
+ * K_lm,b(k) = sqrt(4 pi) i^l jbar_l(|k|; b) R_lm(k-hat), zero on every Nyquist plane and
+ * IDFT normalised by 1/N_g.  alm: device float[(b1-b0) * n^3] (output).  No workspace. */
+int zeta_reconstruct_alm(zeta_ctx* ctx, const float* delta_hat, int l, int m, int b0, int b1,
+                         float* alm, zeta_stream stream);
+
+/* Step (6), grid form, one (l, m): gram[b1][b2] += S for all bins, where
+ *   form = ZETA_SUM_NODE:  S = (1/N_g) sum_l delta_l a_b1(l) a_b2(l)
+ *   form = ZETA_SUM_GAMMA: S = (1/N_g) sum_l delta_l sum_{l1,l2} Gamma_{l1,l2} a_b1(l+l1) a_b2(l+l2)
+ *                          (evaluated as the exact cell quadrature of (1/V) int n_rec f1 f2).
+ * delta: device float[n^3]; alm: device float[nbins * n^3]; gram: device double[nbins^2]. */
+int zeta_sum_grid(zeta_ctx* ctx, const float* delta, const float* alm, int form, double* gram,
+                  zeta_stream stream);
+
+/* Sort particles into 8x8x8-cell tiles (stable within a tile: original order).
+ * particles: device float4[np]; sorted: device float4[np] (output);
+ * tile_start: device int64[zeta_tile_count + 1] (output, exclusive prefix of tile counts). */
+int zeta_sort_particles(zeta_ctx* ctx, const float* particles, int64_t np, float* sorted,
+                        int64_t* tile_start, zeta_stream stream);
+
+/* Step (6), particle form without the uniform term, one (l, m):
+ * gram[b1][b2] += (1/W) sum_p w_p f_b1(x_p) f_b2(x_p), f_b(x) = sum_l beta(x/H - l) a_b(l).
+ * sorted/tile_start: from zeta_sort_particles; wsum: device double[1] (W); alm as above. */
+int zeta_sum_particles(zeta_ctx* ctx, const float* sorted, const int64_t* tile_start, int64_t np,
+                       const double* wsum, const float* alm, double* gram, zeta_stream stream);
+
+/* Step (6), the uniform term of the particle form summed over m for one l:
+ * gram[b1][b2] += sign * U_l, U_l = sum_m (1/V) int f_b1 f_b2 dx
+ *   = (2l+1)/N_g^2 sum_{k non-Nyquist} |delta_hat|^2 jbar_l(k;b1) jbar_l(k;b2) Mhat(k),
+ * Mhat the DFT of the B-spline mass matrix.  sign is +1 or -1. */
+int zeta_mass_term(zeta_ctx* ctx, const float* delta_hat, int l, double sign, double* gram,
+                   zeta_stream stream);
+
+/* Steps (2)-(7): zeta_l(b1, b2) for 0 <= l <= lmax and each requested form.
+ * particles: device float4[np] (may be NULL only if delta is given and forms has no PARTICLE);
+ * delta: device float[n^3] contrast to use instead of assigning the particles (or NULL);
+ * zeta: device double[nforms * (lmax+1) * nbins * nbins] (output, overwritten), forms in
+ * the order NODE, GAMMA, PARTICLE among those requested. */
+int zeta_zeta_ell(zeta_ctx* ctx, const float* particles, int64_t np, const float* delta, int forms,
+                  double* zeta, zeta_stream stream);
+
+/* Synchronise the stream and return the latched device status (ZETA_OK or ZETA_EDATA /
+ * ZETA_ETIMEOUT), clearing it. */
+int zeta_get_status(zeta_ctx* ctx, zeta_stream stream);
+
+/* ---- host-only helpers (no device needed), for inspection and tests ---- */
+
+/* jbar_l(k; [r_lo, r_hi)) in float64 for k = 2 pi sqrt(n2[i]) / box, as used in the tables. */
+int zeta_host_jbar(int l, double box, double r_lo, double r_hi, const int64_t* n2, int64_t count,
+                   double* out);
+
+/* R_lm of the integer direction (vx, vy, vz) in float64 through the same recurrence the
+ * device uses (host copy of the constants). */
+double zeta_host_ylm(int l, int m, double vx, double vy, double vz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZETA_H */

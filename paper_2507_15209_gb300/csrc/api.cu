@@ -1,0 +1,317 @@
+// C ABI of libzeta: context, workspace, argument validation and the per-(l, m) hot loop
+// of the measurement (Fig. 1 steps (2)-(7)).
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "zeta_internal.h"
+
+namespace {
+
+using namespace zk;
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t delta = 0, dhat = 0, fields = 0, partials = 0, small = 0, sorted = 0, tstart = 0, counts = 0, orig = 0;
+  size_t total = 0;
+};
+
+// Workspace regions of the full measurement for np particles (np may be 0).
+Layout layout(const zeta_ctx* c, int64_t np) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  const size_t g = static_cast<size_t>(c->ng) * sizeof(float);
+  L.delta = take(g);
+  L.dhat = take(g);
+  const int nf = c->p.nbins < 2 ? 2 : c->p.nbins;  // fields region doubles as the 64-bit assign accumulator
+  L.fields = take(g * nf);
+  L.partials = take(sizeof(double) * kMaxCtas * c->p.nbins * c->p.nbins);
+  L.small = take(sizeof(double) * (kAssignScratchDoubles + 8));
+  L.sorted = take(sizeof(float4) * static_cast<size_t>(np));
+  L.tstart = take(sizeof(int64_t) * static_cast<size_t>(c->ntiles + 1));
+  L.counts = take(sizeof(int) * static_cast<size_t>(c->ntiles));
+  L.orig = take(sizeof(int) * static_cast<size_t>(np));
+  L.total = off;
+  return L;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int check_ctx(const zeta_ctx* c) { return c ? ZETA_OK : ZETA_EINVAL; }
+
+int need_ws(const zeta_ctx* c, int64_t np) {
+  if (!c->ws) return ZETA_EWORKSPACE;
+  if (layout(c, np).total > c->ws_bytes) return ZETA_EWORKSPACE;
+  return ZETA_OK;
+}
+
+template <typename T>
+T* at(const zeta_ctx* c, size_t off) {
+  return reinterpret_cast<T*>(c->ws + off);
+}
+
+#define ZK_TRY(expr)             \
+  do {                           \
+    const int _rc = (expr);      \
+    if (_rc != ZETA_OK) return _rc; \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int zeta_version(void) { return 10000; }
+
+const char* zeta_strerror(int code) {
+  switch (code) {
+    case ZETA_OK: return "ok";
+    case ZETA_EINVAL: return "invalid argument";
+    case ZETA_ECUDA: return "CUDA runtime error";
+    case ZETA_ENOMEM: return "device allocation failed";
+    case ZETA_ETIMEOUT: return "bounded device wait timed out";
+    case ZETA_ENOTSUP: return "configuration not supported";
+    case ZETA_EWORKSPACE: return "workspace missing or too small";
+    case ZETA_EDATA: return "invalid input data (non-finite particle)";
+    default: return "unknown error";
+  }
+}
+
+int zeta_create(const zeta_params* p, zeta_ctx** out) {
+  if (!out) return ZETA_EINVAL;
+  *out = nullptr;
+  if (!p || !is_pow2(p->n) || p->n < 16 || p->n > 512) return ZETA_EINVAL;
+  if (!(p->box > 0) || !std::isfinite(p->box)) return ZETA_EINVAL;
+  if (p->dsup != 2 && p->dsup != 4) return ZETA_EINVAL;
+  if (p->lmax < 0 || p->lmax > kMaxL) return ZETA_EINVAL;
+  if (p->nbins < 1 || p->nbins > kMaxBins || !p->edges) return ZETA_EINVAL;
+  if (p->gram < ZETA_GRAM_FP32 || p->gram > ZETA_GRAM_BF16X3) return ZETA_EINVAL;
+  if (!(p->edges[0] > 0)) return ZETA_EINVAL;
+  for (int b = 0; b < p->nbins; ++b)
+    if (!(p->edges[b + 1] > p->edges[b]) || !std::isfinite(p->edges[b + 1])) return ZETA_EINVAL;
+  if (!(p->edges[p->nbins] < 0.5 * p->box)) return ZETA_EINVAL;
+
+  zeta_ctx* c = new (std::nothrow) zeta_ctx();
+  if (!c) return ZETA_ENOMEM;
+  c->p = *p;
+  c->edges.assign(p->edges, p->edges + p->nbins + 1);
+  c->p.edges = c->edges.data();
+  c->n = p->n;
+  c->nc = p->n / 2;
+  c->ng = static_cast<int64_t>(p->n) * p->n * p->n;
+  c->nn2 = table_n2_count(p->n);
+  c->ntiles = static_cast<int64_t>(p->n / kTile) * (p->n / kTile) * (p->n / kTile);
+  c->gamma_q = p->dsup == 2 ? 2 : 5;
+  auto fail = [&](int rc) {
+    zeta_destroy(c);
+    return rc;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(ZETA_ECUDA);
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    return fail(ZETA_ECUDA);
+
+  std::vector<float> jtab;
+  host_jbar_table(p->n, p->box, p->lmax, p->nbins, c->edges.data(), jtab);
+  std::vector<float2> tw;
+  host_twiddles(p->n, tw);
+  std::vector<float> mhat;
+  host_mass_hat(p->n, p->dsup, mhat);
+  std::vector<double> qt, qw, qb;
+  host_cell_quadrature(c->gamma_q, p->dsup, qt, qw, qb);
+  std::vector<float> gq;
+  for (double v : qw) gq.push_back(static_cast<float>(v));
+  for (double v : qb) gq.push_back(static_cast<float>(v));
+
+  if (cudaMalloc(&c->d_jtab, jtab.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
+  if (cudaMalloc(&c->d_tw, tw.size() * sizeof(float2)) != cudaSuccess) return fail(ZETA_ENOMEM);
+  if (cudaMalloc(&c->d_mhat, mhat.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
+  if (cudaMalloc(&c->d_gq, gq.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
+  if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) return fail(ZETA_ENOMEM);
+  if (cudaMemcpy(c->d_jtab, jtab.data(), jtab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_mhat, mhat.data(), mhat.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_gq, gq.data(), gq.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess)
+    return fail(ZETA_ECUDA);
+  if (set_ylm_constants() != ZETA_OK) return fail(ZETA_ECUDA);
+  *out = c;
+  return ZETA_OK;
+}
+
+int zeta_destroy(zeta_ctx* c) {
+  if (!c) return ZETA_OK;
+  cudaFree(c->d_jtab);
+  cudaFree(c->d_tw);
+  cudaFree(c->d_mhat);
+  cudaFree(c->d_gq);
+  cudaFree(c->d_status);
+  delete c;
+  return ZETA_OK;
+}
+
+size_t zeta_workspace_bytes(const zeta_ctx* c, int64_t np_max, int forms) {
+  if (!c || np_max < 0 || np_max > 0x7fffffffLL || forms < 0 || forms > 7) return 0;
+  return layout(c, np_max).total;
+}
+
+int zeta_set_workspace(zeta_ctx* c, void* dptr, size_t bytes) {
+  ZK_TRY(check_ctx(c));
+  if (dptr && (reinterpret_cast<uintptr_t>(dptr) % kAlign)) return ZETA_EINVAL;
+  c->ws = static_cast<char*>(dptr);
+  c->ws_bytes = dptr ? bytes : 0;
+  return ZETA_OK;
+}
+
+int64_t zeta_tile_count(const zeta_ctx* c) { return c ? c->ntiles : 0; }
+
+int zeta_assign(zeta_ctx* c, const float* particles, int64_t np, float* delta, double* wsum, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!particles || np < 1 || np > 0x7fffffffLL || !delta) return ZETA_EINVAL;
+  ZK_TRY(need_ws(c, 0));
+  const Layout L = layout(c, 0);
+  double* small = at<double>(c, L.small);
+  double* w = wsum ? wsum : small + kAssignScratchDoubles + 4;
+  return launch_assign(c, reinterpret_cast<const float4*>(particles), np, delta, w,
+                       at<unsigned long long>(c, L.fields), small, stream);
+}
+
+int zeta_fft_r2c(zeta_ctx* c, const float* delta, float* delta_hat, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!delta || !delta_hat) return ZETA_EINVAL;
+  return launch_r2c(c, delta, reinterpret_cast<float2*>(delta_hat), stream);
+}
+
+int zeta_reconstruct_alm(zeta_ctx* c, const float* delta_hat, int l, int m, int b0, int b1, float* alm,
+                         zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!delta_hat || !alm || l < 0 || l > c->p.lmax || m < -l || m > l || b0 < 0 || b1 <= b0 || b1 > c->p.nbins)
+    return ZETA_EINVAL;
+  return launch_alm(c, reinterpret_cast<const float2*>(delta_hat), l, m, b0, b1 - b0, alm, stream);
+}
+
+int zeta_sum_grid(zeta_ctx* c, const float* delta, const float* alm, int form, double* gram, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!delta || !alm || !gram || (form != ZETA_SUM_NODE && form != ZETA_SUM_GAMMA)) return ZETA_EINVAL;
+  if (form == ZETA_SUM_NODE && c->p.gram != ZETA_GRAM_FP32) return ZETA_ENOTSUP;
+  ZK_TRY(need_ws(c, 0));
+  const Layout L = layout(c, 0);
+  double* part = at<double>(c, L.partials);
+  if (form == ZETA_SUM_NODE)
+    ZK_TRY(launch_gram_node(c, delta, alm, part, stream));
+  else
+    ZK_TRY(launch_gram_gamma(c, delta, alm, part, stream));
+  return launch_reduce(c, part, gram_ctas(c), 1.0 / static_cast<double>(c->ng), nullptr, gram, stream);
+}
+
+int zeta_sort_particles(zeta_ctx* c, const float* particles, int64_t np, float* sorted, int64_t* tile_start,
+                        zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!particles || np < 1 || np > 0x7fffffffLL || !sorted || !tile_start) return ZETA_EINVAL;
+  ZK_TRY(need_ws(c, np));
+  const Layout L = layout(c, np);
+  return launch_sort(c, reinterpret_cast<const float4*>(particles), np, reinterpret_cast<float4*>(sorted),
+                     tile_start, at<int>(c, L.counts), at<int>(c, L.orig), stream);
+}
+
+int zeta_sum_particles(zeta_ctx* c, const float* sorted, const int64_t* tile_start, int64_t np, const double* wsum,
+                       const float* alm, double* gram, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!sorted || !tile_start || np < 1 || !wsum || !alm || !gram) return ZETA_EINVAL;
+  ZK_TRY(need_ws(c, 0));
+  const Layout L = layout(c, 0);
+  double* part = at<double>(c, L.partials);
+  ZK_TRY(launch_gram_particles(c, reinterpret_cast<const float4*>(sorted), tile_start, alm, part, stream));
+  return launch_reduce(c, part, gram_ctas(c), 1.0, wsum, gram, stream);
+}
+
+int zeta_mass_term(zeta_ctx* c, const float* delta_hat, int l, double sign, double* gram, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!delta_hat || !gram || l < 0 || l > c->p.lmax || !(sign == 1.0 || sign == -1.0)) return ZETA_EINVAL;
+  ZK_TRY(need_ws(c, 0));
+  const Layout L = layout(c, 0);
+  double* part = at<double>(c, L.partials);
+  ZK_TRY(launch_mass(c, reinterpret_cast<const float2*>(delta_hat), l, part, stream));
+  const double scale = sign * (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846);
+  return launch_reduce(c, part, gram_ctas(c), scale, nullptr, gram, stream);
+}
+
+int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* delta, int forms, double* zeta,
+                  zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!zeta || forms < 1 || forms > 7) return ZETA_EINVAL;
+  const bool want_p = forms & ZETA_SUM_PARTICLE;
+  if ((want_p || !delta) && (!particles || np < 1 || np > 0x7fffffffLL)) return ZETA_EINVAL;
+  if ((forms & ZETA_SUM_NODE) && c->p.gram != ZETA_GRAM_FP32) return ZETA_ENOTSUP;
+  const int64_t npl = want_p ? np : 0;
+  ZK_TRY(need_ws(c, npl));
+  const Layout L = layout(c, npl);
+  const int nb = c->p.nbins, lmax = c->p.lmax;
+  const float4* parts = reinterpret_cast<const float4*>(particles);
+  double* small = at<double>(c, L.small);
+  double* wsum = small + kAssignScratchDoubles + 4;
+  float* dl = delta ? const_cast<float*>(delta) : at<float>(c, L.delta);
+  float2* dhat = at<float2>(c, L.dhat);
+  float* fields = at<float>(c, L.fields);
+  double* part = at<double>(c, L.partials);
+  float4* sorted = at<float4>(c, L.sorted);
+  int64_t* tstart = at<int64_t>(c, L.tstart);
+
+  if (!delta)
+    ZK_TRY(launch_assign(c, parts, np, dl, wsum, reinterpret_cast<unsigned long long*>(fields), small, stream));
+  else if (want_p)
+    ZK_TRY(launch_wsum(c, parts, np, wsum, small, stream));
+  ZK_TRY(launch_r2c(c, dl, dhat, stream));
+  if (want_p)
+    ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream));
+
+  int nforms = 0, idx_node = -1, idx_gamma = -1, idx_part = -1;
+  if (forms & ZETA_SUM_NODE) idx_node = nforms++;
+  if (forms & ZETA_SUM_GAMMA) idx_gamma = nforms++;
+  if (want_p) idx_part = nforms++;
+  const size_t per_form = static_cast<size_t>(lmax + 1) * nb * nb;
+  if (cudaMemsetAsync(zeta, 0, sizeof(double) * per_form * nforms, stream) != cudaSuccess) return ZETA_ECUDA;
+  const int nparts = gram_ctas(c);
+  const double inv_ng = 1.0 / static_cast<double>(c->ng);
+  for (int l = 0; l <= lmax; ++l) {
+    if (want_p) {
+      double* out = zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb;
+      ZK_TRY(launch_mass(c, dhat, l, part, stream));
+      ZK_TRY(launch_reduce(c, part, nparts, -(2.0 * l + 1.0) / (4.0 * 3.14159265358979323846), nullptr, out, stream));
+    }
+    for (int m = -l; m <= l; ++m) {
+      ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, fields, stream));
+      if (idx_node >= 0) {
+        ZK_TRY(launch_gram_node(c, dl, fields, part, stream));
+        ZK_TRY(launch_reduce(c, part, nparts, inv_ng, nullptr, zeta + idx_node * per_form + static_cast<size_t>(l) * nb * nb, stream));
+      }
+      if (idx_gamma >= 0) {
+        ZK_TRY(launch_gram_gamma(c, dl, fields, part, stream));
+        ZK_TRY(launch_reduce(c, part, nparts, inv_ng, nullptr, zeta + idx_gamma * per_form + static_cast<size_t>(l) * nb * nb, stream));
+      }
+      if (idx_part >= 0) {
+        ZK_TRY(launch_gram_particles(c, sorted, tstart, fields, part, stream));
+        ZK_TRY(launch_reduce(c, part, nparts, 1.0, wsum, zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb, stream));
+      }
+    }
+  }
+  return ZETA_OK;
+}
+
+int zeta_get_status(zeta_ctx* c, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return ZETA_ECUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ZETA_ECUDA;
+  if (cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) return ZETA_ECUDA;
+  if (h & 2) return ZETA_ETIMEOUT;
+  if (h & 1) return ZETA_EDATA;
+  return ZETA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,324 @@
+// 3-D DFT stages of the method on sm_103a (Fig. 1 steps (2) and (5)).
+//
+// Forward (once per catalogue):  delta (real [z][y][x]) -> x-pass R2C -> y-pass -> z-pass
+//   gives delta_hat[z][y][nx < n/2]; the x-Nyquist column is dropped because every kernel
+//   of the method vanishes on Nyquist planes.
+// Inverse (per (l, m) and radial bin; the hot loop):  z-pass that reads delta_hat once
+//   per CTA tile and, for every bin of the launch, multiplies by the multipole window
+//   K_lm,b(n) = i^l [sqrt(4 pi) jbar_l(|k|; b) / N_g] R_lm(n-hat) (Eqs. 3PCF-multipole-window
+//   and SFC-3PCF-vertex) before transforming -> y-pass -> x-pass C2R, in place in the
+//   caller's field buffer: each half spectrum (n^3/2 complex) occupies exactly the bytes of
+//   its real field (n^3 floats).
+//
+// Every pass moves a tile of T contiguous complex columns (or RB rows) between HBM and
+// shared memory with coalesced accesses and transforms it with the radix-8 shared-memory
+// FFT of fft.cuh.
+#include "fft.cuh"
+#include "zeta_internal.h"
+
+namespace zk {
+
+__constant__ float c_ylm_mm[kMaxL + 1];
+__constant__ float c_ylm_a[(kMaxL + 1) * (kMaxL + 1)];
+__constant__ float c_ylm_b[(kMaxL + 1) * (kMaxL + 1)];
+
+int set_ylm_constants() {
+  double mm[kMaxL + 1], a[(kMaxL + 1) * (kMaxL + 1)], b[(kMaxL + 1) * (kMaxL + 1)];
+  host_ylm_constants(mm, a, b);
+  float fm[kMaxL + 1], fa[(kMaxL + 1) * (kMaxL + 1)], fb[(kMaxL + 1) * (kMaxL + 1)];
+  for (int i = 0; i <= kMaxL; ++i) fm[i] = static_cast<float>(mm[i]);
+  for (int i = 0; i < (kMaxL + 1) * (kMaxL + 1); ++i) {
+    fa[i] = static_cast<float>(a[i]);
+    fb[i] = static_cast<float>(b[i]);
+  }
+  if (cudaMemcpyToSymbol(c_ylm_mm, fm, sizeof(fm)) != cudaSuccess) return ZETA_ECUDA;
+  if (cudaMemcpyToSymbol(c_ylm_a, fa, sizeof(fa)) != cudaSuccess) return ZETA_ECUDA;
+  if (cudaMemcpyToSymbol(c_ylm_b, fb, sizeof(fb)) != cudaSuccess) return ZETA_ECUDA;
+  return ZETA_OK;
+}
+
+// R_lm of the integer wavevector (nx, ny, nz) != 0: fully normalised associated-Legendre
+// recurrence in cos(theta) times Re/Im of (sin(theta) e^{i phi})^|m|.
+__device__ __forceinline__ float ylm_dev(int l, int m, float nx, float ny, float nz) {
+  const float r2 = nx * nx + ny * ny + nz * nz;
+  if (r2 == 0.f) return l == 0 ? 0.28209479177387814f : 0.f;
+  const float rinv = 1.0f / sqrtf(r2);
+  const float ct = nz * rinv, sx = nx * rinv, sy = ny * rinv;
+  const int am = m < 0 ? -m : m;
+  float cr = 1.f, ci = 0.f;
+  for (int k = 0; k < am; ++k) {
+    const float t = cr * sx - ci * sy;
+    ci = cr * sy + ci * sx;
+    cr = t;
+  }
+  float qm1 = 0.f, qc = c_ylm_mm[am];
+  for (int ll = am + 1; ll <= l; ++ll) {
+    const float qn = c_ylm_a[ll * (kMaxL + 1) + am] * ct * qc - c_ylm_b[ll * (kMaxL + 1) + am] * qm1;
+    qm1 = qc;
+    qc = qn;
+  }
+  const float ang = (m == 0) ? 1.f : 1.41421356237309505f * (m > 0 ? cr : ci);
+  return qc * ang;
+}
+
+__device__ __forceinline__ int signed_freq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// ---------------------------------------------------------------------------------------
+// Complex pencils along y (AXIS 1) or z (AXIS 2), in place; grid (nc/T, n, nfields).
+template <int N, int T, bool INV, int AXIS>
+__global__ void __launch_bounds__(256) k_fft_axis(float2* __restrict__ data, long long fstride,
+                                                  const float2* __restrict__ twg) {
+  constexpr int NC = N / 2;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* buf = sm + N;
+  const int x0 = blockIdx.x * T;
+  const long long o = blockIdx.y;
+  float2* d = data + blockIdx.z * fstride;
+  const long long stride = (AXIS == 1) ? NC : static_cast<long long>(N) * NC;
+  const long long base = (AXIS == 1) ? o * N * NC + x0 : o * NC + x0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+    const int k = idx / T, c = idx % T;
+    buf[idx] = d[base + k * stride + c];
+  }
+  fft_smem<N, INV>(buf, T, T, tw);
+  for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+    const int k = idx / T, c = idx % T;
+    d[base + k * stride + c] = buf[fft_pos_of<N>(k) * T + c];
+  }
+}
+
+// Real rows -> half spectrum without Nyquist; grid (n*n/RB).
+template <int N, int RB>
+__global__ void __launch_bounds__(256) k_r2c_x(const float* __restrict__ in, float2* __restrict__ out,
+                                               const float2* __restrict__ twg) {
+  constexpr int NC = N / 2, PS = RB + 1;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;          // W_N^e, e < N
+  float2* tw2 = sm + N;     // W_NC^e = W_N^{2e}, e < NC
+  float2* buf = tw2 + NC;   // [NC][PS]
+  const long long r0 = static_cast<long long>(blockIdx.x) * RB;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < NC; i += blockDim.x) tw2[i] = twg[2 * i];
+  const float2* rin = reinterpret_cast<const float2*>(in);
+  for (int idx = threadIdx.x; idx < NC * RB; idx += blockDim.x) {
+    const int r = idx / NC, j = idx % NC;
+    buf[j * PS + r] = rin[(r0 + r) * NC + j];
+  }
+  fft_smem<NC, false>(buf, PS, RB, tw2);
+  for (int idx = threadIdx.x; idx < NC * RB; idx += blockDim.x) {
+    const int r = idx / NC, k = idx % NC;
+    const float2 zk = buf[fft_pos_of<NC>(k) * PS + r];
+    const float2 zm = cconj(buf[fft_pos_of<NC>((NC - k) & (NC - 1)) * PS + r]);
+    const float2 e = cscale(cadd(zk, zm), 0.5f);
+    const float2 dd = csub(zk, zm);
+    const float2 od = make_float2(0.5f * dd.y, -0.5f * dd.x);  // (zk - conj zm) / (2i)
+    out[(r0 + r) * NC + k] = cadd(e, cmul(tw[k], od));
+  }
+}
+
+// Half spectrum (x-Nyquist implicitly zero) -> real rows, in place; grid (n*n/RB, nfields).
+template <int N, int RB>
+__global__ void __launch_bounds__(256) k_c2r_x(float2* __restrict__ data, long long fstride,
+                                               const float2* __restrict__ twg) {
+  constexpr int NC = N / 2, PS = RB + 1;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* tw2 = sm + N;
+  float2* buf = tw2 + NC;
+  float2* d = data + blockIdx.y * fstride;
+  const long long r0 = static_cast<long long>(blockIdx.x) * RB;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < NC; i += blockDim.x) tw2[i] = twg[2 * i];
+  for (int idx = threadIdx.x; idx < NC * RB; idx += blockDim.x) {
+    const int r = idx / NC, k = idx % NC;
+    buf[k * PS + r] = d[(r0 + r) * NC + k];
+  }
+  __syncthreads();
+  // Z[k] = (X[k] + conj X[NC-k]) + i e^{+2 pi i k/N} (X[k] - conj X[NC-k]), X[NC] = 0
+  constexpr int NP = NC / 2 + 1;
+  for (int idx = threadIdx.x; idx < NP * RB; idx += blockDim.x) {
+    const int r = idx / NP, k = idx % NP;
+    const int kp = NC - k;  // partner (== NC for k == 0, which is the zero Nyquist)
+    const float2 xk = buf[k * PS + r];
+    const float2 xp = (k == 0) ? make_float2(0.f, 0.f) : buf[kp * PS + r];
+    const float2 wk = cconj(tw[k]);
+    const float2 zk = cadd(cadd(xk, cconj(xp)), mul_i(cmul(wk, csub(xk, cconj(xp)))));
+    if (k != 0 && kp != k) {
+      const float2 wp = cconj(tw[kp]);
+      const float2 zp = cadd(cadd(xp, cconj(xk)), mul_i(cmul(wp, csub(xp, cconj(xk)))));
+      buf[kp * PS + r] = zp;
+    }
+    buf[k * PS + r] = zk;
+  }
+  fft_smem<NC, true>(buf, PS, RB, tw2);
+  for (int idx = threadIdx.x; idx < NC * RB; idx += blockDim.x) {
+    const int r = idx / NC, j = idx % NC;
+    d[(r0 + r) * NC + j] = buf[fft_pos_of<NC>(j) * PS + r];
+  }
+}
+
+// z-pass of the field reconstruction with the multipole window fused in.
+// grid (nc/T, n); each CTA keeps its delta_hat tile [z][T] in shared memory and emits
+// one transformed tile per field f < nf into out + f * fstride.
+template <int N, int T>
+__global__ void __launch_bounds__(256) k_alm_z(const float2* __restrict__ dhat, float2* __restrict__ out,
+                                               long long fstride, int nf, const float* __restrict__ jtab,
+                                               long long nn2, int l, int m, const float2* __restrict__ twg) {
+  constexpr int NC = N / 2;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* sdh = tw + N;        // [N][T]
+  float2* work = sdh + N * T;  // [N][T]
+  float* sang = reinterpret_cast<float*>(work + N * T);
+  int* sn2 = reinterpret_cast<int*>(sang + N * T);
+  const int x0 = blockIdx.x * T;
+  const int iy = blockIdx.y;
+  const long long colbase = static_cast<long long>(iy) * NC + x0;
+  const long long zstride = static_cast<long long>(N) * NC;
+  if (iy == N / 2) {  // y-Nyquist row: the window is zero
+    for (int f = 0; f < nf; ++f)
+      for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+        const int z = idx / T, c = idx % T;
+        out[f * fstride + colbase + z * zstride + c] = make_float2(0.f, 0.f);
+      }
+    return;
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  const float sgn = ((l & 3) < 2) ? 1.f : -1.f;  // real part of i^l (or of i^{l-1} for odd l)
+  const int ny = signed_freq(iy, N);
+  for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+    const int z = idx / T, c = idx % T;
+    sdh[idx] = dhat[colbase + z * zstride + c];
+    const int nz = signed_freq(z, N), nx = x0 + c;
+    const bool nyq = (z == N / 2);
+    sn2[idx] = nyq ? 0 : nx * nx + ny * ny + nz * nz;
+    sang[idx] = nyq ? 0.f : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz));
+  }
+  __syncthreads();
+  for (int f = 0; f < nf; ++f) {
+    const float* jt = jtab + f * nn2;
+    for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+      const float s = sang[idx] * __ldg(jt + sn2[idx]);
+      float2 v = cscale(sdh[idx], s);
+      if (l & 1) v = mul_i(v);
+      work[idx] = v;
+    }
+    fft_smem<N, true>(work, T, T, tw);
+    for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+      const int z = idx / T, c = idx % T;
+      out[f * fstride + colbase + z * zstride + c] = work[fft_pos_of<N>(z) * T + c];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kTz = 8;   // columns per z-pass (window) tile
+constexpr int kTy = 16;  // columns per plain pencil tile
+constexpr int kRB = 8;   // rows per x-pass tile
+
+template <typename K>
+int set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) !=
+        cudaSuccess)
+      return ZETA_ECUDA;
+  }
+  return ZETA_OK;
+}
+
+inline int check_launch() { return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA; }
+
+template <int N>
+int r2c_impl(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t s) {
+  constexpr int NC = N / 2;
+  constexpr int T = kTy < NC ? kTy : NC;
+  size_t smx = (N + NC + NC * (kRB + 1)) * sizeof(float2);
+  if (set_smem(k_r2c_x<N, kRB>, smx)) return ZETA_ECUDA;
+  k_r2c_x<N, kRB><<<N * N / kRB, 256, smx, s>>>(delta, dhat, c->d_tw);
+  size_t sma = (N + N * T) * sizeof(float2);
+  if (set_smem(k_fft_axis<N, T, false, 1>, sma) || set_smem(k_fft_axis<N, T, false, 2>, sma)) return ZETA_ECUDA;
+  k_fft_axis<N, T, false, 1><<<dim3(NC / T, N, 1), 256, sma, s>>>(dhat, 0, c->d_tw);
+  k_fft_axis<N, T, false, 2><<<dim3(NC / T, N, 1), 256, sma, s>>>(dhat, 0, c->d_tw);
+  return check_launch();
+}
+
+template <int N>
+int c2r_impl(const zeta_ctx* c, float2* data, int nf, cudaStream_t s, bool do_y) {
+  constexpr int NC = N / 2;
+  constexpr int T = kTy < NC ? kTy : NC;
+  const long long fstride = static_cast<long long>(N) * N * NC;
+  if (do_y) {
+    size_t sma = (N + N * T) * sizeof(float2);
+    if (set_smem(k_fft_axis<N, T, true, 1>, sma)) return ZETA_ECUDA;
+    k_fft_axis<N, T, true, 1><<<dim3(NC / T, N, nf), 256, sma, s>>>(data, fstride, c->d_tw);
+  }
+  size_t smx = (N + NC + NC * (kRB + 1)) * sizeof(float2);
+  if (set_smem(k_c2r_x<N, kRB>, smx)) return ZETA_ECUDA;
+  k_c2r_x<N, kRB><<<dim3(N * N / kRB, nf), 256, smx, s>>>(data, fstride, c->d_tw);
+  return check_launch();
+}
+
+template <int N>
+int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float* out, cudaStream_t s) {
+  constexpr int NC = N / 2;
+  constexpr int T = kTz < NC ? kTz : NC;
+  const long long fstride = static_cast<long long>(N) * N * NC;
+  size_t smz = N * sizeof(float2) + static_cast<size_t>(N) * T * (2 * sizeof(float2) + sizeof(float) + sizeof(int));
+  if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
+  const float* jt = c->d_jtab + (static_cast<long long>(l) * c->p.nbins + b0) * c->nn2;
+  float2* o = reinterpret_cast<float2*>(out);
+  k_alm_z<N, T><<<dim3(NC / T, N), 256, smz, s>>>(dhat, o, fstride, nf, jt, c->nn2, l, m, c->d_tw);
+  if (check_launch()) return ZETA_ECUDA;
+  return c2r_impl<N>(c, o, nf, s, true);
+}
+
+// Full inverse of nf half spectra in place: z-, y- and x-passes.
+template <int N>
+int c2r_full(const zeta_ctx* c, float2* data, int nf, cudaStream_t s) {
+  constexpr int NC = N / 2;
+  constexpr int T = kTy < NC ? kTy : NC;
+  const long long fstride = static_cast<long long>(N) * N * NC;
+  size_t sma = (N + N * T) * sizeof(float2);
+  if (set_smem(k_fft_axis<N, T, true, 2>, sma)) return ZETA_ECUDA;
+  k_fft_axis<N, T, true, 2><<<dim3(NC / T, N, nf), 256, sma, s>>>(data, fstride, c->d_tw);
+  if (check_launch()) return ZETA_ECUDA;
+  return c2r_impl<N>(c, data, nf, s, true);
+}
+
+}  // namespace
+
+#define ZK_DISPATCH_N(n, CALL) \
+  switch (n) {                 \
+    case 16: return CALL(16);  \
+    case 32: return CALL(32);  \
+    case 64: return CALL(64);  \
+    case 128: return CALL(128); \
+    case 256: return CALL(256); \
+    case 512: return CALL(512); \
+    default: return ZETA_ENOTSUP; \
+  }
+
+int launch_r2c(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t s) {
+#define ZK_CALL(NN) r2c_impl<NN>(c, delta, dhat, s)
+  ZK_DISPATCH_N(c->n, ZK_CALL)
+#undef ZK_CALL
+}
+
+int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float* out, cudaStream_t s) {
+#define ZK_CALL(NN) alm_impl<NN>(c, dhat, l, m, b0, nf, out, s)
+  ZK_DISPATCH_N(c->n, ZK_CALL)
+#undef ZK_CALL
+}
+
+int launch_c2r_inplace(const zeta_ctx* c, float2* data, int nf, cudaStream_t s) {
+#define ZK_CALL(NN) c2r_full<NN>(c, data, nf, s)
+  ZK_DISPATCH_N(c->n, ZK_CALL)
+#undef ZK_CALL
+}
+
+}  // namespace zk

@@ -1,0 +1,282 @@
+// Host float64 tables of the method (Fig. 1 step (3): tabulating the k-space windows).
+//
+//  * jbar_l(k; b): the radial window of bin b, the r^2-weighted shell average of the
+//    spherical Bessel function j_l(k r) (the vertex window of Eq. 3PCF-multipole-window
+//    averaged over a radial bin).  Integrated by Gauss-Legendre on sub-intervals no longer
+//    than 3 radians of k r; j_0..j_L come from the three-term recurrence, upward when x > L
+//    and Miller's downward recurrence (normalised to sin x / x) otherwise, with the power
+//    series for x < 1.  Indexed by the integer |n|^2, so each lattice wavevector reads the
+//    exact value of its own |k|.
+//  * Real spherical harmonics: constants of the fully normalised associated-Legendre
+//    recurrence.
+//  * B-spline mass (Gram) values M(a) = beta_{2D}(a) and the per-cell Gauss-Legendre
+//    quadrature used by the connection-coefficient sum (Eq. con-coeff), from the explicit
+//    truncated-power form of the centred cardinal B-spline.
+//  * DFT twiddles.
+#include <cmath>
+#include <thread>
+#include <vector>
+
+#include "zeta_internal.h"
+
+namespace zk {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(q, 0.0);
+  w.assign(q, 0.0);
+  for (int i = 0; i < q; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (q + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= q; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      // p1 = P_q(z), p0 = P_{q-1}(z)
+      double dp = q * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) {
+        p0 = 1.0;
+        p1 = z;
+        for (int k = 2; k <= q; ++k) {
+          double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = q * (z * p1 - p0) / (z * z - 1.0);
+        break;
+      }
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= q; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    const double dp = q * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = -z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// j_0 .. j_L at x >= 0 into j[0..L] (j must hold max(L, 1) + 1 values).
+void sph_bessel_all(int L, double x, double* j) {
+  if (x == 0.0) {
+    j[0] = 1.0;
+    for (int l = 1; l <= L; ++l) j[l] = 0.0;
+    return;
+  }
+  if (x < 1.0) {
+    // j_l(x) = x^l / (2l+1)!! * sum_k (-x^2/2)^k / (k! (2l+3)(2l+5)...(2l+2k+1))
+    double lead = 1.0;  // x^l / (2l+1)!!
+    for (int l = 0; l <= L; ++l) {
+      if (l > 0) lead *= x / (2.0 * l + 1.0);
+      double term = 1.0, sum = 1.0;
+      for (int k = 1; k < 30; ++k) {
+        term *= -0.5 * x * x / (k * (2.0 * l + 2.0 * k + 1.0));
+        sum += term;
+        if (std::fabs(term) < 1e-18 * std::fabs(sum)) break;
+      }
+      j[l] = lead * sum;
+    }
+    return;
+  }
+  const double s = std::sin(x), c = std::cos(x);
+  const double j0 = s / x;
+  const double j1 = s / (x * x) - c / x;
+  if (x > L) {
+    j[0] = j0;
+    if (L >= 1) j[1] = j1;
+    for (int l = 1; l < L; ++l) j[l + 1] = (2.0 * l + 1.0) / x * j[l] - j[l - 1];
+    return;
+  }
+  const int lstart = L + 30 + static_cast<int>(x);
+  std::vector<double> f(lstart + 2, 0.0);
+  f[lstart] = 1e-300;
+  for (int l = lstart; l >= 1; --l) {
+    f[l - 1] = (2.0 * l + 1.0) / x * f[l] - f[l + 1];
+    if (std::fabs(f[l - 1]) > 1e250) {  // rescale to stay finite
+      for (int q = l - 1; q <= lstart; ++q) f[q] *= 1e-250;
+    }
+  }
+  // f is proportional to the minimal solution j_l; normalise on the larger of j_0, j_1
+  const double scale = (std::fabs(j0) >= std::fabs(j1)) ? j0 / f[0] : j1 / f[1];
+  for (int l = 0; l <= L; ++l) j[l] = f[l] * scale;
+}
+
+double cardinal_bspline(int order, double x) {
+  // centred cardinal B-spline of the given order (degree order-1, support [-order/2, order/2])
+  double sum = 0.0, binom = 1.0, fact = 1.0;
+  for (int k = 1; k < order; ++k) fact *= k;
+  for (int jj = 0; jj <= order; ++jj) {
+    const double t = x + 0.5 * order - jj;
+    if (t > 0.0) sum += ((jj & 1) ? -binom : binom) * std::pow(t, order - 1);
+    binom = binom * (order - jj) / (jj + 1.0);
+  }
+  return sum / fact;
+}
+
+// Accumulate sum_q w_q r_q^2 j_l(k r_q) over [r_lo, r_hi) for l <= L into num[0..L].
+void shell_moments(int L, double k, double r_lo, double r_hi, const std::vector<double>& gx,
+                   const std::vector<double>& gw, double* num) {
+  const int nsub = std::max(1, static_cast<int>(std::ceil(k * (r_hi - r_lo) / 3.0)));
+  const double h = (r_hi - r_lo) / nsub;
+  double jl[kMaxL + 2];
+  for (int l = 0; l <= L; ++l) num[l] = 0.0;
+  for (int s = 0; s < nsub; ++s) {
+    const double a = r_lo + s * h;
+    for (size_t q = 0; q < gx.size(); ++q) {
+      const double r = a + 0.5 * h * (gx[q] + 1.0);
+      sph_bessel_all(L, k * r, jl);
+      const double wr = 0.5 * h * gw[q] * r * r;
+      for (int l = 0; l <= L; ++l) num[l] += wr * jl[l];
+    }
+  }
+}
+
+}  // namespace
+
+void host_jbar_values(int l, double box, double r_lo, double r_hi, const int64_t* n2, int64_t count,
+                      double* out) {
+  std::vector<double> gx, gw;
+  gauss_legendre(12, gx, gw);
+  const double den = (r_hi * r_hi * r_hi - r_lo * r_lo * r_lo) / 3.0;
+  double num[kMaxL + 2];
+  for (int64_t i = 0; i < count; ++i) {
+    const double k = 2.0 * kPi / box * std::sqrt(static_cast<double>(n2[i]));
+    shell_moments(l, k, r_lo, r_hi, gx, gw, num);
+    out[i] = num[l] / den;
+  }
+}
+
+void host_jbar_table(int n, double box, int lmax, int nbins, const double* edges, std::vector<float>& out) {
+  const int64_t nn2 = table_n2_count(n);
+  const double ng = static_cast<double>(n) * n * n;
+  const double pref = std::sqrt(4.0 * kPi) / ng;
+  out.assign(static_cast<size_t>(lmax + 1) * nbins * nn2, 0.0f);
+  std::vector<double> gx, gw;
+  gauss_legendre(12, gx, gw);
+  unsigned nth = std::thread::hardware_concurrency();
+  if (nth == 0) nth = 1;
+  if (nth > 64) nth = 64;
+  auto work = [&](unsigned t) {
+    double num[kMaxL + 2];
+    for (int64_t i = t; i < nn2; i += nth) {
+      const double k = 2.0 * kPi / box * std::sqrt(static_cast<double>(i));
+      for (int b = 0; b < nbins; ++b) {
+        const double r_lo = edges[b], r_hi = edges[b + 1];
+        const double den = (r_hi * r_hi * r_hi - r_lo * r_lo * r_lo) / 3.0;
+        shell_moments(lmax, k, r_lo, r_hi, gx, gw, num);
+        for (int l = 0; l <= lmax; ++l)
+          out[(static_cast<size_t>(l) * nbins + b) * nn2 + i] = static_cast<float>(pref * num[l] / den);
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (unsigned t = 1; t < nth; ++t) pool.emplace_back(work, t);
+  work(0);
+  for (auto& th : pool) th.join();
+}
+
+void host_twiddles(int n, std::vector<float2>& out) {
+  out.resize(n);
+  for (int e = 0; e < n; ++e) {
+    const double ang = 2.0 * kPi * e / n;
+    out[e] = make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(-std::sin(ang)));
+  }
+}
+
+void host_ylm_constants(double* mm, double* a, double* b) {
+  for (int m = 0; m <= kMaxL; ++m) {
+    double prod = 1.0;
+    for (int k = 1; k <= m; ++k) prod *= (2.0 * k - 1.0) / (2.0 * k);
+    mm[m] = std::sqrt((2.0 * m + 1.0) / (4.0 * kPi) * prod);
+  }
+  for (int l = 0; l <= kMaxL; ++l) {
+    for (int m = 0; m <= kMaxL; ++m) {
+      double av = 0.0, bv = 0.0;
+      if (l >= m + 1) {
+        const double l2 = static_cast<double>(l) * l, m2 = static_cast<double>(m) * m;
+        av = std::sqrt((4.0 * l2 - 1.0) / (l2 - m2));
+        if (l >= m + 2) bv = std::sqrt((2.0 * l + 1.0) * ((l - 1.0) * (l - 1.0) - m2) / ((2.0 * l - 3.0) * (l2 - m2)));
+      }
+      a[l * (kMaxL + 1) + m] = av;
+      b[l * (kMaxL + 1) + m] = bv;
+    }
+  }
+}
+
+void host_mass_1d(int dsup, double* out) {
+  for (int a = -(dsup - 1); a <= dsup - 1; ++a) out[a + dsup - 1] = cardinal_bspline(2 * dsup, a);
+}
+
+void host_mass_hat(int n, int dsup, std::vector<float>& out) {
+  double m[16];
+  host_mass_1d(dsup, m);
+  out.resize(n);
+  for (int k = 0; k < n; ++k) {
+    double v = m[dsup - 1];
+    for (int a = 1; a < dsup; ++a) v += 2.0 * m[dsup - 1 + a] * std::cos(2.0 * kPi * k * a / n);
+    out[k] = static_cast<float>(v);
+  }
+}
+
+void host_cell_quadrature(int q, int dsup, std::vector<double>& t, std::vector<double>& wq,
+                          std::vector<double>& beta) {
+  std::vector<double> gx, gw;
+  gauss_legendre(q, gx, gw);
+  t.resize(q);
+  wq.resize(q);
+  beta.resize(static_cast<size_t>(q) * dsup);
+  for (int i = 0; i < q; ++i) {
+    t[i] = 0.5 * (gx[i] + 1.0);
+    wq[i] = 0.5 * gw[i];
+    for (int o = 0; o < dsup; ++o) beta[i * dsup + o] = cardinal_bspline(dsup, t[i] + dsup / 2 - 1 - o);
+  }
+}
+
+}  // namespace zk
+
+extern "C" int zeta_host_jbar(int l, double box, double r_lo, double r_hi, const int64_t* n2, int64_t count,
+                              double* out) {
+  if (l < 0 || l > zk::kMaxL || !(box > 0) || !(r_lo > 0) || !(r_hi > r_lo) || count < 0 || (count && (!n2 || !out)))
+    return ZETA_EINVAL;
+  for (int64_t i = 0; i < count; ++i)
+    if (n2[i] < 0) return ZETA_EINVAL;
+  zk::host_jbar_values(l, box, r_lo, r_hi, n2, count, out);
+  return ZETA_OK;
+}
+
+extern "C" double zeta_host_ylm(int l, int m, double vx, double vy, double vz) {
+  if (l < 0 || l > zk::kMaxL || m < -l || m > l) return 0.0;
+  static double mm[zk::kMaxL + 1], a[(zk::kMaxL + 1) * (zk::kMaxL + 1)], b[(zk::kMaxL + 1) * (zk::kMaxL + 1)];
+  static bool init = false;
+  if (!init) {
+    zk::host_ylm_constants(mm, a, b);
+    init = true;
+  }
+  const double r2 = vx * vx + vy * vy + vz * vz;
+  if (r2 == 0.0) return l == 0 ? 1.0 / std::sqrt(4.0 * 3.14159265358979323846) : 0.0;
+  const double rinv = 1.0 / std::sqrt(r2);
+  const double ct = vz * rinv, sx = vx * rinv, sy = vy * rinv;
+  const int am = m < 0 ? -m : m;
+  double cr = 1.0, ci = 0.0;
+  for (int k = 0; k < am; ++k) {
+    const double t = cr * sx - ci * sy;
+    ci = cr * sy + ci * sx;
+    cr = t;
+  }
+  double qm1 = 0.0, qc = mm[am];
+  for (int ll = am + 1; ll <= l; ++ll) {
+    const double qn = a[ll * (zk::kMaxL + 1) + am] * ct * qc - b[ll * (zk::kMaxL + 1) + am] * qm1;
+    qm1 = qc;
+    qc = qn;
+  }
+  const double ang = (m == 0) ? 1.0 : std::sqrt(2.0) * (m > 0 ? cr : ci);
+  return qc * ang;
+}

@@ -1,0 +1,92 @@
+// Internal declarations shared by the translation units of libzeta.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/zeta.h"
+
+namespace zk {
+
+constexpr int kMaxL = 14;       // highest multipole supported by the tables
+constexpr int kMaxBins = 32;    // highest number of radial bins
+constexpr int kTile = 8;        // particle tiles are kTile^3 cells
+constexpr int kMaxCtas = 4096;  // upper bound on persistent CTAs writing Gram partials
+
+// ---- host tables (tables.cpp), all computed in float64 ----
+// Number of integer |n|^2 values with every |n_d| <= n/2 - 1 (Nyquist planes excluded).
+inline int64_t table_n2_count(int n) {
+  const int64_t h = n / 2 - 1;
+  return 3 * h * h + 1;
+}
+// sqrt(4 pi) jbar_l(k; b) / N_g for l <= lmax, all bins, all n2 < table_n2_count(n).
+void host_jbar_table(int n, double box, int lmax, int nbins, const double* edges, std::vector<float>& out);
+void host_jbar_values(int l, double box, double r_lo, double r_hi, const int64_t* n2, int64_t count,
+                      double* out);
+// W_n^e = exp(-2 pi i e / n), e < n, as (cos, sin) pairs rounded to float32.
+void host_twiddles(int n, std::vector<float2>& out);
+// Real-spherical-harmonic recurrence constants: mm[m], a[l][m], b[l][m] (l, m <= kMaxL).
+void host_ylm_constants(double* mm, double* a, double* b);
+// B-spline Gram values M(a) for |a| < dsup, index a + dsup - 1.
+void host_mass_1d(int dsup, double* out);
+// 1-D DFT of the mass sequence: Mhat(k) = sum_a M(a) cos(2 pi k a / n), k-index < n.
+void host_mass_hat(int n, int dsup, std::vector<float>& out);
+// Gauss-Legendre nodes/weights on [0, 1] (q points) and the stencil weights
+// beta(t_q + dsup/2 - 1 - o) for o < dsup: wq[q], beta[q * dsup + o].
+void host_cell_quadrature(int q, int dsup, std::vector<double>& t, std::vector<double>& wq,
+                          std::vector<double>& beta);
+
+}  // namespace zk
+
+struct zeta_ctx {
+  zeta_params p{};
+  std::vector<double> edges;
+  int n = 0, nc = 0;
+  int64_t ng = 0;
+  int64_t nn2 = 0;
+  int64_t ntiles = 0;
+  int num_sms = 0;
+  int device = 0;
+  int gamma_q = 0;
+  // device tables
+  float* d_jtab = nullptr;    // [(l * nbins + b) * nn2 + n2]
+  float2* d_tw = nullptr;     // W_n^e, e < n
+  float* d_mhat = nullptr;    // Mhat(k) for k-index < n
+  float* d_gq = nullptr;      // cell quadrature: weights[q] then beta[q*dsup+o]
+  int* d_status = nullptr;    // latched device status
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+namespace zk {
+
+// ---- launchers (fft.cu) ----
+int set_ylm_constants();
+int launch_r2c(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t s);
+int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float* out, cudaStream_t s);
+// Inverse-only helpers reused by other stages: C2R of nf half spectra in place.
+int launch_c2r_inplace(const zeta_ctx* c, float2* data, int nf, cudaStream_t s);
+
+// ---- launchers (assign.cu) ----
+int launch_assign(const zeta_ctx* c, const float4* parts, int64_t np, float* delta, double* wsum,
+                  unsigned long long* acc, double* scratch2, cudaStream_t s);
+int launch_wsum(const zeta_ctx* c, const float4* parts, int64_t np, double* wsum, double* scratch, cudaStream_t s);
+constexpr int kAssignScratchDoubles = 2 * 1024 + 4;
+int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sorted, int64_t* tile_start,
+                int* counts, int* orig, cudaStream_t s);
+
+// ---- launchers (sums.cu) ----
+int gram_ctas(const zeta_ctx* c);
+int launch_gram_node(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
+int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, double* partials,
+                      cudaStream_t s);
+int launch_gram_particles(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, const float* alm,
+                          double* partials, cudaStream_t s);
+int launch_mass(const zeta_ctx* c, const float2* dhat, int l, double* partials, cudaStream_t s);
+// out[b1][b2] += scale * (1/ *wdiv if wdiv) * sum_cta partials[cta][b1][b2], symmetrised.
+int launch_reduce(const zeta_ctx* c, const double* partials, int nparts, double scale, const double* wdiv,
+                  double* out, cudaStream_t s);
+
+}  // namespace zk

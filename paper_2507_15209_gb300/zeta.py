@@ -1,0 +1,226 @@
+"""Thin Python binding of libzeta (argument marshalling only).
+
+Every call forwards to the C ABI declared in include/zeta.h with the same name;
+PyTorch supplies device memory (torch.empty on CUDA) and the current stream.
+All arithmetic of the method runs in the library's CUDA kernels.  If the
+library has not been built the import fails loudly: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libzeta.so")
+
+SUM_NODE, SUM_GAMMA, SUM_PARTICLE = 1, 2, 4
+GRAM = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
+FORM_BITS = {"node": SUM_NODE, "gamma": SUM_GAMMA, "particle": SUM_PARTICLE}
+_ERR = {0: "ok", -1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ETIMEOUT", -5: "ENOTSUP", -6: "EWORKSPACE",
+        -7: "EDATA"}
+
+
+class ZetaError(RuntimeError):
+    def __init__(self, name: str, code: int):
+        super().__init__(f"{name} failed: {_ERR.get(code, code)} ({code})")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("box", ctypes.c_double), ("dsup", ctypes.c_int), ("lmax", ctypes.c_int),
+                ("nbins", ctypes.c_int), ("edges", ctypes.POINTER(ctypes.c_double)), ("gram", ctypes.c_int)]
+
+
+_lib = None
+
+_VP, _I64, _INT, _DBL, _SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+_SIGS = {
+    "zeta_version": ([], _INT),
+    "zeta_strerror": ([_INT], ctypes.c_char_p),
+    "zeta_create": ([ctypes.POINTER(_Params), ctypes.POINTER(_VP)], _INT),
+    "zeta_destroy": ([_VP], _INT),
+    "zeta_workspace_bytes": ([_VP, _I64, _INT], _SZ),
+    "zeta_set_workspace": ([_VP, _VP, _SZ], _INT),
+    "zeta_tile_count": ([_VP], _I64),
+    "zeta_assign": ([_VP, _VP, _I64, _VP, _VP, _VP], _INT),
+    "zeta_fft_r2c": ([_VP, _VP, _VP, _VP], _INT),
+    "zeta_reconstruct_alm": ([_VP, _VP, _INT, _INT, _INT, _INT, _VP, _VP], _INT),
+    "zeta_sum_grid": ([_VP, _VP, _VP, _INT, _VP, _VP], _INT),
+    "zeta_sort_particles": ([_VP, _VP, _I64, _VP, _VP, _VP], _INT),
+    "zeta_sum_particles": ([_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP], _INT),
+    "zeta_mass_term": ([_VP, _VP, _INT, _DBL, _VP, _VP], _INT),
+    "zeta_zeta_ell": ([_VP, _VP, _I64, _VP, _INT, _VP, _VP], _INT),
+    "zeta_get_status": ([_VP, _VP], _INT),
+    "zeta_host_jbar": ([_INT, _DBL, _DBL, _DBL, _VP, _I64, _VP], _INT),
+    "zeta_host_ylm": ([_INT, _INT, _DBL, _DBL, _DBL], _DBL),
+}
+
+
+def lib():
+    """Load libzeta.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libzeta.so not built at {LIB_PATH}; run paper_2507_15209_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _check(name, rc):
+    if rc != 0:
+        raise ZetaError(name, rc)
+
+
+def host_jbar(l: int, box: float, r_lo: float, r_hi: float, n2) -> np.ndarray:
+    n2 = np.ascontiguousarray(n2, dtype=np.int64)
+    out = np.empty(n2.shape, np.float64)
+    _check("zeta_host_jbar", lib().zeta_host_jbar(l, box, r_lo, r_hi, n2.ctypes.data, n2.size, out.ctypes.data))
+    return out
+
+
+def host_ylm(l: int, m: int, vx: float, vy: float, vz: float) -> float:
+    return lib().zeta_host_ylm(l, m, vx, vy, vz)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """A libzeta context with a torch-allocated workspace."""
+
+    def __init__(self, n: int, box: float, dsup: int, lmax: int, edges, gram: str = "fp32", np_max: int = 0,
+                 forms=("node",)):
+        import torch
+        self.n, self.box, self.dsup, self.lmax = int(n), float(box), int(dsup), int(lmax)
+        self.edges = np.ascontiguousarray(edges, dtype=np.float64)
+        self.nbins = len(self.edges) - 1
+        self._edges_c = self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p = _Params(self.n, self.box, self.dsup, self.lmax, self.nbins, self._edges_c, GRAM[gram])
+        h = ctypes.c_void_p()
+        _check("zeta_create", lib().zeta_create(ctypes.byref(p), ctypes.byref(h)))
+        self._h = h
+        self.np_max = int(np_max)
+        bits = self.form_bits(forms)
+        nbytes = lib().zeta_workspace_bytes(self._h, self.np_max, bits)
+        if nbytes == 0:
+            raise ZetaError("zeta_workspace_bytes", -1)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        _check("zeta_set_workspace", lib().zeta_set_workspace(self._h, self.workspace.data_ptr(), nbytes))
+
+    @staticmethod
+    def form_bits(forms) -> int:
+        if isinstance(forms, int):
+            return forms
+        return sum(FORM_BITS[f] for f in set(forms))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().zeta_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- grid helpers ----
+    @property
+    def ng(self):
+        return self.n ** 3
+
+    def _grid(self, dtype=None):
+        import torch
+        return torch.empty((self.n, self.n, self.n), dtype=dtype or torch.float32, device="cuda")
+
+    # ---- the C-ABI calls ----
+    def assign(self, particles):
+        import torch
+        delta = self._grid()
+        wsum = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check("zeta_assign", lib().zeta_assign(self._h, _ptr(particles), particles.shape[0], _ptr(delta),
+                                                _ptr(wsum), _stream()))
+        return delta, wsum
+
+    def fft_r2c(self, delta):
+        import torch
+        dhat = torch.empty((self.n, self.n, self.n // 2, 2), dtype=torch.float32, device="cuda")
+        _check("zeta_fft_r2c", lib().zeta_fft_r2c(self._h, _ptr(delta), _ptr(dhat), _stream()))
+        return dhat
+
+    def reconstruct_alm(self, delta_hat, l: int, m: int, b0: int = 0, b1: int | None = None, out=None):
+        import torch
+        b1 = self.nbins if b1 is None else b1
+        if out is None:
+            out = torch.empty((b1 - b0, self.n, self.n, self.n), dtype=torch.float32, device="cuda")
+        _check("zeta_reconstruct_alm", lib().zeta_reconstruct_alm(self._h, _ptr(delta_hat), l, m, b0, b1, _ptr(out),
+                                                                  _stream()))
+        return out
+
+    def _gram(self, gram):
+        import torch
+        if gram is None:
+            gram = torch.zeros((self.nbins, self.nbins), dtype=torch.float64, device="cuda")
+        return gram
+
+    def sum_grid(self, delta, alm, form: str = "node", gram=None):
+        gram = self._gram(gram)
+        _check("zeta_sum_grid", lib().zeta_sum_grid(self._h, _ptr(delta), _ptr(alm), FORM_BITS[form], _ptr(gram),
+                                                    _stream()))
+        return gram
+
+    def sort_particles(self, particles):
+        import torch
+        np_ = particles.shape[0]
+        sorted_ = torch.empty((np_, 4), dtype=torch.float32, device="cuda")
+        ntile = lib().zeta_tile_count(self._h)
+        start = torch.empty(ntile + 1, dtype=torch.int64, device="cuda")
+        _check("zeta_sort_particles", lib().zeta_sort_particles(self._h, _ptr(particles), np_, _ptr(sorted_),
+                                                                _ptr(start), _stream()))
+        return sorted_, start
+
+    def sum_particles(self, sorted_, tile_start, wsum, alm, gram=None):
+        gram = self._gram(gram)
+        _check("zeta_sum_particles", lib().zeta_sum_particles(self._h, _ptr(sorted_), _ptr(tile_start),
+                                                              sorted_.shape[0], _ptr(wsum), _ptr(alm), _ptr(gram),
+                                                              _stream()))
+        return gram
+
+    def mass_term(self, delta_hat, l: int, sign: float = 1.0, gram=None):
+        gram = self._gram(gram)
+        _check("zeta_mass_term", lib().zeta_mass_term(self._h, _ptr(delta_hat), l, float(sign), _ptr(gram),
+                                                      _stream()))
+        return gram
+
+    def zeta_ell(self, particles=None, delta=None, forms=("particle",), out=None):
+        """zeta_l(b1, b2) per form: returns {form: tensor (lmax+1, nb, nb) float64}."""
+        import torch
+        bits = self.form_bits(forms)
+        order = [f for f in ("node", "gamma", "particle") if bits & FORM_BITS[f]]
+        if out is None:
+            out = torch.empty((len(order), self.lmax + 1, self.nbins, self.nbins), dtype=torch.float64,
+                              device="cuda")
+        np_ = 0 if particles is None else particles.shape[0]
+        _check("zeta_zeta_ell", lib().zeta_zeta_ell(self._h, _ptr(particles), np_, _ptr(delta), bits, _ptr(out),
+                                                    _stream()))
+        return {f: out[i] for i, f in enumerate(order)}
+
+    def get_status(self) -> int:
+        return lib().zeta_get_status(self._h, _stream())

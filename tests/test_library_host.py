@@ -1,0 +1,94 @@
+"""CPU-side checks of libzeta: it builds, loads, exports every declared symbol, and its
+host float64 table code agrees with the oracle.  No kernel is launched here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import zeta_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def zmod():
+    from paper_2507_15209_gb300 import build
+    build.build()
+    from paper_2507_15209_gb300 import zeta
+    zeta.lib()
+    return zeta
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "zeta.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(zeta_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(zmod):
+    names = _declared()
+    assert len(names) >= 15
+    lib = zmod.lib()
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(zmod.declared_symbols()) == names
+
+
+def test_version_and_errors(zmod):
+    lib = zmod.lib()
+    assert lib.zeta_version() >= 10000
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.zeta_strerror(code)
+    assert lib.zeta_strerror(-99) == b"unknown error"
+
+
+def test_create_rejects_bad_parameters_without_touching_the_device(zmod):
+    lib = zmod.lib()
+    edges = np.array([5.0, 10.0, 20.0])
+    good = dict(n=32, box=100.0, dsup=4, lmax=4, nbins=2, gram=0)
+    bad = [dict(n=48), dict(n=8), dict(n=1024), dict(box=-1.0), dict(dsup=3), dict(lmax=15), dict(nbins=0),
+           dict(nbins=40), dict(gram=7), dict(box=30.0)]
+    for change in bad:
+        kw = {**good, **change}
+        e = edges if kw["nbins"] <= 2 else np.linspace(5, 20, kw["nbins"] + 1)
+        p = zmod._Params(kw["n"], kw["box"], kw["dsup"], kw["lmax"], kw["nbins"],
+                         e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), kw["gram"])
+        h = ctypes.c_void_p()
+        assert lib.zeta_create(ctypes.byref(p), ctypes.byref(h)) == -1, change
+        assert not h.value
+    for e in (np.array([0.0, 5.0, 10.0]), np.array([5.0, 4.0, 10.0])):
+        p = zmod._Params(32, 100.0, 4, 4, 2, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+        h = ctypes.c_void_p()
+        assert lib.zeta_create(ctypes.byref(p), ctypes.byref(h)) == -1
+    assert lib.zeta_destroy(None) == 0
+    assert lib.zeta_workspace_bytes(None, 0, 1) == 0
+
+
+@pytest.mark.parametrize("box,r_lo,r_hi", [(500.0, 10.0, 20.0), (2000.0, 190.25, 200.0), (1000.0, 5.0, 14.6667)])
+def test_host_jbar_matches_oracle(zmod, box, r_lo, r_hi):
+    n = 512
+    h = n // 2 - 1
+    rng = np.random.default_rng(0)
+    n2 = np.unique(np.concatenate([np.arange(0, 40), rng.integers(0, 3 * h * h + 1, 400), [3 * h * h]]))
+    k = 2 * math.pi / box * np.sqrt(n2.astype(float))
+    for ell in (0, 1, 2, 5, 10, 14):
+        got = zmod.host_jbar(ell, box, r_lo, r_hi, n2)
+        want = O.jbar(ell, k, r_lo, r_hi)
+        np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-13)
+
+
+def test_host_ylm_matches_oracle(zmod):
+    rng = np.random.default_rng(1)
+    v = rng.integers(-255, 256, (200, 3)).astype(float)
+    v[0] = (0, 0, 7)
+    v[1] = (3, 0, 0)
+    for ell in range(15):
+        for m in range(-ell, ell + 1):
+            got = np.array([zmod.host_ylm(ell, m, *row) for row in v])
+            want = O.real_ylm(ell, m, v[:, 0], v[:, 1], v[:, 2])
+            np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12)
+    assert zmod.host_ylm(0, 0, 0.0, 0.0, 0.0) == pytest.approx(1 / math.sqrt(4 * math.pi), rel=1e-15)
+    assert zmod.host_ylm(3, 1, 0.0, 0.0, 0.0) == 0.0
