@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the in-situ multipole 3PCF measurement: seconds per catalogue.
+
+One step = one full measurement of zeta_l(r1, r2), l <= lmax, for one log-normal
+catalogue through libzeta's zeta_ell: B-spline assignment, R2C, the per-(l, m)
+windowed C2R of every radial bin, the particle-form and node-form summations, the
+mass term and the float64 reduction.  Default workload: 512^3 grid, 2000 Mpc/h box,
+16M particles, lmax 10, 20 bins, cubic B-spline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one catalogue per rank (weak scaling, no collective on
+the data path; only a barrier and a max-reduce of the timings).  --impl reference
+times the FP64 CPU oracle on a bounded sample of the same workload and scales it
+to one catalogue.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2507_15209_gb300 import mocks  # noqa: E402
+from paper_2507_15209_gb300.workloads import WORKLOADS, edges as wl_edges  # noqa: E402
+
+METRIC = "zeta_l(r1,r2) s/catalog at Ng=512^3"
+UNIT = "s/catalog"
+FALLBACK_HBM_GBS = 6800.0
+
+# dram bytes per launch from one ncu capture of the kernel, and the sha of the source file
+# it was built from (the entry is ignored once that source changes)
+NCU_TRAFFIC = {}
+
+
+def _sha(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled every 200 ms during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _make_inputs(w, rank):
+    rho = mocks.lognormal_density(w["n"], w["field_seed"] + 100 * rank)
+    parts = mocks.sample_particles(rho, w["n_p"], w["box"], w["sample_seed"] + 100 * rank)
+    return parts
+
+
+def _alg_bytes(stage, w, nb):
+    """Algorithmic HBM bytes of one launch of a stage (minimum traffic of what it computes)."""
+    ng = w["n"] ** 3
+    g = 4.0 * ng  # one float grid == one half spectrum without the x-Nyquist column
+    n_p = w["n_p"]
+    return {
+        "alm_z": g * (1 + nb),          # read delta_hat once, write nb z-transformed spectra
+        "alm_y": 2 * g * nb,            # read + write nb spectra
+        "alm_x": 2 * g * nb,            # read nb half spectra, write nb real fields
+        "gram_particles": g * nb + 16.0 * n_p,  # read nb fields once and the particles
+        "gram_node": g * (nb + 1),      # read nb fields and delta
+        "mass": g,                      # read delta_hat
+        "r2c": 2 * g,                   # per pass: read + write one grid
+    }.get(stage)
+
+
+def _oracle_prepare(w, parts, sub=16):
+    """Oracle assignment of every sub-th particle (timed, scaled by sub) and forward DFT."""
+    from oracle import zeta_oracle as O
+    ps = parts[::sub].astype(np.float64)
+    t0 = time.perf_counter()
+    eps, wsum = O.assign(ps[:, :3], ps[:, 3], w["n"], w["box"], w["dsup"])
+    t_assign = (time.perf_counter() - t0) * sub
+    delta = O.contrast(eps, wsum)
+    del eps
+    t0 = time.perf_counter()
+    dh = np.fft.fftn(delta)
+    t_fft = time.perf_counter() - t0
+    return {"assign": t_assign, "fft": t_fft, "dh": dh, "sub": sub}
+
+
+def _oracle_sample(w, parts, prep):
+    """Time the FP64 oracle on a bounded slice of the workload and scale to one catalogue.
+
+    Slice: the prepared assignment (every 16th particle, x16) and full forward DFT, plus one
+    (l, m, b) = (2, 1, nbins/2) field: R_lm on 1/16 of the grid (x16), jbar of one bin and
+    the full inverse DFT, then interpolation and Gram at every 16th particle (x16).
+    """
+    from oracle import zeta_oracle as O
+    n, box, lmax, dsup = w["n"], w["box"], w["lmax"], w["dsup"]
+    e = wl_edges(w)
+    nb = len(e) - 1
+    sub = prep["sub"]
+    ell, m, b = 2, 1, nb // 2
+    iv = O.fft_integers(n)
+    nz, ny, nx = np.meshgrid(iv[: max(1, n // sub)], iv, iv, indexing="ij")
+    t0 = time.perf_counter()
+    O.real_ylm(ell, m, nx, ny, nz)
+    t_ylm = (time.perf_counter() - t0) * sub
+    del nx, ny, nz
+    t0 = time.perf_counter()
+    a = O.multipole_fields(prep["dh"], ell, m, n, box, e, bins=[b])
+    t_field = time.perf_counter() - t0
+    ps = parts[::sub].astype(np.float64)
+    t0 = time.perf_counter()
+    f = O.interpolate(a, ps[:, :3], n, box, dsup)
+    _ = (f * ps[:, 3]) @ f.T
+    t_interp = (time.perf_counter() - t0) * sub
+    del a, f
+    n_lm = (lmax + 1) ** 2
+    # per (l, m): one R_lm, then per bin jbar + inverse DFT (the field call minus its R_lm) + interpolation
+    t_bin = max(t_field - t_ylm, 0.0) + t_interp
+    total = prep["assign"] + prep["fft"] + n_lm * (t_ylm + nb * t_bin)
+    sample = (f"FP64 oracle on one catalogue of the workload: assignment of every {sub}th particle (x{sub}), "
+              f"full forward DFT, and one (l,m,b) field [R_lm on 1/{sub} of the grid (x{sub}), jbar, full "
+              f"inverse DFT, interpolation+Gram at every {sub}th particle (x{sub})], scaled by "
+              f"(lmax+1)^2={n_lm} (l,m) pairs and {nb} bins")
+    return total, sample
+
+
+def _emit(d):
+    print(json.dumps(d), flush=True)
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    parts = _make_inputs(w, 0)
+    prep = _oracle_prepare(w, parts)
+    vals = []
+    cpu_threads = 1
+    for i in range(args.warmup + args.steps):
+        total, sample = _oracle_sample(w, parts, prep)
+        if i >= args.warmup:
+            vals.append(total)
+    v = statistics.median(vals)
+    _emit({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic log-normal mock (seeded)",
+        "config": {"workload": args.workload, "n": w["n"], "box": w["box"], "n_p": w["n_p"], "lmax": w["lmax"],
+                   "nbins": w["nbins"], "dsup": w["dsup"]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    })
+    return 0
+
+
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2507_15209_gb300 import build as zbuild
+    zbuild.build()
+    from paper_2507_15209_gb300.zeta import Context
+
+    forms = tuple(args.forms.split(","))
+    parts = _make_inputs(w, rank)
+    e = wl_edges(w)
+    nb = len(e) - 1
+    ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=w["n_p"], forms=forms)
+    host = torch.from_numpy(parts).pin_memory()
+    dev = host.to("cuda", non_blocking=True)
+    nforms = len(forms)
+    out = torch.empty((nforms, w["lmax"] + 1, nb, nb), dtype=torch.float64, device="cuda")
+    out_host = torch.empty(out.shape, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctx.zeta_ell(particles=dev, forms=forms, out=out)
+    torch.cuda.synchronize()
+    if ctx.get_status() != 0:
+        raise RuntimeError("device status error during warm-up")
+
+    props = torch.cuda.get_device_properties(local_rank)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local_rank)
+    clocks = ClockSampler(gpu_id)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # device-timed region: inputs resident in HBM
+    clocks.start()
+    ctx.profile_enable(True)
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        ctx.zeta_ell(particles=dev, forms=forms, out=out)
+    t1.record(stream)
+    barrier()
+    ms_dev = t0.elapsed_time(t1)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+
+    # end-to-end region: host particles -> device, measurement, result -> host, every step
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dev.copy_(host, non_blocking=True)
+        ctx.zeta_ell(particles=dev, forms=forms, out=out)
+        out_host.copy_(out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    if ctx.get_status() != 0:
+        raise RuntimeError("device status error in the timed region")
+
+    t = torch.tensor([ms_dev, ms_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_dev, ms_e2e = float(t[0]), float(t[1])
+
+    if rank == 0:
+        cats = args.steps * world
+        value = ms_dev / 1e3 / cats
+        e2e_value = ms_e2e / 1e3 / cats
+        peak, peak_src = _peaks()
+        # dominant memory-bound kernel
+        rows = {k: v for k, v in prof.items() if v[1] > 0 and _alg_bytes(k, w, nb) is not None}
+        dom = max(rows, key=lambda k: rows[k][0])
+        ms_k, launches_k, _ = rows[dom]
+        bytes_launch = _alg_bytes(dom, w, nb)
+        achieved = bytes_launch * launches_k / (ms_k / 1e3) / 1e9
+        src = {"alm_z": "fft.cu", "alm_y": "fft.cu", "alm_x": "fft.cu", "r2c": "fft.cu",
+               "gram_particles": "sums.cu", "gram_node": "sums.cu", "mass": "sums.cu"}[dom]
+        tr = NCU_TRAFFIC.get(dom)
+        traffic = None
+        if tr and tr["sha"] == _sha(os.path.join(ROOT, "paper_2507_15209_gb300", "csrc", src)):
+            traffic = tr["bytes"]
+        gpu_launches = sum(v[1] for v in prof.values())
+        stages = {k: {"ms": round(v[0] / args.steps, 3), "launches": v[1] // args.steps}
+                  for k, v in prof.items() if v[1]}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_dev / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic log-normal mock (seeded), one catalogue per rank",
+            "config": {"workload": args.workload, "n": w["n"], "box": w["box"], "n_p": w["n_p"],
+                       "lmax": w["lmax"], "nbins": nb, "dsup": w["dsup"], "forms": list(forms),
+                       "gram": "fp32", "l2": "inputs larger than L2 (fields 20 x 512 MB, particles 256 MB)",
+                       "parallelism": f"catalogue-per-gpu x{world}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                         "alg_bytes_per_launch": bytes_launch, "launches": launches_k,
+                         "avg_launch_ms": ms_k / launches_k},
+            "stages_ms_per_step": stages,
+            "clocks": ck,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(parts.nbytes),
+                    "d2h_bytes_per_step": int(out.numel() * 8)},
+            "gpu_launches": int(gpu_launches),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            total, sample = _oracle_sample(w, parts, _oracle_prepare(w, parts))
+            line["cpu_baseline"] = {"value": total, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        _emit(line)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="box2000_n512_np16m")
+    ap.add_argument("--forms", default="particle,node")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+    return run_ours(args, w, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

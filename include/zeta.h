@@ -175,6 +175,16 @@ int zeta_zeta_ell(zeta_ctx* ctx, const float* particles, int64_t np, const float
  * ZETA_ETIMEOUT), clearing it. */
 int zeta_get_status(zeta_ctx* ctx, zeta_stream stream);
 
+/* ---- stage timers (tracing) ----
+ * When enabled, every kernel group the library issues is bracketed by a CUDA event pair on
+ * its stream.  zeta_profile_enable resets the totals; zeta_profile_read synchronises the
+ * recorded events and writes, for each stage i < nslots (see zeta_profile_stage_name), the
+ * summed device milliseconds, the number of kernels launched and the number of calls.  It
+ * returns the number of stages.  Launch and call counts are kept even when timing is off. */
+int zeta_profile_enable(zeta_ctx* ctx, int enable);
+int zeta_profile_read(zeta_ctx* ctx, double* ms, int64_t* launches, int64_t* calls, int nslots);
+const char* zeta_profile_stage_name(int stage);
+
 /* ---- host-only helpers (no device needed), for inspection and tests ---- */
 
 /* jbar_l(k; [r_lo, r_hi)) in float64 for k = 2 pi sqrt(n2[i]) / box, as used in the tables. */

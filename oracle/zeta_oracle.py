@@ -178,11 +178,12 @@ def _grid_integers(n: int):
     return nx, ny, nz
 
 
-def window_kernel(ell: int, m: int, n: int, box: float, edges):
+def window_kernel(ell: int, m: int, n: int, box: float, edges, bins=None):
     """K_lm,b(n) = sqrt(4 pi) i^l jbar_l(|k_n|; b) R_lm(k_n-hat), Nyquist planes zero.
 
     Eq. (3PCF-multipole-window) with the bin average of reading R4.
-    Returns complex array (nbins, n, n, n) over the full DFT grid [z, y, x].
+    Returns complex array (len(bins), n, n, n) over the full DFT grid [z, y, x];
+    bins defaults to every bin.
     """
     nx, ny, nz = _grid_integers(n)
     n2 = nx * nx + ny * ny + nz * nz
@@ -190,22 +191,22 @@ def window_kernel(ell: int, m: int, n: int, box: float, edges):
     kmag = 2.0 * math.pi / box * np.sqrt(uniq.astype(np.float64))
     ang = real_ylm(ell, m, nx, ny, nz)
     ny_mask = nyquist_mask(n)
-    nb = len(edges) - 1
-    out = np.empty((nb, n, n, n), np.complex128)
-    for b in range(nb):
+    bins = list(range(len(edges) - 1)) if bins is None else list(bins)
+    out = np.empty((len(bins), n, n, n), np.complex128)
+    for i, b in enumerate(bins):
         jb = jbar(ell, kmag, edges[b], edges[b + 1])[inv].reshape(n2.shape)
         kern = math.sqrt(FOUR_PI) * (1j ** ell) * jb * ang
         kern[ny_mask] = 0.0
-        out[b] = kern
+        out[i] = kern
     return out
 
 
-def multipole_fields(delta_hat, ell: int, m: int, n: int, box: float, edges):
+def multipole_fields(delta_hat, ell: int, m: int, n: int, box: float, edges, bins=None):
     """a_lm,b(l) = IDFT[delta_hat * K_lm,b], Eq. (SFC-3PCF-vertex), Fig. 1 step (5).
 
-    The fields are real (readings R1, R5); returns float64 (nbins, n, n, n).
+    The fields are real (readings R1, R5); returns float64 (len(bins), n, n, n).
     """
-    kern = window_kernel(ell, m, n, box, edges)
+    kern = window_kernel(ell, m, n, box, edges, bins)
     out = np.empty(kern.shape, np.float64)
     for b in range(kern.shape[0]):
         a = np.fft.ifftn(delta_hat * kern[b])

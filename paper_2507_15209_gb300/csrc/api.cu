@@ -146,6 +146,7 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
 
 int zeta_destroy(zeta_ctx* c) {
   if (!c) return ZETA_OK;
+  profile_release(c);
   cudaFree(c->d_jtab);
   cudaFree(c->d_tw);
   cudaFree(c->d_mhat);

@@ -235,6 +235,7 @@ inline int grid_for(long long work, int threads, int sms) {
 int launch_assign(const zeta_ctx* c, const float4* parts, int64_t np, float* delta, double* wsum,
                   unsigned long long* acc, double* scratch, cudaStream_t s) {
   // scratch: 2*kRedCtas partials then 3 values (W, sum|w|, scale)
+  StageScope prof(c, ST_ASSIGN, 4, s);
   double* wstat = scratch + 2 * kRedCtas;
   k_weight_partials<<<kRedCtas, 256, 0, s>>>(parts, np, scratch, c->d_status);
   k_weight_final<<<1, 32, 0, s>>>(scratch, kRedCtas, wstat, wsum);
@@ -250,6 +251,7 @@ int launch_assign(const zeta_ctx* c, const float4* parts, int64_t np, float* del
 }
 
 int launch_wsum(const zeta_ctx* c, const float4* parts, int64_t np, double* wsum, double* scratch, cudaStream_t s) {
+  StageScope prof(c, ST_ASSIGN, 2, s);
   double* wstat = scratch + 2 * kRedCtas;
   k_weight_partials<<<kRedCtas, 256, 0, s>>>(parts, np, scratch, c->d_status);
   k_weight_final<<<1, 32, 0, s>>>(scratch, kRedCtas, wstat, wsum);
@@ -258,6 +260,7 @@ int launch_wsum(const zeta_ctx* c, const float4* parts, int64_t np, double* wsum
 
 int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sorted, int64_t* tile_start,
                 int* counts, int* orig, cudaStream_t s) {
+  StageScope prof(c, ST_SORT, 4, s);
   const double inv_h = c->n / c->p.box;
   if (cudaMemsetAsync(counts, 0, sizeof(int) * c->ntiles, s) != cudaSuccess) return ZETA_ECUDA;
   const int g = grid_for(np, 256, c->num_sms);

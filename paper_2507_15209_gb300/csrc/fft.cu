@@ -237,6 +237,7 @@ template <int N>
 int r2c_impl(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t s) {
   constexpr int NC = N / 2;
   constexpr int T = kTy < NC ? kTy : NC;
+  StageScope prof(c, ST_R2C, 3, s);
   size_t smx = (N + NC + NC * (kRB + 1)) * sizeof(float2);
   if (set_smem(k_r2c_x<N, kRB>, smx)) return ZETA_ECUDA;
   k_r2c_x<N, kRB><<<N * N / kRB, 256, smx, s>>>(delta, dhat, c->d_tw);
@@ -253,10 +254,12 @@ int c2r_impl(const zeta_ctx* c, float2* data, int nf, cudaStream_t s, bool do_y)
   constexpr int T = kTy < NC ? kTy : NC;
   const long long fstride = static_cast<long long>(N) * N * NC;
   if (do_y) {
+    StageScope prof(c, ST_ALM_Y, 1, s);
     size_t sma = (N + N * T) * sizeof(float2);
     if (set_smem(k_fft_axis<N, T, true, 1>, sma)) return ZETA_ECUDA;
     k_fft_axis<N, T, true, 1><<<dim3(NC / T, N, nf), 256, sma, s>>>(data, fstride, c->d_tw);
   }
+  StageScope prof(c, ST_ALM_X, 1, s);
   size_t smx = (N + NC + NC * (kRB + 1)) * sizeof(float2);
   if (set_smem(k_c2r_x<N, kRB>, smx)) return ZETA_ECUDA;
   k_c2r_x<N, kRB><<<dim3(N * N / kRB, nf), 256, smx, s>>>(data, fstride, c->d_tw);
@@ -270,11 +273,14 @@ int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf
   const long long fstride = static_cast<long long>(N) * N * NC;
   size_t smz = N * sizeof(float2) + static_cast<size_t>(N) * T * (2 * sizeof(float2) + sizeof(float) + sizeof(int));
   if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
+  {
+  StageScope prof(c, ST_ALM_Z, 1, s);
   const float* jt = c->d_jtab + (static_cast<long long>(l) * c->p.nbins + b0) * c->nn2;
   float2* o = reinterpret_cast<float2*>(out);
   k_alm_z<N, T><<<dim3(NC / T, N), 256, smz, s>>>(dhat, o, fstride, nf, jt, c->nn2, l, m, c->d_tw);
   if (check_launch()) return ZETA_ECUDA;
-  return c2r_impl<N>(c, o, nf, s, true);
+  }
+  return c2r_impl<N>(c, reinterpret_cast<float2*>(out), nf, s, true);
 }
 
 // Full inverse of nf half spectra in place: z-, y- and x-passes.
@@ -285,6 +291,7 @@ int c2r_full(const zeta_ctx* c, float2* data, int nf, cudaStream_t s) {
   const long long fstride = static_cast<long long>(N) * N * NC;
   size_t sma = (N + N * T) * sizeof(float2);
   if (set_smem(k_fft_axis<N, T, true, 2>, sma)) return ZETA_ECUDA;
+  StageScope prof(c, ST_ALM_Z, 1, s);
   k_fft_axis<N, T, true, 2><<<dim3(NC / T, N, nf), 256, sma, s>>>(data, fstride, c->d_tw);
   if (check_launch()) return ZETA_ECUDA;
   return c2r_impl<N>(c, data, nf, s, true);

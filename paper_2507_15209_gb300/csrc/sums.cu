@@ -401,6 +401,7 @@ int prep(K kernel, size_t bytes) {
 
 template <int NBP>
 int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
+  StageScope prof(c, ST_GRAM_NODE, 1, s);
   const size_t sm = smem_node<NBP>();
   if (prep(k_gram_node<NBP>, sm)) return ZETA_ECUDA;
   k_gram_node<NBP><<<gram_ctas(c), kThreads, sm, s>>>(delta, alm, c->ng, c->p.nbins, partials);
@@ -410,6 +411,7 @@ int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* p
 template <int NBP, int D, int MODE>
 int points_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, const float* delta,
                 const float* alm, double* partials, cudaStream_t s) {
+  StageScope prof(c, MODE == 0 ? ST_GRAM_PART : ST_GRAM_GAMMA, 1, s);
   const size_t sm = smem_points<NBP, D>();
   if (prep(k_gram_points<NBP, D, MODE>, sm)) return ZETA_ECUDA;
   k_gram_points<NBP, D, MODE><<<gram_ctas(c), kThreads, sm, s>>>(
@@ -420,6 +422,7 @@ int points_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_sta
 
 template <int NBP>
 int mass_impl(const zeta_ctx* c, const float2* dhat, int l, double* partials, cudaStream_t s) {
+  StageScope prof(c, ST_MASS, 1, s);
   const size_t sm = smem_node<NBP>();
   if (prep(k_gram_mass<NBP>, sm)) return ZETA_ECUDA;
   const float* jt = c->d_jtab + static_cast<long long>(l) * c->p.nbins * c->nn2;
@@ -483,6 +486,7 @@ int launch_mass(const zeta_ctx* c, const float2* dhat, int l, double* partials, 
 
 int launch_reduce(const zeta_ctx* c, const double* partials, int nparts, double scale, const double* wdiv,
                   double* out, cudaStream_t s) {
+  StageScope prof(c, ST_REDUCE, 1, s);
   const int nb = c->p.nbins;
   k_reduce<<<1, 1024, 0, s>>>(partials, nparts, nb, scale, wdiv, out);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;

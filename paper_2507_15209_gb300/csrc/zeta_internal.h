@@ -37,6 +37,24 @@ void host_mass_hat(int n, int dsup, std::vector<float>& out);
 void host_cell_quadrature(int q, int dsup, std::vector<double>& t, std::vector<double>& wq,
                           std::vector<double>& beta);
 
+// ---- stage timers (profile.cu): CUDA events around every kernel group ----
+enum Stage {
+  ST_ASSIGN = 0, ST_SORT, ST_R2C, ST_ALM_Z, ST_ALM_Y, ST_ALM_X, ST_GRAM_NODE, ST_GRAM_GAMMA, ST_GRAM_PART,
+  ST_MASS, ST_REDUCE, ST_COUNT
+};
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    int stage, nk;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> pending;
+  double ms[ST_COUNT] = {};
+  long long launches[ST_COUNT] = {};
+  long long calls[ST_COUNT] = {};
+};
+
 }  // namespace zk
 
 struct zeta_ctx {
@@ -58,9 +76,26 @@ struct zeta_ctx {
   // workspace
   char* ws = nullptr;
   size_t ws_bytes = 0;
+  mutable zk::Profiler prof;
 };
 
 namespace zk {
+
+// Records an event pair around the kernels issued while it is alive (when profiling).
+class StageScope {
+ public:
+  StageScope(const zeta_ctx* c, int stage, int nkernels, cudaStream_t s);
+  ~StageScope();
+  StageScope(const StageScope&) = delete;
+  StageScope& operator=(const StageScope&) = delete;
+
+ private:
+  const zeta_ctx* c_;
+  int stage_, nk_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr;
+};
+void profile_release(const zeta_ctx* c);
 
 // ---- launchers (fft.cu) ----
 int set_ylm_constants();

@@ -42,7 +42,7 @@ def gaussian_field(n: int, seed: int, slope: float = -1.5) -> np.ndarray:
     amp[0, 0, 0] = 0.0
     wk *= amp
     del amp, k2
-    g = np.fft.irfftn(wk, s=(n, n, n))
+    g = np.fft.irfftn(wk, s=(n, n, n), axes=(0, 1, 2))
     del wk
     g -= g.mean()
     g /= g.std()

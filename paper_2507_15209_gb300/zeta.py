@@ -53,6 +53,9 @@ _SIGS = {
     "zeta_mass_term": ([_VP, _VP, _INT, _DBL, _VP, _VP], _INT),
     "zeta_zeta_ell": ([_VP, _VP, _I64, _VP, _INT, _VP, _VP], _INT),
     "zeta_get_status": ([_VP, _VP], _INT),
+    "zeta_profile_enable": ([_VP, _INT], _INT),
+    "zeta_profile_read": ([_VP, _VP, _VP, _VP, _INT], _INT),
+    "zeta_profile_stage_name": ([_INT], ctypes.c_char_p),
     "zeta_host_jbar": ([_INT, _DBL, _DBL, _DBL, _VP, _I64, _VP], _INT),
     "zeta_host_ylm": ([_INT, _INT, _DBL, _DBL, _DBL], _DBL),
 }
@@ -221,6 +224,19 @@ class Context:
         _check("zeta_zeta_ell", lib().zeta_zeta_ell(self._h, _ptr(particles), np_, _ptr(delta), bits, _ptr(out),
                                                     _stream()))
         return {f: out[i] for i, f in enumerate(order)}
+
+    def profile_enable(self, on: bool = True):
+        _check("zeta_profile_enable", lib().zeta_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        """{stage: (milliseconds, kernel launches, calls)} since the last profile_enable."""
+        ms = np.zeros(32, np.float64)
+        nl = np.zeros(32, np.int64)
+        nc = np.zeros(32, np.int64)
+        k = lib().zeta_profile_read(self._h, ms.ctypes.data, nl.ctypes.data, nc.ctypes.data, 32)
+        if k < 0:
+            raise ZetaError("zeta_profile_read", k)
+        return {lib().zeta_profile_stage_name(i).decode(): (float(ms[i]), int(nl[i]), int(nc[i])) for i in range(k)}
 
     def get_status(self) -> int:
         return lib().zeta_get_status(self._h, _stream())
