@@ -338,11 +338,14 @@ def main():
     ap.add_argument("--workload", default="box2000_n512_np16m")
     ap.add_argument("--forms", default="particle,node")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lmax", type=int, default=None, help="override lmax (small profiling runs only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.lmax is not None:
+        w["lmax"] = args.lmax
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
     return run_ours(args, w, rank, world, local_rank)

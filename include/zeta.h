@@ -24,7 +24,9 @@
  *     with nx in [0, n/2): the x-Nyquist column is not stored, because every kernel of the
  *     method is zero on all Nyquist planes.  Its size is n^3/2 complex = n^3 floats.
  *     Forward DFT unnormalised, e^{-2 pi i n.l / n}; wavevector k = 2 pi n / box.
- *   - A field a_lm(x; b) is a float32 grid; a stack of fields is [field][z][y][x].
+ *   - A field a_lm(x; b) is a float32 grid.  A stack of fields is bin-interleaved in groups of
+ *     four: [group][z][y][x][4] with bin b in group b/4, lane b%4, the last group zero-padded,
+ *     so a stack of nb fields holds 4*ceil(nb/4) * n^3 floats.
  *   - Real spherical harmonics without the Condon-Shortley phase:
  *     R_l0 = Y_l^0, R_lm = sqrt2 N_lm P_l^m(cos t) cos(m p) (m > 0), sin(|m| p) (m < 0).
  *   - Bins are [edges[b], edges[b+1]); the radial window of bin b is the r^2-weighted shell
@@ -132,7 +134,9 @@ int zeta_fft_r2c(zeta_ctx* ctx, const float* delta, float* delta_hat, zeta_strea
 
 /* Steps (3)-(5): for bins b0 <= b < b1, a_lm(.; b) = IDFT[delta_hat * K_lm,b] with
  * K_lm,b(k) = sqrt(4 pi) i^l jbar_l(|k|; b) R_lm(k-hat), zero on every Nyquist plane and
- * IDFT normalised by 1/N_g.  alm: device float[(b1-b0) * n^3] (output).  No workspace. */
+ * IDFT normalised by 1/N_g.  b0 must be a multiple of 4.  alm: device float
+ * [4*ceil((b1-b0)/4) * n^3] (output, bin-interleaved stack, bin b0 in lane 0 of group 0).
+ * Uses the workspace for the intermediate half spectra. */
 int zeta_reconstruct_alm(zeta_ctx* ctx, const float* delta_hat, int l, int m, int b0, int b1,
                          float* alm, zeta_stream stream);
 
@@ -140,7 +144,8 @@ int zeta_reconstruct_alm(zeta_ctx* ctx, const float* delta_hat, int l, int m, in
  *   form = ZETA_SUM_NODE:  S = (1/N_g) sum_l delta_l a_b1(l) a_b2(l)
  *   form = ZETA_SUM_GAMMA: S = (1/N_g) sum_l delta_l sum_{l1,l2} Gamma_{l1,l2} a_b1(l+l1) a_b2(l+l2)
  *                          (evaluated as the exact cell quadrature of (1/V) int n_rec f1 f2).
- * delta: device float[n^3]; alm: device float[nbins * n^3]; gram: device double[nbins^2]. */
+ * delta: device float[n^3]; alm: bin-interleaved stack of all nbins fields; gram: device
+ * double[nbins^2]. */
 int zeta_sum_grid(zeta_ctx* ctx, const float* delta, const float* alm, int form, double* gram,
                   zeta_stream stream);
 

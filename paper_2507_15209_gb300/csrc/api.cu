@@ -14,7 +14,8 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t delta = 0, dhat = 0, fields = 0, partials = 0, small = 0, sorted = 0, tstart = 0, counts = 0, orig = 0;
+  size_t delta = 0, dhat = 0, spectra = 0, fields = 0, partials = 0, small = 0, sorted = 0, tstart = 0, counts = 0,
+         orig = 0;
   size_t total = 0;
 };
 
@@ -30,8 +31,8 @@ Layout layout(const zeta_ctx* c, int64_t np) {
   const size_t g = static_cast<size_t>(c->ng) * sizeof(float);
   L.delta = take(g);
   L.dhat = take(g);
-  const int nf = c->p.nbins < 2 ? 2 : c->p.nbins;  // fields region doubles as the 64-bit assign accumulator
-  L.fields = take(g * nf);
+  L.spectra = take(g * c->p.nbins);                    // plain half spectra of the C2R passes
+  L.fields = take(g * 4 * ((c->p.nbins + 3) / 4));     // bin-interleaved fields; also the assign accumulator
   L.partials = take(sizeof(double) * kMaxCtas * c->p.nbins * c->p.nbins);
   L.small = take(sizeof(double) * (kAssignScratchDoubles + 8));
   L.sorted = take(sizeof(float4) * static_cast<size_t>(np));
@@ -191,9 +192,13 @@ int zeta_fft_r2c(zeta_ctx* c, const float* delta, float* delta_hat, zeta_stream 
 int zeta_reconstruct_alm(zeta_ctx* c, const float* delta_hat, int l, int m, int b0, int b1, float* alm,
                          zeta_stream stream) {
   ZK_TRY(check_ctx(c));
-  if (!delta_hat || !alm || l < 0 || l > c->p.lmax || m < -l || m > l || b0 < 0 || b1 <= b0 || b1 > c->p.nbins)
+  if (!delta_hat || !alm || l < 0 || l > c->p.lmax || m < -l || m > l || b0 < 0 || (b0 & 3) || b1 <= b0 ||
+      b1 > c->p.nbins)
     return ZETA_EINVAL;
-  return launch_alm(c, reinterpret_cast<const float2*>(delta_hat), l, m, b0, b1 - b0, alm, stream);
+  ZK_TRY(need_ws(c, 0));
+  const Layout L = layout(c, 0);
+  return launch_alm(c, reinterpret_cast<const float2*>(delta_hat), l, m, b0, b1 - b0, at<float2>(c, L.spectra), alm,
+                    stream);
 }
 
 int zeta_sum_grid(zeta_ctx* c, const float* delta, const float* alm, int form, double* gram, zeta_stream stream) {
@@ -286,7 +291,7 @@ int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* 
       ZK_TRY(launch_reduce(c, part, nparts, -(2.0 * l + 1.0) / (4.0 * 3.14159265358979323846), nullptr, out, stream));
     }
     for (int m = -l; m <= l; ++m) {
-      ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, fields, stream));
+      ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, at<float2>(c, L.spectra), fields, stream));
       if (idx_node >= 0) {
         ZK_TRY(launch_gram_node(c, dl, fields, part, stream));
         ZK_TRY(launch_reduce(c, part, nparts, inv_ng, nullptr, zeta + idx_node * per_form + static_cast<size_t>(l) * nb * nb, stream));

@@ -6,9 +6,9 @@
 // Inverse (per (l, m) and radial bin; the hot loop):  z-pass that reads delta_hat once
 //   per CTA tile and, for every bin of the launch, multiplies by the multipole window
 //   K_lm,b(n) = i^l [sqrt(4 pi) jbar_l(|k|; b) / N_g] R_lm(n-hat) (Eqs. 3PCF-multipole-window
-//   and SFC-3PCF-vertex) before transforming -> y-pass -> x-pass C2R, in place in the
-//   caller's field buffer: each half spectrum (n^3/2 complex) occupies exactly the bytes of
-//   its real field (n^3 floats).
+//   and SFC-3PCF-vertex) before transforming -> y-pass in place -> x-pass C2R of four
+//   fields at a time, written bin-interleaved ([group][z][y][x][4]) so that every
+//   consumer reads four bins of a point with one 16-byte load.
 //
 // Every pass moves a tile of T contiguous complex columns (or RB rows) between HBM and
 // shared memory with coalesced accesses and transforms it with the radix-8 shared-memory
@@ -159,6 +159,52 @@ __global__ void __launch_bounds__(256) k_c2r_x(float2* __restrict__ data, long l
   }
 }
 
+// x-pass of the field reconstruction: C2R of the rows of four fields at once, written as
+// one bin-interleaved group [z][y][x][4] (lane j = field 4g + j; missing fields give 0).
+// grid (n*n/RB, ngroups); spec holds nf plain half spectra, fstride complex apart.
+template <int N, int RB>
+__global__ void __launch_bounds__(256) k_c2r_x4(const float2* __restrict__ spec, long long fstride, int nf,
+                                                float4* __restrict__ out, const float2* __restrict__ twg) {
+  constexpr int NC = N / 2, C = 4 * RB, PS = C + 1;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* tw2 = sm + N;
+  float2* buf = tw2 + NC;  // [NC][PS], column c = j * RB + r
+  const int g = blockIdx.y;
+  const long long r0 = static_cast<long long>(blockIdx.x) * RB;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < NC; i += blockDim.x) tw2[i] = twg[2 * i];
+  for (int idx = threadIdx.x; idx < NC * C; idx += blockDim.x) {
+    const int c = idx / NC, k = idx % NC;
+    const int f = 4 * g + c / RB, r = c % RB;
+    buf[k * PS + c] = (f < nf) ? spec[f * fstride + (r0 + r) * NC + k] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  constexpr int NP = NC / 2 + 1;
+  for (int idx = threadIdx.x; idx < NP * C; idx += blockDim.x) {
+    const int c = idx / NP, k = idx % NP;
+    const int kp = NC - k;
+    const float2 xk = buf[k * PS + c];
+    const float2 xp = (k == 0) ? make_float2(0.f, 0.f) : buf[kp * PS + c];
+    const float2 wk = cconj(tw[k]);
+    const float2 zk = cadd(cadd(xk, cconj(xp)), mul_i(cmul(wk, csub(xk, cconj(xp)))));
+    if (k != 0 && kp != k) {
+      const float2 wp = cconj(tw[kp]);
+      buf[kp * PS + c] = cadd(cadd(xp, cconj(xk)), mul_i(cmul(wp, csub(xp, cconj(xk)))));
+    }
+    buf[k * PS + c] = zk;
+  }
+  fft_smem<NC, true>(buf, PS, C, tw2);
+  for (int idx = threadIdx.x; idx < NC * RB; idx += blockDim.x) {
+    const int r = idx / NC, j = idx % NC;
+    const float2* src = buf + fft_pos_of<NC>(j) * PS + r;
+    const float2 z0 = src[0], z1 = src[RB], z2 = src[2 * RB], z3 = src[3 * RB];
+    float4* o = out + (static_cast<long long>(g) * N * N + r0 + r) * N + 2 * j;
+    o[0] = make_float4(z0.x, z1.x, z2.x, z3.x);
+    o[1] = make_float4(z0.y, z1.y, z2.y, z3.y);
+  }
+}
+
 // z-pass of the field reconstruction with the multipole window fused in.
 // grid (nc/T, n); each CTA keeps its delta_hat tile [z][T] in shared memory and emits
 // one transformed tile per field f < nf into out + f * fstride.
@@ -220,6 +266,7 @@ namespace {
 constexpr int kTz = 8;   // columns per z-pass (window) tile
 constexpr int kTy = 16;  // columns per plain pencil tile
 constexpr int kRB = 8;   // rows per x-pass tile
+constexpr int kRB4 = 4;  // rows per four-field x-pass tile
 
 template <typename K>
 int set_smem(K kernel, size_t bytes) {
@@ -267,20 +314,35 @@ int c2r_impl(const zeta_ctx* c, float2* data, int nf, cudaStream_t s, bool do_y)
 }
 
 template <int N>
-int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float* out, cudaStream_t s) {
+int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
+             cudaStream_t s) {
   constexpr int NC = N / 2;
   constexpr int T = kTz < NC ? kTz : NC;
+  constexpr int TY = kTy < NC ? kTy : NC;
   const long long fstride = static_cast<long long>(N) * N * NC;
-  size_t smz = N * sizeof(float2) + static_cast<size_t>(N) * T * (2 * sizeof(float2) + sizeof(float) + sizeof(int));
-  if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
   {
-  StageScope prof(c, ST_ALM_Z, 1, s);
-  const float* jt = c->d_jtab + (static_cast<long long>(l) * c->p.nbins + b0) * c->nn2;
-  float2* o = reinterpret_cast<float2*>(out);
-  k_alm_z<N, T><<<dim3(NC / T, N), 256, smz, s>>>(dhat, o, fstride, nf, jt, c->nn2, l, m, c->d_tw);
-  if (check_launch()) return ZETA_ECUDA;
+    StageScope prof(c, ST_ALM_Z, 1, s);
+    size_t smz = N * sizeof(float2) + static_cast<size_t>(N) * T * (2 * sizeof(float2) + sizeof(float) + sizeof(int));
+    if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
+    const float* jt = c->d_jtab + (static_cast<long long>(l) * c->p.nbins + b0) * c->nn2;
+    k_alm_z<N, T><<<dim3(NC / T, N), 256, smz, s>>>(dhat, spec, fstride, nf, jt, c->nn2, l, m, c->d_tw);
+    if (check_launch()) return ZETA_ECUDA;
   }
-  return c2r_impl<N>(c, reinterpret_cast<float2*>(out), nf, s, true);
+  {
+    StageScope prof(c, ST_ALM_Y, 1, s);
+    size_t sma = (N + N * TY) * sizeof(float2);
+    if (set_smem(k_fft_axis<N, TY, true, 1>, sma)) return ZETA_ECUDA;
+    k_fft_axis<N, TY, true, 1><<<dim3(NC / TY, N, nf), 256, sma, s>>>(spec, fstride, c->d_tw);
+    if (check_launch()) return ZETA_ECUDA;
+  }
+  StageScope prof(c, ST_ALM_X, 1, s);
+  constexpr int RB = kRB4;
+  size_t smx = (N + NC + NC * (4 * RB + 1)) * sizeof(float2);
+  if (set_smem(k_c2r_x4<N, RB>, smx)) return ZETA_ECUDA;
+  const int ng4 = (nf + 3) / 4;
+  k_c2r_x4<N, RB><<<dim3(N * N / RB, ng4), 256, smx, s>>>(spec, fstride, nf, reinterpret_cast<float4*>(out),
+                                                          c->d_tw);
+  return check_launch();
 }
 
 // Full inverse of nf half spectra in place: z-, y- and x-passes.
@@ -316,8 +378,9 @@ int launch_r2c(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t
 #undef ZK_CALL
 }
 
-int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float* out, cudaStream_t s) {
-#define ZK_CALL(NN) alm_impl<NN>(c, dhat, l, m, b0, nf, out, s)
+int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
+               cudaStream_t s) {
+#define ZK_CALL(NN) alm_impl<NN>(c, dhat, l, m, b0, nf, spec, out, s)
   ZK_DISPATCH_N(c->n, ZK_CALL)
 #undef ZK_CALL
 }

@@ -11,7 +11,7 @@
 //   mass term      points = half-spectrum modes, v = jbar_b(|k|), w = |delta_hat|^2 Mhat(k)
 // A CTA stages a batch of points' weights and values in shared memory; each thread owns a
 // 4x4 block of the upper triangle of the bin Gram and a slice of the batch, accumulating in
-// float32 and flushing to float64 every 16 points.  Partials per CTA are reduced in a fixed
+// float32 and flushing to float64 every kFlush points.  Partials per CTA are reduced in a fixed
 // order by k_reduce, so results are bit-reproducible.
 #include "fft.cuh"
 #include "zeta_internal.h"
@@ -21,6 +21,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPB = 256;  // points per batch (one per thread in the interpolation phase)
+// float32 partial sums are moved into float64 every kFlush points per thread (float64
+// arithmetic is a small fraction of float32 throughput on this part, so flushes are rare)
+constexpr int kFlush = 128;
 
 template <int NBP>
 struct Gram {
@@ -77,7 +80,7 @@ struct GramAcc {
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xs[i], ys[j], acc[i][j]);
-      if (++pending == 16) flush();
+      if (++pending == kFlush) flush();
     }
   }
 };
@@ -113,38 +116,54 @@ __device__ void cta_store(GramAcc<NBP>& g, double* red, int nb, double* part) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Node form: persistent CTAs over chunks of kPB grid points.
+// Node form: persistent CTAs over chunks of kPB grid points of the bin-interleaved fields;
+// the next chunk is loaded into registers while the current one is contracted.
 template <int NBP>
-__global__ void __launch_bounds__(kThreads) k_gram_node(const float* __restrict__ delta, const float* __restrict__ alm,
+__global__ void __launch_bounds__(kThreads) k_gram_node(const float* __restrict__ delta, const float4* __restrict__ f4,
                                                         long long ng, int nb, double* __restrict__ partials) {
   using G = Gram<NBP>;
+  constexpr int GMAX = NBP / 4;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* vals = reinterpret_cast<float*>(smraw);
   float* wts = vals + kPB * G::NBS;
-  double* red = reinterpret_cast<double*>(wts + kPB);
+  double* red = reinterpret_cast<double*>(smraw);  // reused after the main loop
   const int pr = threadIdx.x % G::NPAIR, grp = threadIdx.x / G::NPAIR;
   int b1 = 0, b2 = 0;
   pair_blocks(pr, G::NBLK, b1, b2);
+  const int ngrp = (nb + 3) / 4;
   GramAcc<NBP> g;
   g.init();
   const long long nchunk = ng / kPB;
-  for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-    const long long p0 = ch * kPB;
+  float dnext = 0.f;
+  float4 vnext[GMAX];
+  long long ch = blockIdx.x;
+  auto fetch = [&](long long c) {
+    const long long p = c * kPB + threadIdx.x;
+    dnext = __ldg(delta + p);
+#pragma unroll
+    for (int q = 0; q < GMAX; ++q)
+      vnext[q] = (q < ngrp) ? __ldg(f4 + q * ng + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  if (ch < nchunk) fetch(ch);
+  for (; ch < nchunk; ch += gridDim.x) {
     __syncthreads();
-    wts[threadIdx.x] = delta[p0 + threadIdx.x];
-    for (int b = 0; b < NBP; ++b) vals[threadIdx.x * G::NBS + b] = (b < nb) ? alm[b * ng + p0 + threadIdx.x] : 0.f;
+    wts[threadIdx.x] = dnext;
+#pragma unroll
+    for (int q = 0; q < GMAX; ++q) *reinterpret_cast<float4*>(vals + threadIdx.x * G::NBS + 4 * q) = vnext[q];
     __syncthreads();
+    if (ch + gridDim.x < nchunk) fetch(ch + gridDim.x);
     if (grp < G::NGRP) g.add(vals, wts, kPB, b1, b2, grp);
   }
+  __syncthreads();
   cta_store<NBP>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb);
 }
 
 // ---------------------------------------------------------------------------------------
-// Particle and Gamma forms: persistent CTAs over 8x8x8-cell tiles; per tile the fields'
-// halo block (tile + stencil reach) is staged in shared memory, kBC bins at a time, laid
-// out [z][y][x][bin] so each stencil point is read as float4s.
-constexpr int kBC = 8;
-
+// Particle and Gamma forms: persistent CTAs over 8x8x8-cell tiles, kPB points per batch.
+// Phase 1 puts each point's stencil origin and B-spline weights in shared memory; phase 2
+// spreads (point, bin group) tasks over the CTA, each gathering its D^3 stencil of float4
+// bin groups straight from the L1-cached fields (the tile's halo stays resident in L1);
+// phase 3 contracts the batch.
 template <int D>
 __device__ __forceinline__ void bsw(float t, float* w) {
   if (D == 2) {
@@ -159,82 +178,34 @@ __device__ __forceinline__ void bsw(float t, float* w) {
   }
 }
 
-// Load fields [b0, b0+cnt) of the halo block starting at cell (x0, y0, z0) (periodic).
-template <int HS>
-__device__ __forceinline__ void load_halo(float* halo, const float* __restrict__ f, long long ng, int n, int x0, int y0,
-                                          int z0, int b0, int cnt) {
-  constexpr int H3 = HS * HS * HS;
-  for (int idx = threadIdx.x; idx < H3 * kBC; idx += blockDim.x) {
-    const int b = idx / H3, r = idx % H3;
-    const int hx = r % HS, hy = (r / HS) % HS, hz = r / (HS * HS);
-    float v = 0.f;
-    if (b < cnt) {
-      const int gx = (x0 + hx) & (n - 1), gy = (y0 + hy) & (n - 1), gz = (z0 + hz) & (n - 1);
-      v = f[(b0 + b) * ng + (static_cast<long long>(gz) * n + gy) * n + gx];
-    }
-    halo[r * kBC + b] = v;
-  }
-}
-
-// Interpolate kBC fields at one point from the halo (local stencil origin lx, ly, lz).
-template <int D, int HS>
-__device__ __forceinline__ void interp_point(const float* halo, int lx, int ly, int lz, const float* wx,
-                                             const float* wy, const float* wz, float* out) {
-  float a[kBC];
-#pragma unroll
-  for (int b = 0; b < kBC; ++b) a[b] = 0.f;
-#pragma unroll
-  for (int oz = 0; oz < D; ++oz) {
-#pragma unroll
-    for (int oy = 0; oy < D; ++oy) {
-      const float wyz = wz[oz] * wy[oy];
-      const float* row = halo + (((lz + oz) * HS + ly + oy) * HS + lx) * kBC;
-#pragma unroll
-      for (int ox = 0; ox < D; ++ox) {
-        const float w = wyz * wx[ox];
-        const float4 v0 = *reinterpret_cast<const float4*>(row + ox * kBC);
-        const float4 v1 = *reinterpret_cast<const float4*>(row + ox * kBC + 4);
-        a[0] = fmaf(w, v0.x, a[0]);
-        a[1] = fmaf(w, v0.y, a[1]);
-        a[2] = fmaf(w, v0.z, a[2]);
-        a[3] = fmaf(w, v0.w, a[3]);
-        a[4] = fmaf(w, v1.x, a[4]);
-        a[5] = fmaf(w, v1.y, a[5]);
-        a[6] = fmaf(w, v1.z, a[6]);
-        a[7] = fmaf(w, v1.w, a[7]);
-      }
-    }
-  }
-#pragma unroll
-  for (int b = 0; b < kBC; ++b) out[b] = a[b];
-}
-
 // MODE 0: particles (sorted, tile_start).  MODE 1: Gamma-form cell quadrature.
 template <int NBP, int D, int MODE>
 __global__ void __launch_bounds__(kThreads)
     k_gram_points(const float4* __restrict__ sorted, const long long* __restrict__ tile_start,
-                  const float* __restrict__ delta, const float* __restrict__ alm, long long ng, int n, int nb,
+                  const float* __restrict__ delta, const float4* __restrict__ f4, long long ng, int n, int nb,
                   double inv_h, const float* __restrict__ gq, int q, double* __restrict__ partials) {
   using G = Gram<NBP>;
-  constexpr int HS = kTile + D - 1;
-  constexpr int H3 = HS * HS * HS;
+  constexpr int GMAX = NBP / 4;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float* halo = reinterpret_cast<float*>(smraw);            // [H3][kBC]
-  float* vals = halo + H3 * kBC;                             // [kPB][NBS]
-  float* wts = vals + kPB * G::NBS;                          // [kPB]
-  double* red = reinterpret_cast<double*>(wts + kPB);        // NGRP*NPAIR*16
+  float* vals = reinterpret_cast<float*>(smraw);    // [kPB][NBS]
+  float* wts = vals + kPB * G::NBS;                  // [kPB]
+  int4* org = reinterpret_cast<int4*>(wts + kPB);    // [kPB] stencil origin (unwrapped cells)
+  float* bw = reinterpret_cast<float*>(org + kPB);   // [kPB][3*D] weights x, y, z
+  double* red = reinterpret_cast<double*>(smraw);    // reused after the main loop
   const int pr = threadIdx.x % G::NPAIR, grp = threadIdx.x / G::NPAIR;
   int b1 = 0, b2 = 0;
   pair_blocks(pr, G::NBLK, b1, b2);
   GramAcc<NBP> g;
   g.init();
+  const int ngrp = (nb + 3) / 4;
   const int nt = n / kTile;
   const long long ntiles = static_cast<long long>(nt) * nt * nt;
   constexpr int OFF = D / 2 - 1;
   const int q3 = q * q * q;
+  const int mask = n - 1;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int tx = static_cast<int>(t % nt), ty = static_cast<int>((t / nt) % nt), tz = static_cast<int>(t / (static_cast<long long>(nt) * nt));
-    const int x0 = tx * kTile - OFF, y0 = ty * kTile - OFF, z0 = tz * kTile - OFF;
+    const int tx = static_cast<int>(t % nt), ty = static_cast<int>((t / nt) % nt),
+              tz = static_cast<int>(t / (static_cast<long long>(nt) * nt));
     long long s0, s1;
     if (MODE == 0) {
       s0 = tile_start[t];
@@ -243,88 +214,110 @@ __global__ void __launch_bounds__(kThreads)
       s0 = 0;
       s1 = static_cast<long long>(kTile * kTile * kTile) * q3;
     }
-    if (s1 == s0) continue;
     for (long long bs = s0; bs < s1; bs += kPB) {
       const int cnt = static_cast<int>((s1 - bs) < kPB ? (s1 - bs) : kPB);
-      // this thread's point: local stencil origin and weights
+      __syncthreads();
+      // phase 1: per point
       const int me = threadIdx.x;
-      int lx = 0, ly = 0, lz = 0;
-      float wx[D], wy[D], wz[D];
-      float pw = 0.f;
       if (me < cnt) {
+        float wx[D], wy[D], wz[D];
+        int cx, cy, cz;
+        float pw;
         if (MODE == 0) {
           const float4 pp = sorted[bs + me];
-          double u[3] = {static_cast<double>(pp.x) * inv_h, static_cast<double>(pp.y) * inv_h,
-                         static_cast<double>(pp.z) * inv_h};
+          const double u[3] = {static_cast<double>(pp.x) * inv_h, static_cast<double>(pp.y) * inv_h,
+                               static_cast<double>(pp.z) * inv_h};
           int ci[3];
           float tt[3];
+#pragma unroll
           for (int d = 0; d < 3; ++d) {
-            double v = u[d] - floor(u[d] / n) * n;
+            const double v = u[d] - floor(u[d] / n) * n;
             int c = static_cast<int>(floor(v));
-            double fr = v - c;
+            const double fr = v - c;
             if (c >= n) c -= n;
             ci[d] = c;
             tt[d] = static_cast<float>(fr);
             if (tt[d] >= 1.f) tt[d] = 0.99999994f;
           }
-          lx = ci[0] - tx * kTile;
-          ly = ci[1] - ty * kTile;
-          lz = ci[2] - tz * kTile;
+          cx = ci[0];
+          cy = ci[1];
+          cz = ci[2];
           bsw<D>(tt[0], wx);
           bsw<D>(tt[1], wy);
           bsw<D>(tt[2], wz);
-          pw = isfinite(pp.w) ? pp.w : 0.f;
-          if (lx < 0 || lx >= kTile || ly < 0 || ly >= kTile || lz < 0 || lz >= kTile) {  // not of this tile
-            lx = ly = lz = 0;
-            pw = 0.f;
-          }
+          pw = (isfinite(pp.x) && isfinite(pp.y) && isfinite(pp.z) && isfinite(pp.w)) ? pp.w : 0.f;
         } else {
           const long long id = bs + me;
           const int cell = static_cast<int>(id / q3), qq = static_cast<int>(id % q3);
-          lx = cell % kTile;
-          ly = (cell / kTile) % kTile;
-          lz = cell / (kTile * kTile);
+          cx = tx * kTile + cell % kTile;
+          cy = ty * kTile + (cell / kTile) % kTile;
+          cz = tz * kTile + cell / (kTile * kTile);
           const int qx = qq % q, qy = (qq / q) % q, qz = qq / (q * q);
           const float* beta = gq + q;
+#pragma unroll
           for (int o = 0; o < D; ++o) {
             wx[o] = beta[qx * D + o];
             wy[o] = beta[qy * D + o];
             wz[o] = beta[qz * D + o];
           }
-          pw = gq[qx] * gq[qy] * gq[qz];
-        }
-      }
-      if (MODE == 1) {  // weight includes n_rec(node) = interpolated delta
-        __syncthreads();
-        load_halo<HS>(halo, delta, ng, n, x0, y0, z0, 0, 1);
-        __syncthreads();
-        if (me < cnt) {
-          float tmp[kBC];
-          interp_point<D, HS>(halo, lx, ly, lz, wx, wy, wz, tmp);
-          pw *= tmp[0];
-        }
-      }
-      for (int bc = 0; bc < nb; bc += kBC) {
-        __syncthreads();
-        load_halo<HS>(halo, alm, ng, n, x0, y0, z0, bc, (nb - bc) < kBC ? (nb - bc) : kBC);
-        __syncthreads();
-        if (me < cnt) {
-          float tmp[kBC];
-          interp_point<D, HS>(halo, lx, ly, lz, wx, wy, wz, tmp);
+          // n_rec at the node: the B-spline expansion of delta
+          float nr = 0.f;
 #pragma unroll
-          for (int b = 0; b < kBC; ++b)
-            if (bc + b < NBP) vals[me * G::NBS + bc + b] = tmp[b];
+          for (int oz = 0; oz < D; ++oz)
+#pragma unroll
+            for (int oy = 0; oy < D; ++oy) {
+              const long long row = (static_cast<long long>((cz - OFF + oz) & mask) * n + ((cy - OFF + oy) & mask)) * n;
+              float a = 0.f;
+#pragma unroll
+              for (int ox = 0; ox < D; ++ox) a = fmaf(wx[ox], __ldg(delta + row + ((cx - OFF + ox) & mask)), a);
+              nr = fmaf(wz[oz] * wy[oy], a, nr);
+            }
+          pw = gq[qx] * gq[qy] * gq[qz] * nr;
         }
+        org[me] = make_int4(cx - OFF, cy - OFF, cz - OFF, 0);
+#pragma unroll
+        for (int o = 0; o < D; ++o) {
+          bw[me * 3 * D + o] = wx[o];
+          bw[me * 3 * D + D + o] = wy[o];
+          bw[me * 3 * D + 2 * D + o] = wz[o];
+        }
+        wts[me] = pw;
+#pragma unroll
+        for (int b = 4 * ngrp; b < NBP; ++b) vals[me * G::NBS + b] = 0.f;
       }
       __syncthreads();
-      if (me < cnt) {
-        wts[me] = pw;
-        for (int b = nb; b < NBP; ++b) vals[me * G::NBS + b] = 0.f;
+      // phase 2: (point, group) gathers
+      for (int task = threadIdx.x; task < cnt * ngrp; task += blockDim.x) {
+        const int p = task % cnt, q4 = task / cnt;
+        const int4 o = org[p];
+        const float* w = bw + p * 3 * D;
+        const float4* base = f4 + q4 * ng;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int oz = 0; oz < D; ++oz) {
+          const long long zrow = static_cast<long long>((o.z + oz) & mask) * n;
+#pragma unroll
+          for (int oy = 0; oy < D; ++oy) {
+            const float wyz = w[2 * D + oz] * w[D + oy];
+            const float4* row = base + (zrow + ((o.y + oy) & mask)) * n;
+#pragma unroll
+            for (int ox = 0; ox < D; ++ox) {
+              const float ww = wyz * w[ox];
+              const float4 v = __ldg(row + ((o.x + ox) & mask));
+              acc.x = fmaf(ww, v.x, acc.x);
+              acc.y = fmaf(ww, v.y, acc.y);
+              acc.z = fmaf(ww, v.z, acc.z);
+              acc.w = fmaf(ww, v.w, acc.w);
+            }
+          }
+        }
+        *reinterpret_cast<float4*>(vals + p * G::NBS + 4 * q4) = acc;
       }
       __syncthreads();
       if (grp < G::NGRP) g.add(vals, wts, cnt, b1, b2, grp);
     }
   }
+  __syncthreads();
   cta_store<NBP>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb);
 }
 
@@ -381,15 +374,26 @@ __global__ void k_reduce(const double* __restrict__ part, int nparts, int nb, do
 }
 
 template <int NBP>
+size_t red_bytes() {
+  using G = Gram<NBP>;
+  return G::NGRP * G::NPAIR * 16 * sizeof(double);
+}
+template <int NBP>
 size_t smem_node() {
   using G = Gram<NBP>;
-  return (kPB * G::NBS + kPB) * sizeof(float) + G::NGRP * G::NPAIR * 16 * sizeof(double);
+  const size_t main = (kPB * G::NBS + kPB) * sizeof(float);
+  return main > red_bytes<NBP>() ? main : red_bytes<NBP>();
+}
+template <int NBP>
+size_t smem_mass() {
+  using G = Gram<NBP>;
+  return (kPB * G::NBS + kPB) * sizeof(float) + red_bytes<NBP>();
 }
 template <int NBP, int D>
 size_t smem_points() {
   using G = Gram<NBP>;
-  constexpr int HS = kTile + D - 1;
-  return (HS * HS * HS * kBC + kPB * G::NBS + kPB) * sizeof(float) + G::NGRP * G::NPAIR * 16 * sizeof(double);
+  const size_t main = (kPB * G::NBS + kPB) * sizeof(float) + kPB * sizeof(int4) + kPB * 3 * D * sizeof(float);
+  return main > red_bytes<NBP>() ? main : red_bytes<NBP>();
 }
 
 template <typename K>
@@ -404,7 +408,8 @@ int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* p
   StageScope prof(c, ST_GRAM_NODE, 1, s);
   const size_t sm = smem_node<NBP>();
   if (prep(k_gram_node<NBP>, sm)) return ZETA_ECUDA;
-  k_gram_node<NBP><<<gram_ctas(c), kThreads, sm, s>>>(delta, alm, c->ng, c->p.nbins, partials);
+  k_gram_node<NBP><<<gram_ctas(c), kThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
+                                                     c->p.nbins, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
@@ -415,7 +420,8 @@ int points_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_sta
   const size_t sm = smem_points<NBP, D>();
   if (prep(k_gram_points<NBP, D, MODE>, sm)) return ZETA_ECUDA;
   k_gram_points<NBP, D, MODE><<<gram_ctas(c), kThreads, sm, s>>>(
-      sorted, reinterpret_cast<const long long*>(tile_start), delta, alm, c->ng, c->n, c->p.nbins, c->n / c->p.box,
+      sorted, reinterpret_cast<const long long*>(tile_start), delta, reinterpret_cast<const float4*>(alm), c->ng,
+      c->n, c->p.nbins, c->n / c->p.box,
       c->d_gq, c->gamma_q, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
@@ -423,7 +429,7 @@ int points_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_sta
 template <int NBP>
 int mass_impl(const zeta_ctx* c, const float2* dhat, int l, double* partials, cudaStream_t s) {
   StageScope prof(c, ST_MASS, 1, s);
-  const size_t sm = smem_node<NBP>();
+  const size_t sm = smem_mass<NBP>();
   if (prep(k_gram_mass<NBP>, sm)) return ZETA_ECUDA;
   const float* jt = c->d_jtab + static_cast<long long>(l) * c->p.nbins * c->nn2;
   k_gram_mass<NBP><<<gram_ctas(c), kThreads, sm, s>>>(dhat, jt, c->nn2, c->d_mhat, c->n, c->p.nbins, partials);
@@ -435,7 +441,7 @@ inline int nbp_of(int nb) { return nb <= 8 ? 8 : nb <= 16 ? 16 : nb <= 24 ? 24 :
 }  // namespace
 
 int gram_ctas(const zeta_ctx* c) {
-  int g = c->num_sms * 2;
+  int g = c->num_sms * 4;
   return g > kMaxCtas ? kMaxCtas : g;
 }
 

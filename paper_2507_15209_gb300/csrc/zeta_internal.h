@@ -100,7 +100,10 @@ void profile_release(const zeta_ctx* c);
 // ---- launchers (fft.cu) ----
 int set_ylm_constants();
 int launch_r2c(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t s);
-int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float* out, cudaStream_t s);
+// nf fields of bins b0.. : plain half spectra in spec (nf * n^3/2 complex, scratch), result in out as
+// ceil(nf/4) bin-interleaved groups [g][z][y][x][4].
+int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
+               cudaStream_t s);
 // Inverse-only helpers reused by other stages: C2R of nf half spectra in place.
 int launch_c2r_inplace(const zeta_ctx* c, float2* data, int nf, cudaStream_t s);
 

@@ -96,6 +96,27 @@ def host_ylm(l: int, m: int, vx: float, vy: float, vz: float) -> float:
     return lib().zeta_host_ylm(l, m, vx, vy, vz)
 
 
+def interleave(a):
+    """Plain stack (nb, n, n, n) -> bin-interleaved (ceil(nb/4), n, n, n, 4), zero-padded (numpy or torch)."""
+    nb, n = a.shape[0], a.shape[1]
+    g = (nb + 3) // 4
+    if hasattr(a, "new_zeros"):
+        pad = a.new_zeros((4 * g, n, n, n))
+        pad[:nb] = a
+        return pad.reshape(g, 4, n, n, n).permute(0, 2, 3, 4, 1).contiguous()
+    pad = np.zeros((4 * g, n, n, n), a.dtype)
+    pad[:nb] = a
+    return np.ascontiguousarray(pad.reshape(g, 4, n, n, n).transpose(0, 2, 3, 4, 1))
+
+
+def deinterleave(a, nb: int):
+    """Bin-interleaved (g, n, n, n, 4) -> plain (nb, n, n, n)."""
+    g, n = a.shape[0], a.shape[1]
+    if hasattr(a, "permute"):
+        return a.permute(0, 4, 1, 2, 3).reshape(4 * g, n, n, n)[:nb]
+    return a.transpose(0, 4, 1, 2, 3).reshape(4 * g, n, n, n)[:nb]
+
+
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -172,7 +193,8 @@ class Context:
         import torch
         b1 = self.nbins if b1 is None else b1
         if out is None:
-            out = torch.empty((b1 - b0, self.n, self.n, self.n), dtype=torch.float32, device="cuda")
+            g = (b1 - b0 + 3) // 4
+            out = torch.empty((g, self.n, self.n, self.n, 4), dtype=torch.float32, device="cuda")
         _check("zeta_reconstruct_alm", lib().zeta_reconstruct_alm(self._h, _ptr(delta_hat), l, m, b0, b1, _ptr(out),
                                                                   _stream()))
         return out

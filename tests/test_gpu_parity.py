@@ -60,13 +60,17 @@ def test_reconstruct_alm_matches_oracle(Z, n, box):
     d = _rand_grid(n, 3 + n)
     dh = ctx.fft_r2c(_dev(d))
     dh64 = np.fft.fftn(d.astype(np.float64))
+    nb = len(edges) - 1
     for l, m in [(0, 0), (1, -1), (1, 1), (2, 0), (3, 2), (4, -4), (5, 3)]:
-        got = ctx.reconstruct_alm(dh, l, m).cpu().numpy()
+        raw = ctx.reconstruct_alm(dh, l, m).cpu().numpy()
+        assert raw.shape == (2, n, n, n, 4)
+        np.testing.assert_array_equal(raw[1, ..., 1:], 0.0)  # zero padding lanes of the last group
+        got = Z.deinterleave(raw, nb)
         want = O.multipole_fields(dh64, l, m, n, box, edges)
-        for b in range(len(edges) - 1):
+        for b in range(nb):
             assert _maxrel(got[b], want[b]) < 1e-5, (l, m, b, _maxrel(got[b], want[b]))
-        sub = ctx.reconstruct_alm(dh, l, m, 2, 4).cpu().numpy()
-        np.testing.assert_array_equal(sub, got[2:4])
+        sub = Z.deinterleave(ctx.reconstruct_alm(dh, l, m, 4, 5).cpu().numpy(), 1)
+        np.testing.assert_array_equal(sub, got[4:5])
 
 
 @pytest.mark.parametrize("n,dsup", [(16, 2), (32, 4), (32, 2)])
@@ -90,15 +94,16 @@ def test_sum_grid_matches_oracle(Z, n, dsup, nb):
     ctx = Z.Context(n, 80.0, dsup, 1, edges)
     d = _rand_grid(n, 5)
     a = np.random.default_rng(6).standard_normal((nb, n, n, n)).astype(np.float32)
-    got = ctx.sum_grid(_dev(d), _dev(a), "node").cpu().numpy()
+    ai = _dev(Z.interleave(a))
+    got = ctx.sum_grid(_dev(d), ai, "node").cpu().numpy()
     want = O.sum_node(d.astype(np.float64), a.astype(np.float64))
     assert _rel(got, want) < 1e-5
     if n == 16:
-        got_g = ctx.sum_grid(_dev(d), _dev(a), "gamma").cpu().numpy()
+        got_g = ctx.sum_grid(_dev(d), ai, "gamma").cpu().numpy()
         want_g = O.sum_gamma(d.astype(np.float64), a.astype(np.float64), dsup)
         assert _rel(got_g, want_g) < 1e-5
         # accumulation semantics: a second call adds
-        g2 = ctx.sum_grid(_dev(d), _dev(a), "node", gram=torch.from_numpy(got).to("cuda")).cpu().numpy()
+        g2 = ctx.sum_grid(_dev(d), ai, "node", gram=torch.from_numpy(got).to("cuda")).cpu().numpy()
         assert _rel(g2, 2 * want) < 1e-5
 
 
@@ -131,7 +136,7 @@ def test_sort_and_particle_sum_match_oracle(Z, n, dsup, nb):
     a = np.random.default_rng(10).standard_normal((nb, n, n, n)).astype(np.float32)
     w = float(parts[:, 3].astype(np.float64).sum())
     wsum = torch.tensor([w], dtype=torch.float64, device="cuda")
-    got = ctx.sum_particles(_dev(srt), _dev(start), wsum, _dev(a)).cpu().numpy()
+    got = ctx.sum_particles(_dev(srt), _dev(start), wsum, _dev(Z.interleave(a))).cpu().numpy()
     want = O.sum_particles(a.astype(np.float64), parts[:, :3], parts[:, 3], n, box, dsup)
     assert _rel(got, want) < 1e-5
 
