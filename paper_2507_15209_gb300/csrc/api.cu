@@ -204,12 +204,12 @@ int zeta_reconstruct_alm(zeta_ctx* c, const float* delta_hat, int l, int m, int 
 int zeta_sum_grid(zeta_ctx* c, const float* delta, const float* alm, int form, double* gram, zeta_stream stream) {
   ZK_TRY(check_ctx(c));
   if (!delta || !alm || !gram || (form != ZETA_SUM_NODE && form != ZETA_SUM_GAMMA)) return ZETA_EINVAL;
-  if (form == ZETA_SUM_NODE && c->p.gram != ZETA_GRAM_FP32) return ZETA_ENOTSUP;
   ZK_TRY(need_ws(c, 0));
   const Layout L = layout(c, 0);
   double* part = at<double>(c, L.partials);
   if (form == ZETA_SUM_NODE)
-    ZK_TRY(launch_gram_node(c, delta, alm, part, stream));
+    ZK_TRY(c->p.gram == ZETA_GRAM_FP32 ? launch_gram_node(c, delta, alm, part, stream)
+                                       : launch_gram_node_tc(c, delta, alm, part, stream));
   else
     ZK_TRY(launch_gram_gamma(c, delta, alm, part, stream));
   return launch_reduce(c, part, gram_ctas(c), 1.0 / static_cast<double>(c->ng), nullptr, gram, stream);
@@ -253,7 +253,6 @@ int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* 
   if (!zeta || forms < 1 || forms > 7) return ZETA_EINVAL;
   const bool want_p = forms & ZETA_SUM_PARTICLE;
   if ((want_p || !delta) && (!particles || np < 1 || np > 0x7fffffffLL)) return ZETA_EINVAL;
-  if ((forms & ZETA_SUM_NODE) && c->p.gram != ZETA_GRAM_FP32) return ZETA_ENOTSUP;
   const int64_t npl = want_p ? np : 0;
   ZK_TRY(need_ws(c, npl));
   const Layout L = layout(c, npl);
@@ -293,7 +292,8 @@ int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* 
     for (int m = -l; m <= l; ++m) {
       ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, at<float2>(c, L.spectra), fields, stream));
       if (idx_node >= 0) {
-        ZK_TRY(launch_gram_node(c, dl, fields, part, stream));
+        ZK_TRY(c->p.gram == ZETA_GRAM_FP32 ? launch_gram_node(c, dl, fields, part, stream)
+                                           : launch_gram_node_tc(c, dl, fields, part, stream));
         ZK_TRY(launch_reduce(c, part, nparts, inv_ng, nullptr, zeta + idx_node * per_form + static_cast<size_t>(l) * nb * nb, stream));
       }
       if (idx_gamma >= 0) {

@@ -14,6 +14,7 @@
 // shared memory with coalesced accesses and transforms it with the radix-8 shared-memory
 // FFT of fft.cuh.
 #include "fft.cuh"
+#include "fftreg.cuh"
 #include "zeta_internal.h"
 
 namespace zk {
@@ -64,29 +65,32 @@ __device__ __forceinline__ float ylm_dev(int l, int m, float nx, float ny, float
 __device__ __forceinline__ int signed_freq(int i, int n) { return i < n / 2 ? i : i - n; }
 
 // ---------------------------------------------------------------------------------------
+// Threads per CTA of a register-staged transform: eight points per thread, at most MAXT.
+template <int L, int C, int MAXT>
+struct RegThreads {
+  static constexpr int V = L * C / 8;
+  static constexpr int NT = V < MAXT ? V : MAXT;
+};
+
 // Complex pencils along y (AXIS 1) or z (AXIS 2), in place; grid (nc/T, n, nfields).
 template <int N, int T, bool INV, int AXIS>
-__global__ void __launch_bounds__(256) k_fft_axis(float2* __restrict__ data, long long fstride,
-                                                  const float2* __restrict__ twg) {
+__global__ void __launch_bounds__(RegThreads<N, T, 512>::NT) k_fft_axis(float2* __restrict__ data, long long fstride,
+                                                                      const float2* __restrict__ twg) {
   constexpr int NC = N / 2;
+  constexpr int NT = RegThreads<N, T, 512>::NT;
   extern __shared__ float2 sm[];
   float2* tw = sm;
-  float2* buf = sm + N;
+  float2* ex = sm + N;  // [N][T]
   const int x0 = blockIdx.x * T;
   const long long o = blockIdx.y;
   float2* d = data + blockIdx.z * fstride;
   const long long stride = (AXIS == 1) ? NC : static_cast<long long>(N) * NC;
   const long long base = (AXIS == 1) ? o * N * NC + x0 : o * NC + x0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-  for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
-    const int k = idx / T, c = idx % T;
-    buf[idx] = d[base + k * stride + c];
-  }
-  fft_smem<N, INV>(buf, T, T, tw);
-  for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
-    const int k = idx / T, c = idx % T;
-    d[base + k * stride + c] = buf[fft_pos_of<N>(k) * T + c];
-  }
+  auto load = [&](int col, int k) { return d[base + k * stride + col]; };
+  auto store = [&](int col, int k, float2 v) { d[base + k * stride + col] = v; };
+  __syncthreads();
+  fft_reg<N, T, NT, INV, false>(ex, T, tw, load, store);
 }
 
 // Real rows -> half spectrum without Nyquist; grid (n*n/RB).
@@ -161,43 +165,41 @@ __global__ void __launch_bounds__(256) k_c2r_x(float2* __restrict__ data, long l
 
 // x-pass of the field reconstruction: C2R of the rows of four fields at once, written as
 // one bin-interleaved group [z][y][x][4] (lane j = field 4g + j; missing fields give 0).
+// The half-length complex transform takes Z[k] = (X[k] + conj X[NC-k]) + i e^{2 pi i k/N}
+// (X[k] - conj X[NC-k]) (X[NC] = 0) straight from global memory; its outputs z[j] =
+// (x[2j], x[2j+1]) are gathered in shared memory and leave as float4 bin groups.
 // grid (n*n/RB, ngroups); spec holds nf plain half spectra, fstride complex apart.
 template <int N, int RB>
-__global__ void __launch_bounds__(256) k_c2r_x4(const float2* __restrict__ spec, long long fstride, int nf,
-                                                float4* __restrict__ out, const float2* __restrict__ twg) {
+__global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
+    k_c2r_x4(const float2* __restrict__ spec, long long fstride, int nf, float4* __restrict__ out,
+             const float2* __restrict__ twg) {
   constexpr int NC = N / 2, C = 4 * RB, PS = C + 1;
+  constexpr int NT = RegThreads<NC, C, 256>::NT;
   extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* tw2 = sm + N;
-  float2* buf = tw2 + NC;  // [NC][PS], column c = j * RB + r
+  float2* tw = sm;          // W_N^e, e < N
+  float2* tw2 = sm + N;     // W_NC^e
+  float2* ex = tw2 + NC;    // [NC][PS] exchange
+  float2* res = ex + NC * PS;  // [NC][PS] outputs in natural order
   const int g = blockIdx.y;
   const long long r0 = static_cast<long long>(blockIdx.x) * RB;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
   for (int i = threadIdx.x; i < NC; i += blockDim.x) tw2[i] = twg[2 * i];
-  for (int idx = threadIdx.x; idx < NC * C; idx += blockDim.x) {
-    const int c = idx / NC, k = idx % NC;
-    const int f = 4 * g + c / RB, r = c % RB;
-    buf[k * PS + c] = (f < nf) ? spec[f * fstride + (r0 + r) * NC + k] : make_float2(0.f, 0.f);
-  }
   __syncthreads();
-  constexpr int NP = NC / 2 + 1;
-  for (int idx = threadIdx.x; idx < NP * C; idx += blockDim.x) {
-    const int c = idx / NP, k = idx % NP;
-    const int kp = NC - k;
-    const float2 xk = buf[k * PS + c];
-    const float2 xp = (k == 0) ? make_float2(0.f, 0.f) : buf[kp * PS + c];
+  auto load = [&](int c, int k) -> float2 {
+    const int f = 4 * g + c / RB;
+    if (f >= nf) return make_float2(0.f, 0.f);
+    const float2* row = spec + f * fstride + (r0 + c % RB) * NC;
+    const float2 xk = row[k];
+    const float2 xp = (k == 0) ? make_float2(0.f, 0.f) : row[NC - k];
     const float2 wk = cconj(tw[k]);
-    const float2 zk = cadd(cadd(xk, cconj(xp)), mul_i(cmul(wk, csub(xk, cconj(xp)))));
-    if (k != 0 && kp != k) {
-      const float2 wp = cconj(tw[kp]);
-      buf[kp * PS + c] = cadd(cadd(xp, cconj(xk)), mul_i(cmul(wp, csub(xp, cconj(xk)))));
-    }
-    buf[k * PS + c] = zk;
-  }
-  fft_smem<NC, true>(buf, PS, C, tw2);
+    return cadd(cadd(xk, cconj(xp)), mul_i(cmul(wk, csub(xk, cconj(xp)))));
+  };
+  auto store = [&](int c, int j, float2 v) { res[j * PS + c] = v; };
+  fft_reg<NC, C, NT, true, true>(ex, PS, tw2, load, store);
+  __syncthreads();
   for (int idx = threadIdx.x; idx < NC * RB; idx += blockDim.x) {
     const int r = idx / NC, j = idx % NC;
-    const float2* src = buf + fft_pos_of<NC>(j) * PS + r;
+    const float2* src = res + j * PS + r;
     const float2 z0 = src[0], z1 = src[RB], z2 = src[2 * RB], z3 = src[3 * RB];
     float4* o = out + (static_cast<long long>(g) * N * N + r0 + r) * N + 2 * j;
     o[0] = make_float4(z0.x, z1.x, z2.x, z3.x);
@@ -206,19 +208,21 @@ __global__ void __launch_bounds__(256) k_c2r_x4(const float2* __restrict__ spec,
 }
 
 // z-pass of the field reconstruction with the multipole window fused in.
-// grid (nc/T, n); each CTA keeps its delta_hat tile [z][T] in shared memory and emits
-// one transformed tile per field f < nf into out + f * fstride.
+// grid (nc/T, n); each thread keeps, for its own stage-0 points, delta_hat, the angular
+// factor R_lm(n-hat) (with the real sign of i^l) and the |n|^2 index in registers.  Bins are
+// taken four at a time: one float4 gather of the window table [n2][bin] per point, then for
+// each of the four fields delta_hat * R * J_b(|n|^2) (* i for odd l) is transformed and the
+// z-transformed tile written to out + f * fstride (fields b0 + f, f < nf; b0 % 4 == 0).
 template <int N, int T>
-__global__ void __launch_bounds__(256) k_alm_z(const float2* __restrict__ dhat, float2* __restrict__ out,
-                                               long long fstride, int nf, const float* __restrict__ jtab,
-                                               long long nn2, int l, int m, const float2* __restrict__ twg) {
+__global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
+    k_alm_z(const float2* __restrict__ dhat, float2* __restrict__ out, long long fstride, int nf,
+            const float4* __restrict__ jt4, int nbp4, int l, int m, const float2* __restrict__ twg) {
   constexpr int NC = N / 2;
+  constexpr int NT = RegThreads<N, T, 512>::NT;
+  constexpr int PPT = N * T / NT;
   extern __shared__ float2 sm[];
   float2* tw = sm;
-  float2* sdh = tw + N;        // [N][T]
-  float2* work = sdh + N * T;  // [N][T]
-  float* sang = reinterpret_cast<float*>(work + N * T);
-  int* sn2 = reinterpret_cast<int*>(sang + N * T);
+  float2* ex = tw + N;  // [N][T] exchange
   const int x0 = blockIdx.x * T;
   const int iy = blockIdx.y;
   const long long colbase = static_cast<long long>(iy) * NC + x0;
@@ -234,29 +238,37 @@ __global__ void __launch_bounds__(256) k_alm_z(const float2* __restrict__ dhat, 
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
   const float sgn = ((l & 3) < 2) ? 1.f : -1.f;  // real part of i^l (or of i^{l-1} for odd l)
   const int ny = signed_freq(iy, N);
-  for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
-    const int z = idx / T, c = idx % T;
-    sdh[idx] = dhat[colbase + z * zstride + c];
+  float2 pd[PPT];
+  int pn[PPT];
+#pragma unroll
+  for (int s = 0; s < PPT; ++s) {
+    int c, z;
+    reg_slot<N, T, NT, false>(s, c, z);
     const int nz = signed_freq(z, N), nx = x0 + c;
     const bool nyq = (z == N / 2);
-    sn2[idx] = nyq ? 0 : nx * nx + ny * ny + nz * nz;
-    sang[idx] = nyq ? 0.f : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz));
+    pn[s] = nyq ? 0 : nx * nx + ny * ny + nz * nz;
+    const float a = nyq ? 0.f : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz));
+    pd[s] = cscale(dhat[colbase + z * zstride + c], a);
   }
   __syncthreads();
-  for (int f = 0; f < nf; ++f) {
-    const float* jt = jtab + f * nn2;
-    for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
-      const float s = sang[idx] * __ldg(jt + sn2[idx]);
-      float2 v = cscale(sdh[idx], s);
-      if (l & 1) v = mul_i(v);
-      work[idx] = v;
+  for (int g = 0; 4 * g < nf; ++g) {
+    float4 jv[PPT];
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) jv[s] = __ldg(jt4 + static_cast<long long>(pn[s]) * nbp4 + g);
+    const int nj = (nf - 4 * g) < 4 ? (nf - 4 * g) : 4;
+    for (int j = 0; j < nj; ++j) {
+      const int f = 4 * g + j;
+      float2 v[PPT];
+#pragma unroll
+      for (int s = 0; s < PPT; ++s) {
+        const float jj = j == 0 ? jv[s].x : j == 1 ? jv[s].y : j == 2 ? jv[s].z : jv[s].w;
+        v[s] = cscale(pd[s], jj);
+        if (l & 1) v[s] = mul_i(v[s]);
+      }
+      float2* of = out + f * fstride;
+      auto store = [&](int c, int z, float2 val) { of[colbase + z * zstride + c] = val; };
+      fft_reg_v<N, T, NT, true, false>(v, ex, T, tw, store);
     }
-    fft_smem<N, true>(work, T, T, tw);
-    for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
-      const int z = idx / T, c = idx % T;
-      out[f * fstride + colbase + z * zstride + c] = work[fft_pos_of<N>(z) * T + c];
-    }
-    __syncthreads();
   }
 }
 
@@ -290,8 +302,8 @@ int r2c_impl(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t s
   k_r2c_x<N, kRB><<<N * N / kRB, 256, smx, s>>>(delta, dhat, c->d_tw);
   size_t sma = (N + N * T) * sizeof(float2);
   if (set_smem(k_fft_axis<N, T, false, 1>, sma) || set_smem(k_fft_axis<N, T, false, 2>, sma)) return ZETA_ECUDA;
-  k_fft_axis<N, T, false, 1><<<dim3(NC / T, N, 1), 256, sma, s>>>(dhat, 0, c->d_tw);
-  k_fft_axis<N, T, false, 2><<<dim3(NC / T, N, 1), 256, sma, s>>>(dhat, 0, c->d_tw);
+  k_fft_axis<N, T, false, 1><<<dim3(NC / T, N, 1), RegThreads<N, T, 512>::NT, sma, s>>>(dhat, 0, c->d_tw);
+  k_fft_axis<N, T, false, 2><<<dim3(NC / T, N, 1), RegThreads<N, T, 512>::NT, sma, s>>>(dhat, 0, c->d_tw);
   return check_launch();
 }
 
@@ -304,7 +316,7 @@ int c2r_impl(const zeta_ctx* c, float2* data, int nf, cudaStream_t s, bool do_y)
     StageScope prof(c, ST_ALM_Y, 1, s);
     size_t sma = (N + N * T) * sizeof(float2);
     if (set_smem(k_fft_axis<N, T, true, 1>, sma)) return ZETA_ECUDA;
-    k_fft_axis<N, T, true, 1><<<dim3(NC / T, N, nf), 256, sma, s>>>(data, fstride, c->d_tw);
+    k_fft_axis<N, T, true, 1><<<dim3(NC / T, N, nf), RegThreads<N, T, 512>::NT, sma, s>>>(data, fstride, c->d_tw);
   }
   StageScope prof(c, ST_ALM_X, 1, s);
   size_t smx = (N + NC + NC * (kRB + 1)) * sizeof(float2);
@@ -322,26 +334,28 @@ int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf
   const long long fstride = static_cast<long long>(N) * N * NC;
   {
     StageScope prof(c, ST_ALM_Z, 1, s);
-    size_t smz = N * sizeof(float2) + static_cast<size_t>(N) * T * (2 * sizeof(float2) + sizeof(float) + sizeof(int));
+    size_t smz = (N + static_cast<size_t>(N) * T) * sizeof(float2);
     if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
-    const float* jt = c->d_jtab + (static_cast<long long>(l) * c->p.nbins + b0) * c->nn2;
-    k_alm_z<N, T><<<dim3(NC / T, N), 256, smz, s>>>(dhat, spec, fstride, nf, jt, c->nn2, l, m, c->d_tw);
+    const int nbp4 = (c->p.nbins + 3) / 4;
+    const float4* jt4 = reinterpret_cast<const float4*>(c->d_jtab) + static_cast<long long>(l) * c->nn2 * nbp4 + b0 / 4;
+    k_alm_z<N, T><<<dim3(NC / T, N), RegThreads<N, T, 512>::NT, smz, s>>>(dhat, spec, fstride, nf, jt4, nbp4, l, m,
+                                                                     c->d_tw);
     if (check_launch()) return ZETA_ECUDA;
   }
   {
     StageScope prof(c, ST_ALM_Y, 1, s);
     size_t sma = (N + N * TY) * sizeof(float2);
     if (set_smem(k_fft_axis<N, TY, true, 1>, sma)) return ZETA_ECUDA;
-    k_fft_axis<N, TY, true, 1><<<dim3(NC / TY, N, nf), 256, sma, s>>>(spec, fstride, c->d_tw);
+    k_fft_axis<N, TY, true, 1><<<dim3(NC / TY, N, nf), RegThreads<N, TY, 512>::NT, sma, s>>>(spec, fstride, c->d_tw);
     if (check_launch()) return ZETA_ECUDA;
   }
   StageScope prof(c, ST_ALM_X, 1, s);
   constexpr int RB = kRB4;
-  size_t smx = (N + NC + NC * (4 * RB + 1)) * sizeof(float2);
+  size_t smx = (N + NC + 2 * NC * (4 * RB + 1)) * sizeof(float2);
   if (set_smem(k_c2r_x4<N, RB>, smx)) return ZETA_ECUDA;
   const int ng4 = (nf + 3) / 4;
-  k_c2r_x4<N, RB><<<dim3(N * N / RB, ng4), 256, smx, s>>>(spec, fstride, nf, reinterpret_cast<float4*>(out),
-                                                          c->d_tw);
+  k_c2r_x4<N, RB><<<dim3(N * N / RB, ng4), RegThreads<N / 2, 4 * RB, 256>::NT, smx, s>>>(
+      spec, fstride, nf, reinterpret_cast<float4*>(out), c->d_tw);
   return check_launch();
 }
 
@@ -354,7 +368,7 @@ int c2r_full(const zeta_ctx* c, float2* data, int nf, cudaStream_t s) {
   size_t sma = (N + N * T) * sizeof(float2);
   if (set_smem(k_fft_axis<N, T, true, 2>, sma)) return ZETA_ECUDA;
   StageScope prof(c, ST_ALM_Z, 1, s);
-  k_fft_axis<N, T, true, 2><<<dim3(NC / T, N, nf), 256, sma, s>>>(data, fstride, c->d_tw);
+  k_fft_axis<N, T, true, 2><<<dim3(NC / T, N, nf), RegThreads<N, T, 512>::NT, sma, s>>>(data, fstride, c->d_tw);
   if (check_launch()) return ZETA_ECUDA;
   return c2r_impl<N>(c, data, nf, s, true);
 }

@@ -353,7 +353,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_mass(const float2* __restrict
       w = (ix == 0 ? 1.f : 2.f) * (d.x * d.x + d.y * d.y) * mhat[ix] * mhat[iy] * mhat[iz];
     }
     wts[threadIdx.x] = w;
-    for (int b = 0; b < NBP; ++b) vals[threadIdx.x * G::NBS + b] = (b < nb && !nyq) ? __ldg(jt + b * nn2 + n2) : 0.f;
+    const int nbp = 4 * ((nb + 3) / 4);
+    for (int b = 0; b < NBP; ++b) vals[threadIdx.x * G::NBS + b] = (b < nb && !nyq) ? __ldg(jt + n2 * nbp + b) : 0.f;
     __syncthreads();
     if (grp < G::NGRP) g.add(vals, wts, kPB, b1, b2, grp);
   }
@@ -431,7 +432,7 @@ int mass_impl(const zeta_ctx* c, const float2* dhat, int l, double* partials, cu
   StageScope prof(c, ST_MASS, 1, s);
   const size_t sm = smem_mass<NBP>();
   if (prep(k_gram_mass<NBP>, sm)) return ZETA_ECUDA;
-  const float* jt = c->d_jtab + static_cast<long long>(l) * c->p.nbins * c->nn2;
+  const float* jt = c->d_jtab + static_cast<long long>(l) * c->nn2 * (4 * ((c->p.nbins + 3) / 4));
   k_gram_mass<NBP><<<gram_ctas(c), kThreads, sm, s>>>(dhat, jt, c->nn2, c->d_mhat, c->n, c->p.nbins, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }

@@ -158,7 +158,8 @@ void host_jbar_table(int n, double box, int lmax, int nbins, const double* edges
   const int64_t nn2 = table_n2_count(n);
   const double ng = static_cast<double>(n) * n * n;
   const double pref = std::sqrt(4.0 * kPi) / ng;
-  out.assign(static_cast<size_t>(lmax + 1) * nbins * nn2, 0.0f);
+  const int nbp = 4 * ((nbins + 3) / 4);
+  out.assign(static_cast<size_t>(lmax + 1) * nn2 * nbp, 0.0f);
   std::vector<double> gx, gw;
   gauss_legendre(12, gx, gw);
   unsigned nth = std::thread::hardware_concurrency();
@@ -173,7 +174,7 @@ void host_jbar_table(int n, double box, int lmax, int nbins, const double* edges
         const double den = (r_hi * r_hi * r_hi - r_lo * r_lo * r_lo) / 3.0;
         shell_moments(lmax, k, r_lo, r_hi, gx, gw, num);
         for (int l = 0; l <= lmax; ++l)
-          out[(static_cast<size_t>(l) * nbins + b) * nn2 + i] = static_cast<float>(pref * num[l] / den);
+          out[(static_cast<size_t>(l) * nn2 + i) * nbp + b] = static_cast<float>(pref * num[l] / den);
       }
     }
   };

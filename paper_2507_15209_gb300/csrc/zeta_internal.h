@@ -20,7 +20,8 @@ inline int64_t table_n2_count(int n) {
   const int64_t h = n / 2 - 1;
   return 3 * h * h + 1;
 }
-// sqrt(4 pi) jbar_l(k; b) / N_g for l <= lmax, all bins, all n2 < table_n2_count(n).
+// sqrt(4 pi) jbar_l(k; b) / N_g for l <= lmax, all n2 < table_n2_count(n), all bins, laid out
+// [l][n2][b] with the bins padded to a multiple of 4 (one float4 gathers four bins).
 void host_jbar_table(int n, double box, int lmax, int nbins, const double* edges, std::vector<float>& out);
 void host_jbar_values(int l, double box, double r_lo, double r_hi, const int64_t* n2, int64_t count,
                       double* out);
@@ -68,7 +69,7 @@ struct zeta_ctx {
   int device = 0;
   int gamma_q = 0;
   // device tables
-  float* d_jtab = nullptr;    // [(l * nbins + b) * nn2 + n2]
+  float* d_jtab = nullptr;    // [(l * nn2 + n2) * nbp + b], nbp = 4 * ceil(nbins / 4)
   float2* d_tw = nullptr;     // W_n^e, e < n
   float* d_mhat = nullptr;    // Mhat(k) for k-index < n
   float* d_gq = nullptr;      // cell quadrature: weights[q] then beta[q*dsup+o]
@@ -122,6 +123,8 @@ int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, d
                       cudaStream_t s);
 int launch_gram_particles(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, const float* alm,
                           double* partials, cudaStream_t s);
+// tensor-core node Gram (gram_tc.cu), arithmetic chosen by c->p.gram
+int launch_gram_node_tc(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
 int launch_mass(const zeta_ctx* c, const float2* dhat, int l, double* partials, cudaStream_t s);
 // out[b1][b2] += scale * (1/ *wdiv if wdiv) * sum_cta partials[cta][b1][b2], symmetrised.
 int launch_reduce(const zeta_ctx* c, const double* partials, int nparts, double scale, const double* wdiv,

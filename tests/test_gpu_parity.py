@@ -205,3 +205,32 @@ def test_nonfinite_particle_is_reported_and_workspace_checked(Z):
     with pytest.raises(Z.ZetaError) as e:
         ctx.zeta_ell(particles=_dev(parts), forms=("particle",))
     assert e.value.code == -6
+
+
+# --- node-form Gram on the tensor cores (tcgen05): per-arithmetic error bounds -------------
+@pytest.mark.parametrize("gram,tol", [("tf32", 5e-3), ("bf16", 3e-2), ("bf16x3", 1e-4)])
+@pytest.mark.parametrize("nb", [5, 20])
+def test_tensor_core_node_gram(Z, gram, tol, nb):
+    n = 32
+    edges = np.linspace(5.0, 30.0, nb + 1)
+    ctx = Z.Context(n, 80.0, 4, 1, edges, gram=gram)
+    d = _rand_grid(n, 15)
+    a = np.random.default_rng(16).standard_normal((nb, n, n, n)).astype(np.float32)
+    got = ctx.sum_grid(_dev(d), _dev(Z.interleave(a)), "node").cpu().numpy()
+    assert ctx.get_status() == 0
+    want = O.sum_node(d.astype(np.float64), a.astype(np.float64))
+    err = _rel(got, want)
+    assert err < tol, (gram, nb, err)
+
+
+def test_tensor_core_zeta_ell_node_form(Z):
+    n, box, lmax = 32, 240.0, 3
+    edges = np.linspace(10.0, 85.0, 6)
+    parts = mocks.lognormal_catalogue(n, 12000, box, 51, 52)
+    want, _ = O.zeta_multipoles(parts.astype(np.float64), n, box, edges, lmax, 4, forms=("node",))
+    for gram, tol in (("bf16x3", 1e-4), ("tf32", 5e-3)):
+        ctx = Z.Context(n, box, 4, lmax, edges, gram=gram, np_max=len(parts), forms=("node",))
+        got = ctx.zeta_ell(particles=_dev(parts), forms=("node",))["node"].cpu().numpy()
+        assert ctx.get_status() == 0
+        for l in range(lmax + 1):
+            assert _rel(got[l], want["node"][l]) < tol, (gram, l)
