@@ -180,6 +180,25 @@ int zeta_zeta_ell(zeta_ctx* ctx, const float* particles, int64_t np, const float
  * ZETA_ETIMEOUT), clearing it. */
 int zeta_get_status(zeta_ctx* ctx, zeta_stream stream);
 
+/* Assignment that allocates nothing, for callers that cannot allocate device memory when
+ * they call: code inside a host framework whose memory pool already owns the device,
+ * latency-critical loops that cannot afford an allocation's implicit synchronisation, and
+ * services that must not run out of memory once started.  The paper has no counterpart; it
+ * computes exactly what zeta_assign computes (same kernels, same fixed-point sums), without
+ * a context or workspace: n (16 <= n <= 128, power of two), box and dsup (2 or 4) are passed
+ * directly.  particles: device float4[np]; delta: device float[n^3] (output); wsum: device
+ * double[1] (output) or NULL.
+ *   - Scratch is a fixed array of 16 MiB + 16 KiB inside the library; every GPU that loads
+ *     the library holds it until the process exits.  n > 128 returns ZETA_EINVAL.
+ *   - The first call on a device looks up that array's device address (cudaGetSymbolAddress)
+ *     with the device current; make that first call before any stream capture begins.
+ *   - Every call reuses the same array and clears it itself; calls that can overlap on the
+ *     GPU (different streams, or different host threads on one device) race on it and must be
+ *     ordered by the caller.
+ *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
+int zeta_assign_noalloc(int n, double box, int dsup, const float* particles, int64_t np, float* delta,
+                        double* wsum, zeta_stream stream);
+
 /* ---- stage timers (tracing) ----
  * When enabled, every kernel group the library issues is bracketed by a CUDA event pair on
  * its stream.  zeta_profile_enable resets the totals; zeta_profile_read synchronises the

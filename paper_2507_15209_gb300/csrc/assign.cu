@@ -10,6 +10,8 @@
 //
 // Tiling: particles are counted into 8x8x8-cell tiles, prefix-summed, scattered, and each
 // tile's list is put back into original order, so particle-form sums are reproducible.
+#include <mutex>
+
 #include "zeta_internal.h"
 
 namespace zk {
@@ -274,3 +276,74 @@ int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sort
 }
 
 }  // namespace zk
+
+// ---------------------------------------------------------------------------------------
+// Assignment without any allocation, for callers that cannot allocate device memory when
+// they call: code inside a host framework whose memory pool already owns the device (a raw
+// allocation would fail or fragment that pool), latency-critical loops that cannot afford
+// the implicit synchronisation of an allocation, and services that must not hit an
+// out-of-memory error once they are up.  Its scratch lives in a fixed array that every GPU
+// which loads this library holds until the process exits.
+namespace zk {
+namespace {
+
+constexpr int kStaticMaxN = 128;  // largest grid side the fixed scratch can hold
+constexpr long long kStaticAcc = static_cast<long long>(kStaticMaxN) * kStaticMaxN * kStaticMaxN;
+// layout (64-bit words): [fixed-point grid kStaticAcc][reduction partials 2*kRedCtas]
+//                        [W, sum|w|, scale, spare][status word]
+constexpr long long kStaticWords = kStaticAcc + 2 * kRedCtas + 4 + 1;
+
+static __device__ __align__(256) unsigned long long g_assign_scratch[kStaticWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned long long* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the fixed scratch on the current device, looked up once per device.
+int static_scratch(unsigned long long** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ZETA_ECUDA;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_assign_scratch) != cudaSuccess || !p) return ZETA_ECUDA;
+    g_static_ptr[dev] = static_cast<unsigned long long*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return ZETA_OK;
+}
+
+}  // namespace
+}  // namespace zk
+
+extern "C" int zeta_assign_noalloc(int n, double box, int dsup, const float* particles, int64_t np, float* delta,
+                                   double* wsum, zeta_stream stream) {
+  using namespace zk;
+  if (n < 16 || n > kStaticMaxN || (n & (n - 1)) || !(box > 0) || (dsup != 2 && dsup != 4)) return ZETA_EINVAL;
+  if (!particles || np < 1 || np > 0x7fffffffLL || !delta) return ZETA_EINVAL;
+  unsigned long long* base = nullptr;
+  if (static_scratch(&base) != ZETA_OK) return ZETA_ECUDA;
+  const long long ng = static_cast<long long>(n) * n * n;
+  unsigned long long* acc = base;
+  double* part = reinterpret_cast<double*>(base + kStaticAcc);
+  double* wstat = part + 2 * kRedCtas;
+  int* status = reinterpret_cast<int*>(base + kStaticAcc + 2 * kRedCtas + 4);
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ZETA_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  cudaStream_t s = stream;
+  const float4* p = reinterpret_cast<const float4*>(particles);
+  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return ZETA_ECUDA;
+  k_weight_partials<<<kRedCtas, 256, 0, s>>>(p, np, part, status);
+  k_weight_final<<<1, 32, 0, s>>>(part, kRedCtas, wstat, wsum);
+  if (cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * ng, s) != cudaSuccess) return ZETA_ECUDA;
+  const double inv_h = n / box;
+  const int g = grid_for(np, 256, sms);
+  if (dsup == 2)
+    k_assign_scatter<2><<<g, 256, 0, s>>>(p, np, n, inv_h, wstat, acc);
+  else
+    k_assign_scatter<4><<<g, 256, 0, s>>>(p, np, n, inv_h, wstat, acc);
+  k_assign_finalize<<<grid_for(ng, 256, sms), 256, 0, s>>>(acc, ng, wstat, delta);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+

@@ -53,6 +53,7 @@ _SIGS = {
     "zeta_mass_term": ([_VP, _VP, _INT, _DBL, _VP, _VP], _INT),
     "zeta_zeta_ell": ([_VP, _VP, _I64, _VP, _INT, _VP, _VP], _INT),
     "zeta_get_status": ([_VP, _VP], _INT),
+    "zeta_assign_noalloc": ([_INT, _DBL, _INT, _VP, _I64, _VP, _VP, _VP], _INT),
     "zeta_profile_enable": ([_VP, _INT], _INT),
     "zeta_profile_read": ([_VP, _VP, _VP, _VP, _INT], _INT),
     "zeta_profile_stage_name": ([_INT], ctypes.c_char_p),
@@ -94,6 +95,19 @@ def host_jbar(l: int, box: float, r_lo: float, r_hi: float, n2) -> np.ndarray:
 
 def host_ylm(l: int, m: int, vx: float, vy: float, vz: float) -> float:
     return lib().zeta_host_ylm(l, m, vx, vy, vz)
+
+
+def assign_noalloc(n: int, box: float, dsup: int, particles, delta=None, wsum=None):
+    """zeta_assign_noalloc: B-spline assignment with the library's fixed scratch (no allocation
+    inside the call; the caller may pass preallocated delta / wsum tensors)."""
+    import torch
+    if delta is None:
+        delta = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    if wsum is None:
+        wsum = torch.empty(1, dtype=torch.float64, device="cuda")
+    _check("zeta_assign_noalloc", lib().zeta_assign_noalloc(n, float(box), dsup, _ptr(particles), particles.shape[0],
+                                                            _ptr(delta), _ptr(wsum), _stream()))
+    return delta, wsum
 
 
 def interleave(a):
