@@ -176,6 +176,26 @@ int zeta_mass_term(zeta_ctx* ctx, const float* delta_hat, int l, double sign, do
 int zeta_zeta_ell(zeta_ctx* ctx, const float* particles, int64_t np, const float* delta, int forms,
                   double* zeta, zeta_stream stream);
 
+/* Many catalogues in one launch: catalogue i is particles[offsets[i] .. offsets[i+1]) (device
+ * float4, concatenated; offsets is a host array of ncat+1 increasing values, each catalogue
+ * non-empty).  The whole batch -- every catalogue's assignment, sorting, R2C and per-(l, m)
+ * loop, in order -- is captured once into a CUDA graph that is instantiated and launched
+ * with a single cudaGraphLaunch on `stream`; a later call with the same pointers, forms and
+ * offsets relaunches the cached graph.  zeta: device double[ncat * nforms * (lmax+1) * nb * nb]
+ * (each catalogue's block as zeta_zeta_ell writes it).  The workspace must cover the largest
+ * catalogue.  Changing the workspace or the tuning drops the cached graph. */
+int zeta_batch(zeta_ctx* ctx, const float* particles, const int64_t* offsets, int ncat, int forms, double* zeta,
+               zeta_stream stream);
+
+/* Autotuner: on this catalogue, times the Gram kernels that `forms` uses at persistent grid
+ * sizes of 1, 2, 3, 4, 6 and 8 CTAs per SM and keeps the fastest for each kernel (used by all
+ * later calls).  Synchronises the stream; overwrites the workspace. */
+int zeta_autotune(zeta_ctx* ctx, const float* particles, int64_t np, int forms, zeta_stream stream);
+
+/* The tuned persistent grid sizes in CTAs per SM: [node fp32, particle, Gamma, mass,
+ * node tensor-core].  Returns 5. */
+int zeta_get_tuning(const zeta_ctx* ctx, int* ctas_per_sm, int n);
+
 /* Synchronise the stream and return the latched device status (ZETA_OK or ZETA_EDATA /
  * ZETA_ETIMEOUT), clearing it. */
 int zeta_get_status(zeta_ctx* ctx, zeta_stream stream);

@@ -48,6 +48,7 @@ __all__ = [
     "jbar", "real_ylm", "window_kernel", "multipole_fields", "sum_node",
     "gamma_1d", "mass_1d", "sum_gamma", "interpolate", "sum_particles",
     "mass_term", "zeta_multipoles", "zeta_from_delta", "brute_force_raw",
+    "bspline_deriv", "interpolate_grad", "loss", "grad_node_delta", "grad_particle_positions",
 ]
 
 FOUR_PI = 4.0 * math.pi
@@ -434,3 +435,112 @@ def brute_force_raw(particles, box: float, edges, lmax: int):
                 abar *= vol / (wsum * vb)
                 out[ell] += w[i] * np.outer(abar, abar)
     return out * FOUR_PI / wsum
+
+
+# ---------------------------------------------------------------------------
+# Gradients of a scalar loss L = sum_l sum_ij W_l[i, j] zeta_l[i, j] (field-level
+# inference), by the transpose of every linear step of the measurement above.
+# With S_l = (W_l + W_l^T) / 2 (zeta is symmetric), and A_lm,b the map delta -> a_lm,b:
+#   A^T h = (-1)^l IDFT[K_lm,b DFT(h)]   (the window is i^l times a real function).
+# ---------------------------------------------------------------------------
+def bspline_deriv(u, dsup: int):
+    """d beta_D / du."""
+    u = np.asarray(u, dtype=np.float64)
+    a = np.abs(u)
+    sg = np.sign(u)
+    if dsup == 2:
+        return np.where(a < 1.0, -sg, 0.0)
+    if dsup == 4:
+        inner = -2.0 * u + 1.5 * u * a
+        outer = -0.5 * sg * (2.0 - a) ** 2
+        return np.where(a < 1.0, inner, np.where(a < 2.0, outer, 0.0))
+    raise ValueError("dsup must be 2 or 4")
+
+
+def interpolate_grad(a, pos, n: int, box: float, dsup: int):
+    """Gradient with respect to the point of f_b(x) = sum_l beta(x/H - l) a_b(l): (nb, N_p, 3)."""
+    pos = np.asarray(pos, np.float64)
+    h = box / n
+    u = pos / h
+    base = stencil_base(u, dsup)
+    nb = a.shape[0]
+    af = a.reshape(nb, -1)
+    g = np.zeros((nb, pos.shape[0], 3))
+    for oz in range(dsup):
+        lz = base[:, 2] + oz
+        bz, dz = bspline(u[:, 2] - lz, dsup), bspline_deriv(u[:, 2] - lz, dsup)
+        for oy in range(dsup):
+            ly = base[:, 1] + oy
+            by, dy = bspline(u[:, 1] - ly, dsup), bspline_deriv(u[:, 1] - ly, dsup)
+            for ox in range(dsup):
+                lx = base[:, 0] + ox
+                bx, dx = bspline(u[:, 0] - lx, dsup), bspline_deriv(u[:, 0] - lx, dsup)
+                idx = ((lz % n) * n + (ly % n)) * n + (lx % n)
+                v = af[:, idx]
+                g[:, :, 0] += (dx * by * bz)[None, :] * v
+                g[:, :, 1] += (bx * dy * bz)[None, :] * v
+                g[:, :, 2] += (bx * by * dz)[None, :] * v
+    return g / h
+
+
+def loss(zeta_l, weights):
+    """L = sum_l sum_ij W_l[i, j] zeta_l[i, j]."""
+    return float(np.sum(np.asarray(weights) * np.asarray(zeta_l)))
+
+
+def grad_node_delta(delta, weights, n: int, box: float, edges, lmax: int):
+    """dL/d delta for the node form: (1/N_g) [sum_lm sum S a a + IDFT(sum_lm (-1)^l sum_b K_b DFT(h_b))],
+    h_b = 2 delta sum_b' S[b, b'] a_b'."""
+    delta = np.asarray(delta, np.float64)
+    ng = delta.size
+    dh = np.fft.fftn(delta)
+    q = np.zeros(delta.shape)
+    gk = np.zeros(delta.shape, np.complex128)
+    for ell in range(lmax + 1):
+        s = 0.5 * (weights[ell] + weights[ell].T)
+        for m in range(-ell, ell + 1):
+            kern = window_kernel(ell, m, n, box, edges)
+            a = np.stack([np.fft.ifftn(dh * kern[b]).real for b in range(kern.shape[0])])
+            q += np.einsum("ij,ixyz,jxyz->xyz", s, a, a)
+            hb = 2.0 * delta[None] * np.einsum("ij,jxyz->ixyz", s, a)
+            gk += (-1.0) ** ell * sum(kern[b] * np.fft.fftn(hb[b]) for b in range(kern.shape[0]))
+    return (q + np.fft.ifftn(gk).real) / ng
+
+
+def grad_particle_positions(particles, weights, n: int, box: float, edges, lmax: int, dsup: int):
+    """dL/dx_p (N_p, 3) for the particle form, with the fields built from the particles' own
+    assignment: the direct term through f_b(x_p), plus the term through delta (assignment),
+    where dL/d delta = IDFT(sum_lm (-1)^l sum_b K_b DFT(h_b - u_b)), h_b the assignment of
+    (2 w_p / W) (S f)_b, u_b = dU/da_b = (2/N_g) sum_b' S[b, b'] (M3 * a_b')."""
+    p = np.asarray(particles, np.float64)
+    pos, w = p[:, :3], p[:, 3]
+    wsum = float(w.sum())
+    ng = n ** 3
+    eps, _ = assign(pos, w, n, box, dsup)
+    delta = contrast(eps, wsum)
+    dh = np.fft.fftn(delta)
+    m1 = mass_1d(dsup)
+    direct = np.zeros((len(p), 3))
+    gk = np.zeros((n, n, n), np.complex128)
+    for ell in range(lmax + 1):
+        s = 0.5 * (weights[ell] + weights[ell].T)
+        for m in range(-ell, ell + 1):
+            kern = window_kernel(ell, m, n, box, edges)
+            nb = kern.shape[0]
+            a = np.stack([np.fft.ifftn(dh * kern[b]).real for b in range(nb)])
+            f = interpolate(a, pos, n, box, dsup)
+            df = interpolate_grad(a, pos, n, box, dsup)
+            c = (2.0 * w / wsum)[None, :] * (s @ f)
+            direct += np.einsum("bp,bpd->pd", c, df)
+            for b in range(nb):
+                hb, _ = assign(pos, c[b], n, box, dsup)
+                mb = np.zeros((n, n, n))
+                for dz, mz in m1.items():
+                    for dy, my in m1.items():
+                        for dx, mx in m1.items():
+                            mb += mz * my * mx * _shift(np.einsum("j,jxyz->xyz", s[b], a), (dz, dy, dx))
+                ub = 2.0 / ng * mb
+                gk += (-1.0) ** ell * kern[b] * np.fft.fftn(hb - ub)
+    gdelta = np.fft.ifftn(gk).real
+    via = (ng / wsum) * w[:, None] * interpolate_grad(gdelta[None], pos, n, box, dsup)[0]
+    return direct + via

@@ -58,6 +58,12 @@ T* at(const zeta_ctx* c, size_t off) {
   return reinterpret_cast<T*>(c->ws + off);
 }
 
+void drop_batch_graph(zeta_ctx* c) {
+  if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+  c->batch_exec = nullptr;
+  c->batch_key.clear();
+}
+
 #define ZK_TRY(expr)             \
   do {                           \
     const int _rc = (expr);      \
@@ -148,6 +154,8 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
 int zeta_destroy(zeta_ctx* c) {
   if (!c) return ZETA_OK;
   profile_release(c);
+  if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->d_jtab);
   cudaFree(c->d_tw);
   cudaFree(c->d_mhat);
@@ -167,6 +175,7 @@ int zeta_set_workspace(zeta_ctx* c, void* dptr, size_t bytes) {
   if (dptr && (reinterpret_cast<uintptr_t>(dptr) % kAlign)) return ZETA_EINVAL;
   c->ws = static_cast<char*>(dptr);
   c->ws_bytes = dptr ? bytes : 0;
+  drop_batch_graph(c);  // a captured batch refers to the old workspace
   return ZETA_OK;
 }
 
@@ -212,7 +221,8 @@ int zeta_sum_grid(zeta_ctx* c, const float* delta, const float* alm, int form, d
                                        : launch_gram_node_tc(c, delta, alm, part, stream));
   else
     ZK_TRY(launch_gram_gamma(c, delta, alm, part, stream));
-  return launch_reduce(c, part, gram_ctas(c), 1.0 / static_cast<double>(c->ng), nullptr, gram, stream);
+  return launch_reduce(c, part, gram_ctas(c, form == ZETA_SUM_NODE ? (c->p.gram == ZETA_GRAM_FP32 ? GK_NODE : GK_TC) : GK_GAMMA),
+                       1.0 / static_cast<double>(c->ng), nullptr, gram, stream);
 }
 
 int zeta_sort_particles(zeta_ctx* c, const float* particles, int64_t np, float* sorted, int64_t* tile_start,
@@ -233,7 +243,7 @@ int zeta_sum_particles(zeta_ctx* c, const float* sorted, const int64_t* tile_sta
   const Layout L = layout(c, 0);
   double* part = at<double>(c, L.partials);
   ZK_TRY(launch_gram_particles(c, reinterpret_cast<const float4*>(sorted), tile_start, alm, part, stream));
-  return launch_reduce(c, part, gram_ctas(c), 1.0, wsum, gram, stream);
+  return launch_reduce(c, part, gram_ctas(c, GK_PART), 1.0, wsum, gram, stream);
 }
 
 int zeta_mass_term(zeta_ctx* c, const float* delta_hat, int l, double sign, double* gram, zeta_stream stream) {
@@ -244,7 +254,7 @@ int zeta_mass_term(zeta_ctx* c, const float* delta_hat, int l, double sign, doub
   double* part = at<double>(c, L.partials);
   ZK_TRY(launch_mass(c, reinterpret_cast<const float2*>(delta_hat), l, part, stream));
   const double scale = sign * (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846);
-  return launch_reduce(c, part, gram_ctas(c), scale, nullptr, gram, stream);
+  return launch_reduce(c, part, gram_ctas(c, GK_MASS), scale, nullptr, gram, stream);
 }
 
 int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* delta, int forms, double* zeta,
@@ -281,32 +291,158 @@ int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* 
   if (want_p) idx_part = nforms++;
   const size_t per_form = static_cast<size_t>(lmax + 1) * nb * nb;
   if (cudaMemsetAsync(zeta, 0, sizeof(double) * per_form * nforms, stream) != cudaSuccess) return ZETA_ECUDA;
-  const int nparts = gram_ctas(c);
   const double inv_ng = 1.0 / static_cast<double>(c->ng);
   for (int l = 0; l <= lmax; ++l) {
     if (want_p) {
       double* out = zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb;
       ZK_TRY(launch_mass(c, dhat, l, part, stream));
-      ZK_TRY(launch_reduce(c, part, nparts, -(2.0 * l + 1.0) / (4.0 * 3.14159265358979323846), nullptr, out, stream));
+      ZK_TRY(launch_reduce(c, part, gram_ctas(c, GK_MASS), -(2.0 * l + 1.0) / (4.0 * 3.14159265358979323846), nullptr,
+                           out, stream));
     }
     for (int m = -l; m <= l; ++m) {
       ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, at<float2>(c, L.spectra), fields, stream));
       if (idx_node >= 0) {
         ZK_TRY(c->p.gram == ZETA_GRAM_FP32 ? launch_gram_node(c, dl, fields, part, stream)
                                            : launch_gram_node_tc(c, dl, fields, part, stream));
-        ZK_TRY(launch_reduce(c, part, nparts, inv_ng, nullptr, zeta + idx_node * per_form + static_cast<size_t>(l) * nb * nb, stream));
+        ZK_TRY(launch_reduce(c, part, gram_ctas(c, c->p.gram == ZETA_GRAM_FP32 ? GK_NODE : GK_TC), inv_ng, nullptr,
+                             zeta + idx_node * per_form + static_cast<size_t>(l) * nb * nb, stream));
       }
       if (idx_gamma >= 0) {
         ZK_TRY(launch_gram_gamma(c, dl, fields, part, stream));
-        ZK_TRY(launch_reduce(c, part, nparts, inv_ng, nullptr, zeta + idx_gamma * per_form + static_cast<size_t>(l) * nb * nb, stream));
+        ZK_TRY(launch_reduce(c, part, gram_ctas(c, GK_GAMMA), inv_ng, nullptr,
+                             zeta + idx_gamma * per_form + static_cast<size_t>(l) * nb * nb, stream));
       }
       if (idx_part >= 0) {
         ZK_TRY(launch_gram_particles(c, sorted, tstart, fields, part, stream));
-        ZK_TRY(launch_reduce(c, part, nparts, 1.0, wsum, zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb, stream));
+        ZK_TRY(launch_reduce(c, part, gram_ctas(c, GK_PART), 1.0, wsum,
+                             zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb, stream));
       }
     }
   }
   return ZETA_OK;
+}
+
+int zeta_batch(zeta_ctx* c, const float* particles, const int64_t* offsets, int ncat, int forms, double* zeta,
+               zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!particles || !offsets || ncat < 1 || !zeta || forms < 1 || forms > 7 || offsets[0] < 0) return ZETA_EINVAL;
+  int64_t np_max = 0;
+  for (int i = 0; i < ncat; ++i) {
+    const int64_t np = offsets[i + 1] - offsets[i];
+    if (np < 1 || np > 0x7fffffffLL) return ZETA_EINVAL;
+    if (np > np_max) np_max = np;
+  }
+  ZK_TRY(need_ws(c, (forms & ZETA_SUM_PARTICLE) ? np_max : 0));
+  std::vector<int64_t> key = {static_cast<int64_t>(reinterpret_cast<uintptr_t>(particles)),
+                              static_cast<int64_t>(reinterpret_cast<uintptr_t>(zeta)), forms, ncat};
+  key.insert(key.end(), offsets, offsets + ncat + 1);
+  if (!c->batch_exec || key != c->batch_key) {
+    drop_batch_graph(c);
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return ZETA_ECUDA;
+    int nforms = ((forms & 1) ? 1 : 0) + ((forms & 2) ? 1 : 0) + ((forms & 4) ? 1 : 0);
+    const size_t per_cat = static_cast<size_t>(nforms) * (c->p.lmax + 1) * c->p.nbins * c->p.nbins;
+    c->capturing = true;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      c->capturing = false;
+      return ZETA_ECUDA;
+    }
+    int rc = ZETA_OK;
+    for (int i = 0; i < ncat && rc == ZETA_OK; ++i)
+      rc = zeta_zeta_ell(c, particles + 4 * offsets[i], offsets[i + 1] - offsets[i], nullptr, forms,
+                         zeta + i * per_cat, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &g);
+    c->capturing = false;
+    if (rc != ZETA_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc != ZETA_OK ? rc : ZETA_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->batch_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      c->batch_exec = nullptr;
+      return ZETA_ECUDA;
+    }
+    c->batch_key = key;
+  }
+  return cudaGraphLaunch(c->batch_exec, stream) == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
+int zeta_autotune(zeta_ctx* c, const float* particles, int64_t np, int forms, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!particles || np < 1 || np > 0x7fffffffLL || forms < 1 || forms > 7) return ZETA_EINVAL;
+  const bool want_p = forms & ZETA_SUM_PARTICLE;
+  ZK_TRY(need_ws(c, want_p ? np : 0));
+  const Layout L = layout(c, want_p ? np : 0);
+  const float4* parts = reinterpret_cast<const float4*>(particles);
+  double* small = at<double>(c, L.small);
+  double* wsum = small + kAssignScratchDoubles + 4;
+  float* dl = at<float>(c, L.delta);
+  float2* dhat = at<float2>(c, L.dhat);
+  float* fields = at<float>(c, L.fields);
+  double* part = at<double>(c, L.partials);
+  float4* sorted = at<float4>(c, L.sorted);
+  int64_t* tstart = at<int64_t>(c, L.tstart);
+  // representative data: this catalogue's fields for one (l, m)
+  ZK_TRY(launch_assign(c, parts, np, dl, wsum, reinterpret_cast<unsigned long long*>(fields), small, stream));
+  ZK_TRY(launch_r2c(c, dl, dhat, stream));
+  if (want_p) ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream));
+  const int l = c->p.lmax < 2 ? c->p.lmax : 2;
+  ZK_TRY(launch_alm(c, dhat, l, 0, 0, c->p.nbins, at<float2>(c, L.spectra), fields, stream));
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return ZETA_ECUDA;
+  auto run = [&](int kind) -> int {
+    switch (kind) {
+      case GK_NODE: return launch_gram_node(c, dl, fields, part, stream);
+      case GK_TC: return launch_gram_node_tc(c, dl, fields, part, stream);
+      case GK_GAMMA: return launch_gram_gamma(c, dl, fields, part, stream);
+      case GK_PART: return launch_gram_particles(c, sorted, tstart, fields, part, stream);
+      default: return launch_mass(c, dhat, l, part, stream);
+    }
+  };
+  std::vector<int> kinds;
+  if (forms & ZETA_SUM_NODE) kinds.push_back(c->p.gram == ZETA_GRAM_FP32 ? GK_NODE : GK_TC);
+  if (forms & ZETA_SUM_GAMMA) kinds.push_back(GK_GAMMA);
+  if (want_p) {
+    kinds.push_back(GK_PART);
+    kinds.push_back(GK_MASS);
+  }
+  const int cand[] = {1, 2, 3, 4, 6, 8};
+  int rc = ZETA_OK;
+  for (int kind : kinds) {
+    float best = 1e30f;
+    int best_c = c->tune[kind];
+    for (int cc : cand) {
+      c->tune[kind] = cc;
+      if ((rc = run(kind)) != ZETA_OK) break;  // warm
+      cudaEventRecord(e0, stream);
+      for (int r = 0; r < 3 && rc == ZETA_OK; ++r) rc = run(kind);
+      cudaEventRecord(e1, stream);
+      if (rc != ZETA_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = rc ? rc : ZETA_ECUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_c = cc;
+      }
+    }
+    c->tune[kind] = best_c;
+    if (rc != ZETA_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_batch_graph(c);
+  return rc;
+}
+
+int zeta_get_tuning(const zeta_ctx* c, int* ctas_per_sm, int n) {
+  if (!c || !ctas_per_sm || n < 0) return ZETA_EINVAL;
+  for (int i = 0; i < n && i < 5; ++i) ctas_per_sm[i] = c->tune[i];
+  return 5;
 }
 
 int zeta_get_status(zeta_ctx* c, zeta_stream stream) {

@@ -273,6 +273,106 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
 }
 
 // ---------------------------------------------------------------------------------------
+// Adjoint (transpose) passes of the field reconstruction, for gradients.
+//
+// x-pass R2C of four bin-interleaved real fields (one group [z][y][x][4]) into four plain
+// half spectra without the x-Nyquist column: the half-length complex transform of
+// z[j] = (x[2j], x[2j+1]) followed by X[k] = E[k] + W_N^k O[k].  grid (n*n/RB, ngroups).
+template <int N, int RB>
+__global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
+    k_r2c_x4(const float4* __restrict__ in, int nf, float2* __restrict__ spec, long long fstride,
+             const float2* __restrict__ twg) {
+  constexpr int NC = N / 2, C = 4 * RB, PS = C + 1;
+  constexpr int NT = RegThreads<NC, C, 256>::NT;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* tw2 = sm + N;
+  float2* ex = tw2 + NC;
+  float2* res = ex + NC * PS;
+  const int g = blockIdx.y;
+  const long long r0 = static_cast<long long>(blockIdx.x) * RB;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < NC; i += blockDim.x) tw2[i] = twg[2 * i];
+  __syncthreads();
+  auto load = [&](int c, int k) -> float2 {
+    const int j = c / RB, r = c % RB;
+    const float4* row = in + (static_cast<long long>(g) * N * N + r0 + r) * N;
+    const float4 a = row[2 * k], b = row[2 * k + 1];
+    const float* fa = reinterpret_cast<const float*>(&a);
+    const float* fb = reinterpret_cast<const float*>(&b);
+    return make_float2(fa[j], fb[j]);
+  };
+  auto store = [&](int c, int k, float2 v) { res[k * PS + c] = v; };
+  fft_reg<NC, C, NT, false, true>(ex, PS, tw2, load, store);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NC * C; idx += blockDim.x) {
+    const int c = idx / NC, k = idx % NC;
+    const int f = 4 * g + c / RB;
+    if (f >= nf) continue;
+    const float2 zk = res[k * PS + c];
+    const float2 zm = cconj(res[((NC - k) & (NC - 1)) * PS + c]);
+    const float2 e = cscale(cadd(zk, zm), 0.5f);
+    const float2 dd = csub(zk, zm);
+    const float2 od = make_float2(0.5f * dd.y, -0.5f * dd.x);
+    spec[f * fstride + (r0 + c % RB) * NC + k] = cadd(e, cmul(tw[k], od));
+  }
+}
+
+// Adjoint z-pass: forward z-transform of nf x,y-transformed spectra and the transposed window,
+// gk += sum_f (-1)^l K_lm,f(n) spec_f(n) with K = i^l R_lm J_f (|n|^2) as in the forward pass.
+// grid (nc/T, n).
+template <int N, int T>
+__global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
+    k_adj_z(const float2* __restrict__ spec, long long fstride, int nf, const float4* __restrict__ jt4, int nbp4,
+            int l, int m, float2* __restrict__ gk, const float2* __restrict__ twg) {
+  constexpr int NC = N / 2;
+  constexpr int NT = RegThreads<N, T, 512>::NT;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* ex = tw + N;              // [N][T]
+  float2* acc = ex + N * T;         // [N][T] sum over fields
+  float* ang = reinterpret_cast<float*>(acc + N * T);  // [N][T]
+  int* n2 = reinterpret_cast<int*>(ang + N * T);        // [N][T]
+  const int x0 = blockIdx.x * T;
+  const int iy = blockIdx.y;
+  if (iy == N / 2) return;  // the window vanishes on the y-Nyquist plane
+  const long long colbase = static_cast<long long>(iy) * NC + x0;
+  const long long zstride = static_cast<long long>(N) * NC;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  // (-1)^l i^l = (-i)^l: real sign and one factor of -i for odd l
+  const float sgn = ((l & 3) == 0 || (l & 3) == 3) ? 1.f : -1.f;
+  const int ny = signed_freq(iy, N);
+  for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+    const int z = idx / T, c = idx % T;
+    const int nz = signed_freq(z, N), nx = x0 + c;
+    const bool nyq = (z == N / 2);
+    n2[idx] = nyq ? 0 : nx * nx + ny * ny + nz * nz;
+    ang[idx] = nyq ? 0.f : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz));
+    acc[idx] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const float* jt = reinterpret_cast<const float*>(jt4);
+  for (int f = 0; f < nf; ++f) {
+    const float2* sf = spec + f * fstride;
+    auto load = [&](int c, int z) { return sf[colbase + z * zstride + c]; };
+    auto store = [&](int c, int z, float2 v) {
+      const int idx = z * T + c;
+      const float a = ang[idx] * __ldg(jt + static_cast<long long>(n2[idx]) * 4 * nbp4 + f);
+      acc[idx] = cadd(acc[idx], cscale(v, a));
+    };
+    fft_reg<N, T, NT, false, false>(ex, T, tw, load, store);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
+    const int z = idx / T, c = idx % T;
+    float2 v = acc[idx];
+    if (l & 1) v = make_float2(v.y, -v.x);  // times -i
+    float2* o = gk + colbase + z * zstride + c;
+    *o = cadd(*o, v);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 namespace {
 
 constexpr int kTz = 8;   // columns per z-pass (window) tile
@@ -282,12 +382,7 @@ constexpr int kRB4 = 4;  // rows per four-field x-pass tile
 
 template <typename K>
 int set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) !=
-        cudaSuccess)
-      return ZETA_ECUDA;
-  }
-  return ZETA_OK;
+  return ensure_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 inline int check_launch() { return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA; }
@@ -395,6 +490,37 @@ int launch_r2c(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t
 int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
                cudaStream_t s) {
 #define ZK_CALL(NN) alm_impl<NN>(c, dhat, l, m, b0, nf, spec, out, s)
+  ZK_DISPATCH_N(c->n, ZK_CALL)
+#undef ZK_CALL
+}
+
+template <int N>
+int adj_impl(const zeta_ctx* c, const float* fields, int nf, float2* spec, int l, int m, float2* gk, cudaStream_t s) {
+  constexpr int NC = N / 2;
+  constexpr int TY = kTy < NC ? kTy : NC;
+  constexpr int TZ = kTz < NC ? kTz : NC;
+  constexpr int RB = kRB4;
+  const long long fstride = static_cast<long long>(N) * N * NC;
+  StageScope prof(c, ST_ADJ_FFT, 3, s);
+  const size_t smx = (N + NC + 2 * NC * (4 * RB + 1)) * sizeof(float2);
+  if (set_smem(k_r2c_x4<N, RB>, smx)) return ZETA_ECUDA;
+  k_r2c_x4<N, RB><<<dim3(N * N / RB, (nf + 3) / 4), RegThreads<N / 2, 4 * RB, 256>::NT, smx, s>>>(
+      reinterpret_cast<const float4*>(fields), nf, spec, fstride, c->d_tw);
+  const size_t sma = (N + N * TY) * sizeof(float2);
+  if (set_smem(k_fft_axis<N, TY, false, 1>, sma)) return ZETA_ECUDA;
+  k_fft_axis<N, TY, false, 1><<<dim3(NC / TY, N, nf), RegThreads<N, TY, 512>::NT, sma, s>>>(spec, fstride, c->d_tw);
+  const size_t smz = (N + 2 * static_cast<size_t>(N) * TZ) * sizeof(float2) + 2 * static_cast<size_t>(N) * TZ * 4;
+  if (set_smem(k_adj_z<N, TZ>, smz)) return ZETA_ECUDA;
+  const int nbp4 = (c->p.nbins + 3) / 4;
+  const float4* jt4 = reinterpret_cast<const float4*>(c->d_jtab) + static_cast<long long>(l) * c->nn2 * nbp4;
+  k_adj_z<N, TZ><<<dim3(NC / TZ, N), RegThreads<N, TZ, 512>::NT, smz, s>>>(spec, fstride, nf, jt4, nbp4, l, m, gk,
+                                                                          c->d_tw);
+  return check_launch();
+}
+
+int launch_adj_spectral(const zeta_ctx* c, const float* fields, int nf, float2* spec, int l, int m, float2* gk,
+                        cudaStream_t s) {
+#define ZK_CALL(NN) adj_impl<NN>(c, fields, nf, spec, l, m, gk, s)
   ZK_DISPATCH_N(c->n, ZK_CALL)
 #undef ZK_CALL
 }

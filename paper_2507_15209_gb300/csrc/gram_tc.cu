@@ -298,10 +298,8 @@ template <int MODE>
 int tc_impl(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
   using T = TcT<MODE>;
   const size_t sm = 2 * T::SPLIT * static_cast<size_t>(kM + kN) * kKT * T::ES;
-  if (cudaFuncSetAttribute(k_gram_node_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)) !=
-      cudaSuccess)
-    return ZETA_ECUDA;
-  k_gram_node_tc<MODE><<<gram_ctas(c), kTcThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
+  if (ensure_smem(reinterpret_cast<const void*>(k_gram_node_tc<MODE>), sm) != ZETA_OK) return ZETA_ECUDA;
+  k_gram_node_tc<MODE><<<gram_ctas(c, GK_TC), kTcThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
                                                             c->p.nbins, partials, c->d_status);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }

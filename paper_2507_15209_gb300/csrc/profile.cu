@@ -1,8 +1,24 @@
 // Stage timers: a CUDA event pair around every kernel group when profiling is on, read back
 // (after a synchronisation) as total milliseconds, kernel launches and calls per stage.
+#include <mutex>
+#include <unordered_map>
+
 #include "zeta_internal.h"
 
 namespace zk {
+
+int ensure_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> done;
+  if (bytes <= 48 * 1024) return ZETA_OK;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find(kernel);
+  if (it != done.end() && it->second >= bytes) return ZETA_OK;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) != cudaSuccess)
+    return ZETA_ECUDA;
+  done[kernel] = bytes;
+  return ZETA_OK;
+}
 namespace {
 
 cudaEvent_t take_event(Profiler& p) {
@@ -16,8 +32,9 @@ cudaEvent_t take_event(Profiler& p) {
   return e;
 }
 
-const char* kNames[ST_COUNT] = {"assign",     "sort",        "r2c",            "alm_z",  "alm_y", "alm_x",
-                                "gram_node",  "gram_gamma",  "gram_particles", "mass",   "reduce"};
+const char* kNames[ST_COUNT] = {"assign",    "sort",      "r2c",       "alm_z",     "alm_y",     "alm_x",
+                                "gram_node", "gram_gamma", "gram_particles", "mass", "reduce", "adj_points",
+                                "adj_fft",   "adj_other"};
 
 }  // namespace
 
@@ -26,14 +43,14 @@ StageScope::StageScope(const zeta_ctx* c, int stage, int nkernels, cudaStream_t 
   Profiler& p = c_->prof;
   p.launches[stage_] += nk_;
   p.calls[stage_] += 1;
-  if (!p.on) return;
+  if (!p.on || c_->capturing) return;
   a_ = take_event(p);
   if (a_) cudaEventRecord(a_, s_);
 }
 
 StageScope::~StageScope() {
   Profiler& p = c_->prof;
-  if (!p.on || !a_) return;
+  if (!p.on || !a_ || c_->capturing) return;
   cudaEvent_t b = take_event(p);
   if (!b) {
     p.pool.push_back(a_);

@@ -399,9 +399,7 @@ size_t smem_points() {
 
 template <typename K>
 int prep(K kernel, size_t bytes) {
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) != cudaSuccess)
-    return ZETA_ECUDA;
-  return ZETA_OK;
+  return ensure_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 template <int NBP>
@@ -409,7 +407,7 @@ int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* p
   StageScope prof(c, ST_GRAM_NODE, 1, s);
   const size_t sm = smem_node<NBP>();
   if (prep(k_gram_node<NBP>, sm)) return ZETA_ECUDA;
-  k_gram_node<NBP><<<gram_ctas(c), kThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
+  k_gram_node<NBP><<<gram_ctas(c, GK_NODE), kThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
                                                      c->p.nbins, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
@@ -420,7 +418,7 @@ int points_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_sta
   StageScope prof(c, MODE == 0 ? ST_GRAM_PART : ST_GRAM_GAMMA, 1, s);
   const size_t sm = smem_points<NBP, D>();
   if (prep(k_gram_points<NBP, D, MODE>, sm)) return ZETA_ECUDA;
-  k_gram_points<NBP, D, MODE><<<gram_ctas(c), kThreads, sm, s>>>(
+  k_gram_points<NBP, D, MODE><<<gram_ctas(c, MODE == 0 ? GK_PART : GK_GAMMA), kThreads, sm, s>>>(
       sorted, reinterpret_cast<const long long*>(tile_start), delta, reinterpret_cast<const float4*>(alm), c->ng,
       c->n, c->p.nbins, c->n / c->p.box,
       c->d_gq, c->gamma_q, partials);
@@ -433,7 +431,7 @@ int mass_impl(const zeta_ctx* c, const float2* dhat, int l, double* partials, cu
   const size_t sm = smem_mass<NBP>();
   if (prep(k_gram_mass<NBP>, sm)) return ZETA_ECUDA;
   const float* jt = c->d_jtab + static_cast<long long>(l) * c->nn2 * (4 * ((c->p.nbins + 3) / 4));
-  k_gram_mass<NBP><<<gram_ctas(c), kThreads, sm, s>>>(dhat, jt, c->nn2, c->d_mhat, c->n, c->p.nbins, partials);
+  k_gram_mass<NBP><<<gram_ctas(c, GK_MASS), kThreads, sm, s>>>(dhat, jt, c->nn2, c->d_mhat, c->n, c->p.nbins, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
@@ -441,8 +439,10 @@ inline int nbp_of(int nb) { return nb <= 8 ? 8 : nb <= 16 ? 16 : nb <= 24 ? 24 :
 
 }  // namespace
 
-int gram_ctas(const zeta_ctx* c) {
-  int g = c->num_sms * 4;
+int gram_ctas(const zeta_ctx* c, int kind) {
+  int per = c->tune[kind];
+  if (per < 1) per = 1;
+  int g = c->num_sms * per;
   return g > kMaxCtas ? kMaxCtas : g;
 }
 

@@ -41,7 +41,7 @@ void host_cell_quadrature(int q, int dsup, std::vector<double>& t, std::vector<d
 // ---- stage timers (profile.cu): CUDA events around every kernel group ----
 enum Stage {
   ST_ASSIGN = 0, ST_SORT, ST_R2C, ST_ALM_Z, ST_ALM_Y, ST_ALM_X, ST_GRAM_NODE, ST_GRAM_GAMMA, ST_GRAM_PART,
-  ST_MASS, ST_REDUCE, ST_COUNT
+  ST_MASS, ST_REDUCE, ST_ADJ_POINT, ST_ADJ_FFT, ST_ADJ_OTHER, ST_COUNT
 };
 struct Profiler {
   bool on = false;
@@ -78,6 +78,13 @@ struct zeta_ctx {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   mutable zk::Profiler prof;
+  // persistent-grid size of each Gram kind, in CTAs per SM (set by zeta_autotune)
+  int tune[5] = {4, 4, 4, 4, 4};
+  // CUDA graph of the last batch (zeta_batch)
+  bool capturing = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t batch_exec = nullptr;
+  std::vector<int64_t> batch_key;
 };
 
 namespace zk {
@@ -97,6 +104,9 @@ class StageScope {
   cudaEvent_t a_ = nullptr;
 };
 void profile_release(const zeta_ctx* c);
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, calling the runtime only the
+// first time a kernel needs more (so later launches can be captured into a CUDA graph).
+int ensure_smem(const void* kernel, size_t bytes);
 
 // ---- launchers (fft.cu) ----
 int set_ylm_constants();
@@ -105,6 +115,10 @@ int launch_r2c(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t
 // ceil(nf/4) bin-interleaved groups [g][z][y][x][4].
 int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
                cudaStream_t s);
+// Adjoint of the reconstruction for nf bin-interleaved real fields h_b (bins 0..nf-1):
+// gk += sum_b (-1)^l K_lm,b DFT(h_b); spec is scratch for nf half spectra.
+int launch_adj_spectral(const zeta_ctx* c, const float* fields, int nf, float2* spec, int l, int m, float2* gk,
+                        cudaStream_t s);
 // Inverse-only helpers reused by other stages: C2R of nf half spectra in place.
 int launch_c2r_inplace(const zeta_ctx* c, float2* data, int nf, cudaStream_t s);
 
@@ -117,7 +131,8 @@ int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sort
                 int* counts, int* orig, cudaStream_t s);
 
 // ---- launchers (sums.cu) ----
-int gram_ctas(const zeta_ctx* c);
+enum GramKind { GK_NODE = 0, GK_PART = 1, GK_GAMMA = 2, GK_MASS = 3, GK_TC = 4 };
+int gram_ctas(const zeta_ctx* c, int kind);
 int launch_gram_node(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
 int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, double* partials,
                       cudaStream_t s);

@@ -25,6 +25,7 @@ __all__ = [
     "uniform_particles",
     "lognormal_catalogue",
     "batch_sizes",
+    "loss_weights",
 ]
 
 
@@ -103,6 +104,12 @@ def lognormal_catalogue(n: int, n_p: int, box: float, field_seed: int, sample_se
     """Log-normal mock catalogue on an n^3 density grid (float32 (n_p, 4))."""
     rho = lognormal_density(n, field_seed)
     return sample_particles(rho, n_p, box, sample_seed)
+
+
+def loss_weights(lmax: int, nbins: int, seed: int) -> np.ndarray:
+    """Gaussian weights w[l, i, j] of the scalar loss L = sum w * zeta_l(r_i, r_j)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal((lmax + 1, nbins, nbins))
 
 
 def batch_sizes(n_cat: int, lo: int, hi: int, seed: int) -> np.ndarray:

@@ -53,6 +53,9 @@ _SIGS = {
     "zeta_mass_term": ([_VP, _VP, _INT, _DBL, _VP, _VP], _INT),
     "zeta_zeta_ell": ([_VP, _VP, _I64, _VP, _INT, _VP, _VP], _INT),
     "zeta_get_status": ([_VP, _VP], _INT),
+    "zeta_batch": ([_VP, _VP, _VP, _INT, _INT, _VP, _VP], _INT),
+    "zeta_autotune": ([_VP, _VP, _I64, _INT, _VP], _INT),
+    "zeta_get_tuning": ([_VP, _VP, _INT], _INT),
     "zeta_assign_noalloc": ([_INT, _DBL, _INT, _VP, _I64, _VP, _VP, _VP], _INT),
     "zeta_profile_enable": ([_VP, _INT], _INT),
     "zeta_profile_read": ([_VP, _VP, _VP, _VP, _INT], _INT),
@@ -273,6 +276,34 @@ class Context:
         if k < 0:
             raise ZetaError("zeta_profile_read", k)
         return {lib().zeta_profile_stage_name(i).decode(): (float(ms[i]), int(nl[i]), int(nc[i])) for i in range(k)}
+
+    def batch(self, particles, offsets, forms=("particle",), out=None):
+        """zeta_batch: catalogues particles[offsets[i]:offsets[i+1]] in one CUDA-graph launch.
+
+        Returns a tensor (ncat, nforms, lmax+1, nb, nb); keep `offsets` and `out` to reuse the
+        captured graph on later calls."""
+        import torch
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        ncat = len(offs) - 1
+        bits = self.form_bits(forms)
+        nforms = bin(bits).count("1")
+        if out is None:
+            out = torch.empty((ncat, nforms, self.lmax + 1, self.nbins, self.nbins), dtype=torch.float64,
+                              device="cuda")
+        self._batch_offsets = offs  # the library keeps a copy; hold ours for the caller's reuse
+        _check("zeta_batch", lib().zeta_batch(self._h, _ptr(particles), offs.ctypes.data, ncat, bits, _ptr(out),
+                                              _stream()))
+        return out
+
+    def autotune(self, particles, forms=("particle",)) -> list:
+        _check("zeta_autotune", lib().zeta_autotune(self._h, _ptr(particles), particles.shape[0],
+                                                    self.form_bits(forms), _stream()))
+        return self.tuning()
+
+    def tuning(self) -> list:
+        t = np.zeros(5, np.int32)
+        lib().zeta_get_tuning(self._h, t.ctypes.data, 5)
+        return [int(x) for x in t]
 
     def get_status(self) -> int:
         return lib().zeta_get_status(self._h, _stream())

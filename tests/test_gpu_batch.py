@@ -1,0 +1,68 @@
+"""Batched measurement (zeta_batch, one CUDA-graph launch for many catalogues of uneven
+size) and the persistent-grid autotuner, on the GPU."""
+import numpy as np
+import pytest
+
+from oracle import zeta_oracle as O
+from paper_2507_15209_gb300 import mocks
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def Z():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_15209_gb300 import build
+    build.build()
+    from paper_2507_15209_gb300 import zeta
+    return zeta
+
+
+def _cats(n, box, sizes, seed0):
+    return [mocks.lognormal_catalogue(n, int(s), box, seed0 + 2 * i, seed0 + 2 * i + 1) for i, s in enumerate(sizes)]
+
+
+def test_batch_equals_one_by_one_and_replays(Z):
+    n, box, lmax, dsup = 32, 200.0, 3, 4
+    edges = np.linspace(10.0, 70.0, 6)
+    sizes = mocks.batch_sizes(5, 800, 9000, 77)
+    cats = _cats(n, box, sizes, 500)
+    allp = np.concatenate(cats)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    forms = ("node", "particle")
+    ctx = Z.Context(n, box, dsup, lmax, edges, np_max=int(sizes.max()), forms=forms)
+    dev = torch.from_numpy(allp).to("cuda")
+    out = ctx.batch(dev, offs, forms=forms)
+    again = ctx.batch(dev, offs, forms=forms, out=out.clone())  # new output pointer: re-captured
+    replay = ctx.batch(dev, offs, forms=forms, out=out)          # same key: cached graph relaunched
+    torch.cuda.synchronize()
+    assert ctx.get_status() == 0
+    for i, p in enumerate(cats):
+        one = ctx.zeta_ell(particles=torch.from_numpy(p).to("cuda"), forms=forms)
+        for k, f in enumerate(("node", "particle")):
+            np.testing.assert_array_equal(out[i, k].cpu().numpy(), one[f].cpu().numpy())
+            np.testing.assert_array_equal(again[i, k].cpu().numpy(), one[f].cpu().numpy())
+    # the first catalogue against the FP64 oracle
+    want, _ = O.zeta_multipoles(cats[0].astype(np.float64), n, box, edges, lmax, dsup, forms=forms)
+    for k, f in enumerate(("node", "particle")):
+        got = replay[0, k].cpu().numpy()
+        for l in range(lmax + 1):
+            err = np.linalg.norm(got[l] - want[f][l]) / np.linalg.norm(want[f][l])
+            assert err < 1e-5, (f, l, err)
+
+
+def test_autotune_keeps_results(Z):
+    n, box, lmax, dsup = 32, 200.0, 2, 4
+    edges = np.linspace(10.0, 70.0, 5)
+    p = torch.from_numpy(mocks.lognormal_catalogue(n, 20000, box, 91, 92)).to("cuda")
+    forms = ("node", "particle")
+    ctx = Z.Context(n, box, dsup, lmax, edges, np_max=20000, forms=forms)
+    before = {f: v.cpu().numpy() for f, v in ctx.zeta_ell(particles=p, forms=forms).items()}
+    tune = ctx.autotune(p, forms=forms)
+    assert len(tune) == 5 and all(1 <= t <= 8 for t in tune)
+    after = {f: v.cpu().numpy() for f, v in ctx.zeta_ell(particles=p, forms=forms).items()}
+    for f in forms:  # only the partition of points among CTAs changed: rounding-level differences
+        np.testing.assert_allclose(after[f], before[f], rtol=1e-9, atol=1e-12 * np.abs(before[f]).max())

@@ -422,3 +422,53 @@ def test_raw_reading_converges_to_brute_force():
         errs.append(np.abs(z["particle"] - ref).max() / np.abs(ref).max())
     assert errs[2] < errs[1] < errs[0]
     assert errs[0] / errs[2] > 2.5
+
+
+# --- gradients: central finite differences of the FP64 loss --------------------------------
+def test_bspline_derivative_matches_finite_difference():
+    u = np.linspace(-2.3, 2.3, 97) + 1e-3
+    for dsup in (2, 4):
+        fd = (O.bspline(u + 1e-6, dsup) - O.bspline(u - 1e-6, dsup)) / 2e-6
+        np.testing.assert_allclose(O.bspline_deriv(u, dsup), fd, atol=1e-6)
+
+
+def test_node_gradient_matches_finite_differences():
+    n, box, lmax = 8, 60.0, 2
+    edges = np.array([7.0, 14.0, 22.0])
+    rng = np.random.default_rng(21)
+    delta = rng.standard_normal((n, n, n))
+    wts = rng.standard_normal((lmax + 1, 2, 2))
+
+    def lossf(d):
+        z, _ = O.zeta_from_delta(d, n, box, edges, lmax, 2, forms=("node",))
+        return O.loss(z["node"], wts)
+
+    g = O.grad_node_delta(delta, wts, n, box, edges, lmax)
+    for k in range(3):
+        v = rng.standard_normal((n, n, n))
+        e = 1e-4
+        fd = (lossf(delta + e * v) - lossf(delta - e * v)) / (2 * e)
+        assert abs(fd - float((g * v).sum())) < 1e-7 * max(1.0, abs(fd)), (fd, float((g * v).sum()))
+
+
+def test_particle_position_gradient_matches_finite_differences():
+    n, box, lmax, dsup = 8, 40.0, 2, 4
+    edges = np.array([5.0, 10.0, 17.0])
+    rng = np.random.default_rng(22)
+    parts = np.empty((150, 4))
+    parts[:, :3] = rng.uniform(0, box, (150, 3))
+    parts[:, 3] = rng.uniform(0.5, 1.5, 150)
+    wts = rng.standard_normal((lmax + 1, 2, 2))
+
+    def lossf(p):
+        z, _ = O.zeta_multipoles(p, n, box, edges, lmax, dsup, forms=("particle",))
+        return O.loss(z["particle"], wts)
+
+    g = O.grad_particle_positions(parts, wts, n, box, edges, lmax, dsup)
+    for pi, d in [(0, 0), (3, 1), (17, 2), (88, 0), (149, 2)]:
+        e = 1e-4
+        pp, pm = parts.copy(), parts.copy()
+        pp[pi, d] += e
+        pm[pi, d] -= e
+        fd = (lossf(pp) - lossf(pm)) / (2 * e)
+        assert abs(fd - g[pi, d]) < 1e-6 * max(1.0, np.abs(g).max()), (pi, d, fd, g[pi, d])
