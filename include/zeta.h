@@ -74,8 +74,8 @@ enum {
   ZETA_EDATA = -7       /* device found invalid input data (non-finite particle)    */
 };
 
-/* Summation forms (bit mask). */
-enum { ZETA_SUM_NODE = 1, ZETA_SUM_GAMMA = 2, ZETA_SUM_PARTICLE = 4 };
+/* Summation forms (bit mask).  ZETA_WS_BACKWARD only sizes the workspace for the gradient calls. */
+enum { ZETA_SUM_NODE = 1, ZETA_SUM_GAMMA = 2, ZETA_SUM_PARTICLE = 4, ZETA_WS_BACKWARD = 8 };
 
 /* Arithmetic of the node-form Gram contraction (Sec. 2.2 grid sum). */
 enum {
@@ -175,6 +175,21 @@ int zeta_mass_term(zeta_ctx* ctx, const float* delta_hat, int l, double sign, do
  * the order NODE, GAMMA, PARTICLE among those requested. */
 int zeta_zeta_ell(zeta_ctx* ctx, const float* particles, int64_t np, const float* delta, int forms,
                   double* zeta, zeta_stream stream);
+
+/* Gradients of L = sum_l sum_ij W_l[i][j] zeta_l[i][j] (weights: host double
+ * [(lmax+1) * nbins * nbins]), by the transpose of every step with per-(l, m) recomputation of
+ * the fields (nothing per (l, m) is stored).  With S_l = (W_l + W_l^T)/2, A_b the map delta ->
+ * a_lm,b and A_b^T = (-1)^l IDFT diag(K_lm,b) DFT:
+ *   zeta_backward_node:      grad = dL/d delta of the node form for the contrast grid delta
+ *                            (device float[n^3] in and out);
+ *   zeta_backward_particles: grad = dL/dx_p of the particle form with delta assigned from the
+ *                            same particles (device float[np * 3] out, original order; the
+ *                            weights w_p are held fixed).
+ * The workspace must be sized with ZETA_WS_BACKWARD.  The particle scatter uses float atomics,
+ * so that gradient is reproducible to float32 rounding only. */
+int zeta_backward_node(zeta_ctx* ctx, const float* delta, const double* weights, float* grad, zeta_stream stream);
+int zeta_backward_particles(zeta_ctx* ctx, const float* particles, int64_t np, const double* weights, float* grad,
+                            zeta_stream stream);
 
 /* Many catalogues in one launch: catalogue i is particles[offsets[i] .. offsets[i+1]) (device
  * float4, concatenated; offsets is a host array of ncat+1 increasing values, each catalogue

@@ -16,11 +16,14 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
   size_t delta = 0, dhat = 0, spectra = 0, fields = 0, partials = 0, small = 0, sorted = 0, tstart = 0, counts = 0,
          orig = 0;
+  // backward (gradient) regions
+  size_t gk = 0, q = 0, wts = 0, hfield = 0, direct = 0, sidx = 0;
   size_t total = 0;
 };
 
-// Workspace regions of the full measurement for np particles (np may be 0).
-Layout layout(const zeta_ctx* c, int64_t np) {
+// Workspace regions of the full measurement for np particles (np may be 0); with backward,
+// also the regions of the gradient calls (placed after the forward ones).
+Layout layout(const zeta_ctx* c, int64_t np, bool backward = false) {
   Layout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -39,6 +42,14 @@ Layout layout(const zeta_ctx* c, int64_t np) {
   L.tstart = take(sizeof(int64_t) * static_cast<size_t>(c->ntiles + 1));
   L.counts = take(sizeof(int) * static_cast<size_t>(c->ntiles));
   L.orig = take(sizeof(int) * static_cast<size_t>(np));
+  if (backward) {
+    L.gk = take(g);
+    L.q = take(g);
+    L.wts = take(sizeof(float) * (kMaxL + 1) * kMaxBins * kMaxBins);
+    L.hfield = take(g * 4 * ((c->p.nbins + 3) / 4));
+    L.direct = take(sizeof(float) * 3 * static_cast<size_t>(np));
+    L.sidx = take(sizeof(int) * static_cast<size_t>(np));
+  }
   L.total = off;
   return L;
 }
@@ -47,9 +58,9 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int check_ctx(const zeta_ctx* c) { return c ? ZETA_OK : ZETA_EINVAL; }
 
-int need_ws(const zeta_ctx* c, int64_t np) {
+int need_ws(const zeta_ctx* c, int64_t np, bool backward = false) {
   if (!c->ws) return ZETA_EWORKSPACE;
-  if (layout(c, np).total > c->ws_bytes) return ZETA_EWORKSPACE;
+  if (layout(c, np, backward).total > c->ws_bytes) return ZETA_EWORKSPACE;
   return ZETA_OK;
 }
 
@@ -166,8 +177,8 @@ int zeta_destroy(zeta_ctx* c) {
 }
 
 size_t zeta_workspace_bytes(const zeta_ctx* c, int64_t np_max, int forms) {
-  if (!c || np_max < 0 || np_max > 0x7fffffffLL || forms < 0 || forms > 7) return 0;
-  return layout(c, np_max).total;
+  if (!c || np_max < 0 || np_max > 0x7fffffffLL || forms < 0 || forms > 15) return 0;
+  return layout(c, np_max, (forms & ZETA_WS_BACKWARD) != 0).total;
 }
 
 int zeta_set_workspace(zeta_ctx* c, void* dptr, size_t bytes) {
@@ -443,6 +454,99 @@ int zeta_get_tuning(const zeta_ctx* c, int* ctas_per_sm, int n) {
   if (!c || !ctas_per_sm || n < 0) return ZETA_EINVAL;
   for (int i = 0; i < n && i < 5; ++i) ctas_per_sm[i] = c->tune[i];
   return 5;
+}
+
+}  // extern "C"
+
+namespace {
+// S_l = (W_l + W_l^T) / 2 as float, uploaded to the workspace
+int upload_weights(zeta_ctx* c, const double* w, float* dst, cudaStream_t s) {
+  const int nb = c->p.nbins, L1 = c->p.lmax + 1;
+  std::vector<float> h(static_cast<size_t>(L1) * nb * nb);
+  for (int l = 0; l < L1; ++l)
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        const double a = w[(static_cast<size_t>(l) * nb + i) * nb + j], b = w[(static_cast<size_t>(l) * nb + j) * nb + i];
+        if (!std::isfinite(a)) return ZETA_EINVAL;
+        h[(static_cast<size_t>(l) * nb + i) * nb + j] = static_cast<float>(0.5 * (a + b));
+      }
+  if (cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess) return ZETA_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+}  // namespace
+
+extern "C" {
+
+int zeta_backward_node(zeta_ctx* c, const float* delta, const double* weights, float* grad, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!delta || !weights || !grad) return ZETA_EINVAL;
+  ZK_TRY(need_ws(c, 0, true));
+  const Layout L = layout(c, 0, true);
+  const int nb = c->p.nbins;
+  float* S = at<float>(c, L.wts);
+  ZK_TRY(upload_weights(c, weights, S, stream));
+  float2* dhat = at<float2>(c, L.dhat);
+  float2* gk = at<float2>(c, L.gk);
+  float* q = at<float>(c, L.q);
+  float* fields = at<float>(c, L.fields);
+  float2* spec = at<float2>(c, L.spectra);
+  ZK_TRY(launch_r2c(c, delta, dhat, stream));
+  if (cudaMemsetAsync(q, 0, sizeof(float) * c->ng, stream) != cudaSuccess ||
+      cudaMemsetAsync(gk, 0, sizeof(float) * c->ng, stream) != cudaSuccess)
+    return ZETA_ECUDA;
+  for (int l = 0; l <= c->p.lmax; ++l) {
+    const float* Sl = S + static_cast<size_t>(l) * nb * nb;
+    for (int m = -l; m <= l; ++m) {
+      ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, spec, fields, stream));
+      ZK_TRY(launch_adj_node_point(c, delta, fields, Sl, q, stream));
+      ZK_TRY(launch_adj_spectral(c, fields, nb, spec, l, m, gk, stream));
+    }
+  }
+  ZK_TRY(launch_c2r_inplace(c, gk, 1, stream));
+  return launch_adj_finish_node(c, q, reinterpret_cast<float*>(gk), grad, stream);
+}
+
+int zeta_backward_particles(zeta_ctx* c, const float* particles, int64_t np, const double* weights, float* grad,
+                            zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!particles || np < 1 || np > 0x7fffffffLL || !weights || !grad) return ZETA_EINVAL;
+  ZK_TRY(need_ws(c, np, true));
+  const Layout L = layout(c, np, true);
+  const int nb = c->p.nbins;
+  float* S = at<float>(c, L.wts);
+  ZK_TRY(upload_weights(c, weights, S, stream));
+  const float4* parts = reinterpret_cast<const float4*>(particles);
+  double* small = at<double>(c, L.small);
+  double* wsum = small + kAssignScratchDoubles + 4;
+  float* dl = at<float>(c, L.delta);
+  float2* dhat = at<float2>(c, L.dhat);
+  float* fields = at<float>(c, L.fields);
+  float2* spec = at<float2>(c, L.spectra);
+  float4* sorted = at<float4>(c, L.sorted);
+  int64_t* tstart = at<int64_t>(c, L.tstart);
+  int* sidx = at<int>(c, L.sidx);
+  float2* gk = at<float2>(c, L.gk);
+  float* hfield = at<float>(c, L.hfield);
+  float* direct = at<float>(c, L.direct);
+  const size_t hbytes = sizeof(float) * c->ng * 4 * ((nb + 3) / 4);
+  ZK_TRY(launch_assign(c, parts, np, dl, wsum, reinterpret_cast<unsigned long long*>(fields), small, stream));
+  ZK_TRY(launch_r2c(c, dl, dhat, stream));
+  ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream, sidx));
+  if (cudaMemsetAsync(gk, 0, sizeof(float) * c->ng, stream) != cudaSuccess ||
+      cudaMemsetAsync(direct, 0, sizeof(float) * 3 * np, stream) != cudaSuccess)
+    return ZETA_ECUDA;
+  for (int l = 0; l <= c->p.lmax; ++l) {
+    const float* Sl = S + static_cast<size_t>(l) * nb * nb;
+    ZK_TRY(launch_adj_mass(c, dhat, l, Sl, gk, stream));
+    for (int m = -l; m <= l; ++m) {
+      ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, spec, fields, stream));
+      if (cudaMemsetAsync(hfield, 0, hbytes, stream) != cudaSuccess) return ZETA_ECUDA;
+      ZK_TRY(launch_adj_points(c, sorted, tstart, sidx, fields, Sl, wsum, hfield, direct, stream));
+      ZK_TRY(launch_adj_spectral(c, hfield, nb, spec, l, m, gk, stream));
+    }
+  }
+  ZK_TRY(launch_c2r_inplace(c, gk, 1, stream));
+  return launch_adj_finish_particles(c, parts, np, reinterpret_cast<float*>(gk), wsum, direct, grad, stream);
 }
 
 int zeta_get_status(zeta_ctx* c, zeta_stream stream) {

@@ -210,7 +210,7 @@ __global__ void k_tile_scatter(const float4* __restrict__ p, long long np, int n
 
 // One warp per tile: rank every entry by its original index and gather the particles.
 __global__ void k_tile_order(const float4* __restrict__ p, const long long* __restrict__ start, long long ntiles,
-                             const int* __restrict__ orig, float4* __restrict__ sorted) {
+                             const int* __restrict__ orig, float4* __restrict__ sorted, int* __restrict__ sorted_idx) {
   const long long warp = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= ntiles) return;
@@ -221,6 +221,7 @@ __global__ void k_tile_order(const float4* __restrict__ p, const long long* __re
     int rank = 0;
     for (int j = 0; j < c; ++j) rank += (orig[s + j] < v);
     sorted[s + rank] = p[v];
+    if (sorted_idx) sorted_idx[s + rank] = v;
   }
 }
 
@@ -261,7 +262,7 @@ int launch_wsum(const zeta_ctx* c, const float4* parts, int64_t np, double* wsum
 }
 
 int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sorted, int64_t* tile_start,
-                int* counts, int* orig, cudaStream_t s) {
+                int* counts, int* orig, cudaStream_t s, int* sorted_idx) {
   StageScope prof(c, ST_SORT, 4, s);
   const double inv_h = c->n / c->p.box;
   if (cudaMemsetAsync(counts, 0, sizeof(int) * c->ntiles, s) != cudaSuccess) return ZETA_ECUDA;
@@ -271,7 +272,8 @@ int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sort
   k_tile_scan<<<1, 1024, 0, s>>>(counts, c->ntiles, st);
   k_tile_scatter<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, st, counts, orig);
   const long long warps = c->ntiles;
-  k_tile_order<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, s>>>(parts, st, c->ntiles, orig, sorted);
+  k_tile_order<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, s>>>(parts, st, c->ntiles, orig, sorted,
+                                                                             sorted_idx);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 

@@ -339,8 +339,8 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
   const long long colbase = static_cast<long long>(iy) * NC + x0;
   const long long zstride = static_cast<long long>(N) * NC;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-  // (-1)^l i^l = (-i)^l: real sign and one factor of -i for odd l
-  const float sgn = ((l & 3) == 0 || (l & 3) == 3) ? 1.f : -1.f;
+  // (-1)^l i^l = (-i)^l = sgn * (-i)^(l mod 2): sgn = +1 for l mod 4 in {0, 1}, -1 otherwise
+  const float sgn = ((l & 3) < 2) ? 1.f : -1.f;
   const int ny = signed_freq(iy, N);
   for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
     const int z = idx / T, c = idx % T;

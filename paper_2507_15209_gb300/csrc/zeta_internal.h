@@ -127,8 +127,21 @@ int launch_assign(const zeta_ctx* c, const float4* parts, int64_t np, float* del
                   unsigned long long* acc, double* scratch2, cudaStream_t s);
 int launch_wsum(const zeta_ctx* c, const float4* parts, int64_t np, double* wsum, double* scratch, cudaStream_t s);
 constexpr int kAssignScratchDoubles = 2 * 1024 + 4;
+// sorted_idx (optional): original index of each sorted particle
 int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sorted, int64_t* tile_start,
-                int* counts, int* orig, cudaStream_t s);
+                int* counts, int* orig, cudaStream_t s, int* sorted_idx = nullptr);
+
+// ---- adjoint (adjoint.cu) ----
+// S: symmetrised loss weights of one l, device float [nb][nb]
+int launch_adj_node_point(const zeta_ctx* c, const float* delta, float* fields, const float* S, float* q,
+                          cudaStream_t s);
+int launch_adj_mass(const zeta_ctx* c, const float2* dhat, int l, const float* S, float2* gk, cudaStream_t s);
+int launch_adj_points(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, const int* sorted_idx,
+                      const float* fields, const float* S, const double* wsum, float* hfield, float* direct,
+                      cudaStream_t s);
+int launch_adj_finish_node(const zeta_ctx* c, const float* q, const float* g, float* grad, cudaStream_t s);
+int launch_adj_finish_particles(const zeta_ctx* c, const float4* parts, int64_t np, const float* gdelta,
+                                const double* wsum, const float* direct, float* grad, cudaStream_t s);
 
 // ---- launchers (sums.cu) ----
 enum GramKind { GK_NODE = 0, GK_PART = 1, GK_GAMMA = 2, GK_MASS = 3, GK_TC = 4 };

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libzeta.so")
 
 SUM_NODE, SUM_GAMMA, SUM_PARTICLE = 1, 2, 4
 GRAM = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
-FORM_BITS = {"node": SUM_NODE, "gamma": SUM_GAMMA, "particle": SUM_PARTICLE}
+FORM_BITS = {"node": SUM_NODE, "gamma": SUM_GAMMA, "particle": SUM_PARTICLE, "backward": 8}
 _ERR = {0: "ok", -1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ETIMEOUT", -5: "ENOTSUP", -6: "EWORKSPACE",
         -7: "EDATA"}
 
@@ -54,6 +54,8 @@ _SIGS = {
     "zeta_zeta_ell": ([_VP, _VP, _I64, _VP, _INT, _VP, _VP], _INT),
     "zeta_get_status": ([_VP, _VP], _INT),
     "zeta_batch": ([_VP, _VP, _VP, _INT, _INT, _VP, _VP], _INT),
+    "zeta_backward_node": ([_VP, _VP, _VP, _VP, _VP], _INT),
+    "zeta_backward_particles": ([_VP, _VP, _I64, _VP, _VP, _VP], _INT),
     "zeta_autotune": ([_VP, _VP, _I64, _INT, _VP], _INT),
     "zeta_get_tuning": ([_VP, _VP, _INT], _INT),
     "zeta_assign_noalloc": ([_INT, _DBL, _INT, _VP, _I64, _VP, _VP, _VP], _INT),
@@ -254,7 +256,7 @@ class Context:
     def zeta_ell(self, particles=None, delta=None, forms=("particle",), out=None):
         """zeta_l(b1, b2) per form: returns {form: tensor (lmax+1, nb, nb) float64}."""
         import torch
-        bits = self.form_bits(forms)
+        bits = self.form_bits(forms) & 7
         order = [f for f in ("node", "gamma", "particle") if bits & FORM_BITS[f]]
         if out is None:
             out = torch.empty((len(order), self.lmax + 1, self.nbins, self.nbins), dtype=torch.float64,
@@ -276,6 +278,31 @@ class Context:
         if k < 0:
             raise ZetaError("zeta_profile_read", k)
         return {lib().zeta_profile_stage_name(i).decode(): (float(ms[i]), int(nl[i]), int(nc[i])) for i in range(k)}
+
+    def _weights(self, w):
+        if hasattr(w, "detach"):
+            w = w.detach().double().cpu().numpy()
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(self.lmax + 1, self.nbins, self.nbins)
+        return w
+
+    def backward_node(self, delta, weights, grad=None):
+        """zeta_backward_node: dL/d delta of L = sum weights * zeta_node."""
+        import torch
+        w = self._weights(weights)
+        if grad is None:
+            grad = torch.empty((self.n, self.n, self.n), dtype=torch.float32, device="cuda")
+        _check("zeta_backward_node", lib().zeta_backward_node(self._h, _ptr(delta), w.ctypes.data, _ptr(grad), _stream()))
+        return grad
+
+    def backward_particles(self, particles, weights, grad=None):
+        """zeta_backward_particles: dL/dx_p (np, 3) of L = sum weights * zeta_particle."""
+        import torch
+        w = self._weights(weights)
+        if grad is None:
+            grad = torch.empty((particles.shape[0], 3), dtype=torch.float32, device="cuda")
+        _check("zeta_backward_particles", lib().zeta_backward_particles(self._h, _ptr(particles), particles.shape[0],
+                                                                        w.ctypes.data, _ptr(grad), _stream()))
+        return grad
 
     def batch(self, particles, offsets, forms=("particle",), out=None):
         """zeta_batch: catalogues particles[offsets[i]:offsets[i+1]] in one CUDA-graph launch.
@@ -307,3 +334,49 @@ class Context:
 
     def get_status(self) -> int:
         return lib().zeta_get_status(self._h, _stream())
+
+
+def _autograd():
+    import torch
+
+    class ZetaNode(torch.autograd.Function):
+        """zeta_l of the node form of a contrast grid; differentiable in the grid."""
+
+        @staticmethod
+        def forward(fctx, delta, zctx):
+            d = delta.detach().contiguous()
+            fctx.save_for_backward(d)
+            fctx.zctx = zctx
+            return zctx.zeta_ell(delta=d, forms=("node",))["node"].clone()
+
+        @staticmethod
+        def backward(fctx, g):
+            (d,) = fctx.saved_tensors
+            return fctx.zctx.backward_node(d, g), None
+
+    class ZetaParticles(torch.autograd.Function):
+        """zeta_l of the particle form of a catalogue; differentiable in the positions."""
+
+        @staticmethod
+        def forward(fctx, pos, w, zctx):
+            parts = torch.cat([pos.detach(), w.detach()[:, None]], 1).contiguous()
+            fctx.save_for_backward(parts)
+            fctx.zctx = zctx
+            return zctx.zeta_ell(particles=parts, forms=("particle",))["particle"].clone()
+
+        @staticmethod
+        def backward(fctx, g):
+            (parts,) = fctx.saved_tensors
+            return fctx.zctx.backward_particles(parts, g), None, None
+
+    return ZetaNode, ZetaParticles
+
+
+def zeta_node(delta, zctx):
+    """Differentiable node-form zeta_l (torch.autograd.Function backed by zeta_backward_node)."""
+    return _autograd()[0].apply(delta, zctx)
+
+
+def zeta_particles(pos, w, zctx):
+    """Differentiable particle-form zeta_l in the positions (backed by zeta_backward_particles)."""
+    return _autograd()[1].apply(pos, w, zctx)
