@@ -180,6 +180,104 @@ def _oracle_sample(w, parts, prep):
     return total, sample
 
 
+def _gen_catalogue(args):
+    n, n_p, box, fs, ss = args
+    return mocks.lognormal_catalogue(n, n_p, box, fs, ss)
+
+
+def _events_ms(fn, reps, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _gram_variants(ctx, dev, w, stream):
+    """Node-form Gram per arithmetic on the fields of one (l, m) of this catalogue: ms per
+    launch, speedup over float32, relative Frobenius error against the float32 result."""
+    import torch
+    nb = ctx.nbins
+    delta, _ = ctx.assign(dev)
+    dhat = ctx.fft_r2c(delta)
+    alm = ctx.reconstruct_alm(dhat, 2, 1)
+    out = {}
+    ref = None
+    for g in ("fp32", "tf32", "bf16", "bf16x3"):
+        ctx.set_gram(g)
+        gram = torch.zeros((nb, nb), dtype=torch.float64, device="cuda")
+        ms = _events_ms(lambda: ctx.sum_grid(delta, alm, "node", gram=gram), 5, stream)
+        val = ctx.sum_grid(delta, alm, "node").cpu().numpy()
+        if ref is None:
+            ref = val
+        err = float(np.linalg.norm(val - ref) / np.linalg.norm(ref))
+        out[g] = {"ms_per_launch": round(ms, 4), "rel_err_vs_fp32": err}
+    ctx.set_gram("fp32")
+    for g in out:
+        out[g]["speedup_vs_fp32"] = round(out["fp32"]["ms_per_launch"] / out[g]["ms_per_launch"], 3)
+    del alm
+    return out
+
+
+def _batch_sample(ncat, stream):
+    """Batched (one CUDA-graph launch) against one-by-one zeta_ell on ncat catalogues of the
+    batched workload (256^3, lmax 8, 12 bins, sizes drawn uniformly in 0.5M-4M)."""
+    import multiprocessing as mp
+    import torch
+    from paper_2507_15209_gb300.workloads import batch_seeds
+    from paper_2507_15209_gb300.zeta import Context
+    w = WORKLOADS["batch64_n256"]
+    sizes = mocks.batch_sizes(w["n_cat"], w["n_p_lo"], w["n_p_hi"], w["size_seed"])[:ncat]
+    jobs = [(w["n"], int(sizes[i]), w["box"], *batch_seeds(i)) for i in range(ncat)]
+    with mp.get_context("spawn").Pool(min(ncat, 8)) as pool:
+        cats = pool.map(_gen_catalogue, jobs)
+    allp = torch.from_numpy(np.concatenate(cats)).cuda()
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    e = wl_edges(w)
+    ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=int(sizes.max()), forms=("particle",))
+    tune = ctx.autotune(allp[: int(sizes[0])], forms=("particle",))
+    views = [allp[int(offs[i]):int(offs[i + 1])] for i in range(ncat)]
+    out = torch.empty((ncat, 1, w["lmax"] + 1, len(e) - 1, len(e) - 1), dtype=torch.float64, device="cuda")
+
+    def one_by_one():
+        for i in range(ncat):
+            ctx.zeta_ell(particles=views[i], forms=("particle",), out=out[i])
+
+    ms_seq = _events_ms(one_by_one, 2, stream)
+    ms_batch = _events_ms(lambda: ctx.batch(allp, offs, forms=("particle",), out=out), 2, stream)
+    ctx.close()
+    return {"workload": "batch64_n256", "catalogues": ncat, "particles": int(sizes.sum()),
+            "s_per_catalog_batched": ms_batch / 1e3 / ncat, "s_per_catalog_one_by_one": ms_seq / 1e3 / ncat,
+            "speedup": round(ms_seq / ms_batch, 4), "tuned_ctas_per_sm": tune}
+
+
+def _adjoint_ratio(stream):
+    """Gradient cost on the adjoint workload (256^3 grid and 1M particles, lmax 6, 10 bins):
+    backward / forward time of the node form (dL/d delta) and the particle form (dL/dx)."""
+    import torch
+    from paper_2507_15209_gb300.zeta import Context
+    w = WORKLOADS["adjoint_n256_np1m"]
+    rho = mocks.lognormal_density(w["n"], w["field_seed"])
+    delta = torch.from_numpy((rho - 1.0).astype(np.float32)).cuda()
+    parts = torch.from_numpy(mocks.sample_particles(rho, w["n_p"], w["box"], w["sample_seed"])).cuda()
+    wts = mocks.loss_weights(w["lmax"], w["nbins"], w["loss_seed"])
+    e = wl_edges(w)
+    ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=w["n_p"], forms=("node", "particle", "backward"))
+    f_node = _events_ms(lambda: ctx.zeta_ell(delta=delta, forms=("node",)), 2, stream)
+    b_node = _events_ms(lambda: ctx.backward_node(delta, wts), 2, stream)
+    f_part = _events_ms(lambda: ctx.zeta_ell(particles=parts, forms=("particle",)), 2, stream)
+    b_part = _events_ms(lambda: ctx.backward_particles(parts, wts), 2, stream)
+    ctx.close()
+    return {"workload": "adjoint_n256_np1m", "node_forward_ms": f_node, "node_backward_ms": b_node,
+            "node_backward_over_forward": round(b_node / f_node, 3), "particle_forward_ms": f_part,
+            "particle_backward_ms": b_part, "particle_backward_over_forward": round(b_part / f_part, 3)}
+
+
 def _emit(d):
     print(json.dumps(d), flush=True)
 
@@ -319,6 +417,10 @@ def run_ours(args, w, rank, world, local_rank):
                     "d2h_bytes_per_step": int(out.numel() * 8)},
             "gpu_launches": int(gpu_launches),
         }
+        if not args.no_extras:
+            line["gram_variants"] = _gram_variants(ctx, dev, w, stream)
+            line["batch_sample"] = _batch_sample(8, stream)
+            line["adjoint"] = _adjoint_ratio(stream)
         if world == 1 and not args.no_cpu_baseline:
             total, sample = _oracle_sample(w, parts, _oracle_prepare(w, parts))
             line["cpu_baseline"] = {"value": total, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -338,6 +440,7 @@ def main():
     ap.add_argument("--workload", default="box2000_n512_np16m")
     ap.add_argument("--forms", default="particle,node")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the Gram-variant, batch and adjoint extras")
     ap.add_argument("--lmax", type=int, default=None, help="override lmax (small profiling runs only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

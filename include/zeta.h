@@ -118,6 +118,9 @@ size_t zeta_workspace_bytes(const zeta_ctx* ctx, int64_t np_max, int forms);
  * The library keeps the pointer, never frees it. */
 int zeta_set_workspace(zeta_ctx* ctx, void* dptr, size_t bytes);
 
+/* Switch the arithmetic of the node-form Gram (ZETA_GRAM_*) of an existing context. */
+int zeta_set_gram(zeta_ctx* ctx, int gram);
+
 /* Number of 8x8x8-cell tiles that particle sorting uses: (n/8)^3. */
 int64_t zeta_tile_count(const zeta_ctx* ctx);
 
@@ -210,6 +213,12 @@ int zeta_autotune(zeta_ctx* ctx, const float* particles, int64_t np, int forms, 
 /* The tuned persistent grid sizes in CTAs per SM: [node fp32, particle, Gamma, mass,
  * node tensor-core].  Returns 5. */
 int zeta_get_tuning(const zeta_ctx* ctx, int* ctas_per_sm, int n);
+
+/* Failure-detection self-test: launch one thread that waits, with the library's bounded
+ * device wait of `spins` polls, on an mbarrier that nothing ever arrives on.  The wait runs
+ * out, latches ZETA_ETIMEOUT in the device status word (read it with zeta_get_status) and the
+ * kernel returns; the context stays usable.  No GPU fault, trap or hang is involved. */
+int zeta_selftest_wait(zeta_ctx* ctx, int64_t spins, zeta_stream stream);
 
 /* Synchronise the stream and return the latched device status (ZETA_OK or ZETA_EDATA /
  * ZETA_ETIMEOUT), clearing it. */

@@ -192,6 +192,14 @@ int zeta_set_workspace(zeta_ctx* c, void* dptr, size_t bytes) {
 
 int64_t zeta_tile_count(const zeta_ctx* c) { return c ? c->ntiles : 0; }
 
+int zeta_set_gram(zeta_ctx* c, int gram) {
+  ZK_TRY(check_ctx(c));
+  if (gram < ZETA_GRAM_FP32 || gram > ZETA_GRAM_BF16X3) return ZETA_EINVAL;
+  c->p.gram = gram;
+  drop_batch_graph(c);
+  return ZETA_OK;
+}
+
 int zeta_assign(zeta_ctx* c, const float* particles, int64_t np, float* delta, double* wsum, zeta_stream stream) {
   ZK_TRY(check_ctx(c));
   if (!particles || np < 1 || np > 0x7fffffffLL || !delta) return ZETA_EINVAL;
@@ -547,6 +555,12 @@ int zeta_backward_particles(zeta_ctx* c, const float* particles, int64_t np, con
   }
   ZK_TRY(launch_c2r_inplace(c, gk, 1, stream));
   return launch_adj_finish_particles(c, parts, np, reinterpret_cast<float*>(gk), wsum, direct, grad, stream);
+}
+
+int zeta_selftest_wait(zeta_ctx* c, int64_t spins, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (spins < 0) return ZETA_EINVAL;
+  return launch_wait_selftest(c, spins, stream);
 }
 
 int zeta_get_status(zeta_ctx* c, zeta_stream stream) {

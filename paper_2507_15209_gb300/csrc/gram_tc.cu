@@ -294,6 +294,28 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_node_tc(const float* __rest
   }
 }
 
+// Diagnostic: wait on an mbarrier that nothing ever arrives on, with the same bounded wait
+// the tensor-core kernel uses; the timeout must latch ZETA_ETIMEOUT and return.
+__global__ void k_wait_selftest(long long spins, int* __restrict__ status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const uint32_t a = smem_u32(&bar);
+  bool done = false;
+  for (long long it = 0; it < spins && !done; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(0u)
+        : "memory");
+    done = ok != 0;
+  }
+  if (!done) atomicOr(status, 2);
+}
+
 template <int MODE>
 int tc_impl(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
   using T = TcT<MODE>;
@@ -305,6 +327,11 @@ int tc_impl(const zeta_ctx* c, const float* delta, const float* alm, double* par
 }
 
 }  // namespace
+
+int launch_wait_selftest(const zeta_ctx* c, long long spins, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(spins, c->d_status);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
 
 int launch_gram_node_tc(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
   StageScope prof(c, ST_GRAM_NODE, 1, s);

@@ -153,6 +153,7 @@ int launch_gram_particles(const zeta_ctx* c, const float4* sorted, const int64_t
                           double* partials, cudaStream_t s);
 // tensor-core node Gram (gram_tc.cu), arithmetic chosen by c->p.gram
 int launch_gram_node_tc(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
+int launch_wait_selftest(const zeta_ctx* c, long long spins, cudaStream_t s);
 int launch_mass(const zeta_ctx* c, const float2* dhat, int l, double* partials, cudaStream_t s);
 // out[b1][b2] += scale * (1/ *wdiv if wdiv) * sum_cta partials[cta][b1][b2], symmetrised.
 int launch_reduce(const zeta_ctx* c, const double* partials, int nparts, double scale, const double* wdiv,

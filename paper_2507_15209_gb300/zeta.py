@@ -44,6 +44,7 @@ _SIGS = {
     "zeta_workspace_bytes": ([_VP, _I64, _INT], _SZ),
     "zeta_set_workspace": ([_VP, _VP, _SZ], _INT),
     "zeta_tile_count": ([_VP], _I64),
+    "zeta_set_gram": ([_VP, _INT], _INT),
     "zeta_assign": ([_VP, _VP, _I64, _VP, _VP, _VP], _INT),
     "zeta_fft_r2c": ([_VP, _VP, _VP, _VP], _INT),
     "zeta_reconstruct_alm": ([_VP, _VP, _INT, _INT, _INT, _INT, _VP, _VP], _INT),
@@ -53,6 +54,7 @@ _SIGS = {
     "zeta_mass_term": ([_VP, _VP, _INT, _DBL, _VP, _VP], _INT),
     "zeta_zeta_ell": ([_VP, _VP, _I64, _VP, _INT, _VP, _VP], _INT),
     "zeta_get_status": ([_VP, _VP], _INT),
+    "zeta_selftest_wait": ([_VP, _I64, _VP], _INT),
     "zeta_batch": ([_VP, _VP, _VP, _INT, _INT, _VP, _VP], _INT),
     "zeta_backward_node": ([_VP, _VP, _VP, _VP, _VP], _INT),
     "zeta_backward_particles": ([_VP, _VP, _I64, _VP, _VP, _VP], _INT),
@@ -279,6 +281,9 @@ class Context:
             raise ZetaError("zeta_profile_read", k)
         return {lib().zeta_profile_stage_name(i).decode(): (float(ms[i]), int(nl[i]), int(nc[i])) for i in range(k)}
 
+    def set_gram(self, gram: str):
+        _check("zeta_set_gram", lib().zeta_set_gram(self._h, GRAM[gram]))
+
     def _weights(self, w):
         if hasattr(w, "detach"):
             w = w.detach().double().cpu().numpy()
@@ -331,6 +336,9 @@ class Context:
         t = np.zeros(5, np.int32)
         lib().zeta_get_tuning(self._h, t.ctypes.data, 5)
         return [int(x) for x in t]
+
+    def selftest_wait(self, spins: int = 1000):
+        _check("zeta_selftest_wait", lib().zeta_selftest_wait(self._h, int(spins), _stream()))
 
     def get_status(self) -> int:
         return lib().zeta_get_status(self._h, _stream())

@@ -191,6 +191,15 @@ def test_zeta_ell_from_delta_grid(Z):
         assert _rel(got[l], want["node"][l]) < 1e-5, l
 
 
+def test_bounded_device_wait_reports_timeout_and_context_survives(Z):
+    ctx = Z.Context(16, 100.0, 4, 1, [10.0, 20.0], np_max=500, forms=("particle",))
+    ctx.selftest_wait(2000)
+    assert ctx.get_status() == -4  # ZETA_ETIMEOUT, then cleared
+    parts = torch.from_numpy(mocks.uniform_particles(500, 100.0, 4)).cuda()
+    z = ctx.zeta_ell(particles=parts, forms=("particle",))["particle"]
+    assert ctx.get_status() == 0 and bool(torch.isfinite(z).all())
+
+
 def test_nonfinite_particle_is_reported_and_workspace_checked(Z):
     n, box = 16, 100.0
     parts = mocks.uniform_particles(500, box, 3)
