@@ -417,9 +417,12 @@ def run_ours(args, w, rank, world, local_rank):
                     "d2h_bytes_per_step": int(out.numel() * 8)},
             "gpu_launches": int(gpu_launches),
         }
-        if not args.no_extras:
+        extras = set() if args.no_extras else set(args.extras.split(","))
+        if "variants" in extras:
             line["gram_variants"] = _gram_variants(ctx, dev, w, stream)
+        if "batch" in extras:
             line["batch_sample"] = _batch_sample(8, stream)
+        if "adjoint" in extras:
             line["adjoint"] = _adjoint_ratio(stream)
         if world == 1 and not args.no_cpu_baseline:
             total, sample = _oracle_sample(w, parts, _oracle_prepare(w, parts))
@@ -441,6 +444,7 @@ def main():
     ap.add_argument("--forms", default="particle,node")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the Gram-variant, batch and adjoint extras")
+    ap.add_argument("--extras", default="variants,batch,adjoint", help="comma list of extras to measure")
     ap.add_argument("--lmax", type=int, default=None, help="override lmax (small profiling runs only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -3,14 +3,15 @@
 // G[b1][b2] = sum_x a_b1(x) * (delta(x) a_b2(x)) (the grid sum of Eq. 3PCF-multipole-sum at one
 // (l, m)) is a dense contraction over the grid points: D = A B^T with A[b][x] = a_b(x) and
 // B[b][x] = delta(x) a_b(x), K = the points.  A CTA streams chunks of kKT points:
-//   * 256 threads load the bin-interleaved fields (float4 = four bins) and delta for the next
-//     chunk into registers while the tensor core works on the current one, convert them to
-//     the MMA operand type and store them into shared memory in the canonical no-swizzle
-//     K-major layout (8-row x 16-byte core matrices; LBO = 128 B along K, SBO along rows);
-//   * one thread issues tcgen05.mma (M = 128 bin rows, zero-padded; N = 32; D in TMEM, fp32)
-//     and tcgen05.commit to the buffer's mbarrier; two buffers alternate;
-//   * every kFlushStages chunks (and at the end) warp 0 reads D with tcgen05.ld and adds it
-//     to float64 registers, so long sums do not accumulate in float32.
+//   * 256 threads load the bin-interleaved fields (float4 = four bins) and delta of one stage,
+//     convert them to the MMA operand type and store them into shared memory in the canonical
+//     no-swizzle K-major layout (8-row x 16-byte core matrices; LBO = 128 B along K, SBO along
+//     rows) while the tensor core works on the previous stage (two buffers, mbarriers);
+//   * block-diagonal packing fills all 128 rows: 128 / nb slots of nb bins, each slot a
+//     different run of points; one thread issues tcgen05.mma (M = N = 128, D fp32 in TMEM,
+//     128 columns) and tcgen05.commit;
+//   * every kFlushStages stages (and at the end) warps 0-3 read D with tcgen05.ld and add the
+//     diagonal blocks into float64 registers, so long sums do not accumulate in float32.
 // Operand arithmetic: TF32 (kind::tf32), BF16 (kind::f16), or split BF16 with three products
 // hi*hi + hi*lo + lo*hi (the lo*lo term is below float32 resolution of the result).
 // Waits on an mbarrier are bounded: on timeout the CTA latches ZETA_ETIMEOUT in the status
@@ -25,28 +26,29 @@ namespace zk {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr int kKT = 64;           // points per chunk (K of one stage)
-constexpr int kM = 128;           // MMA M: bin rows of A, zero-padded
-constexpr int kN = 32;            // MMA N: bin rows of B, zero-padded
-constexpr int kFlushStages = 64;  // chunks between float64 flushes
-constexpr uint32_t kTmemCols = 32;
+constexpr int kM = 128;           // MMA M
+constexpr int kN = 128;           // MMA N
+constexpr int kFlushStages = 8;   // stages between float64 flushes of the accumulator
+constexpr uint32_t kTmemCols = 128;
 constexpr long long kSpinLimit = 1LL << 26;
 
 template <int MODE>
 struct TcT;
+// ES: operand bytes; KI: K of one instruction; KT: points per slot and stage (32 bytes of K per
+// instruction -> KT * ES / 32 instructions per stage)
 template <>
 struct TcT<ZETA_GRAM_TF32> {
-  static constexpr int ES = 4, KI = 8, SPLIT = 1;
+  static constexpr int ES = 4, KI = 8, SPLIT = 1, KT = 32;
   static constexpr uint32_t FMT = 2;
 };
 template <>
 struct TcT<ZETA_GRAM_BF16> {
-  static constexpr int ES = 2, KI = 16, SPLIT = 1;
+  static constexpr int ES = 2, KI = 16, SPLIT = 1, KT = 64;
   static constexpr uint32_t FMT = 1;
 };
 template <>
 struct TcT<ZETA_GRAM_BF16X3> {
-  static constexpr int ES = 2, KI = 16, SPLIT = 2;
+  static constexpr int ES = 2, KI = 16, SPLIT = 2, KT = 64;
   static constexpr uint32_t FMT = 1;
 };
 
@@ -132,41 +134,60 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-// byte offset of element (row, e) in an operand tile of kKT elements per row
-template <int ES>
+// byte offset of element (row, e) in an operand tile of KT elements per row
+template <int ES, int KT>
 __device__ __forceinline__ uint32_t tile_off(int row, int e) {
-  constexpr uint32_t SBO = kKT * ES * 8;
+  constexpr uint32_t SBO = KT * ES * 8;
   return (row >> 3) * SBO + ((e * ES) >> 4) * 128 + (row & 7) * 16 + ((e * ES) & 15);
 }
 
+// Pack CP = 16 / ES consecutive values into one 16-byte core-matrix row segment (and the
+// low parts for split BF16).
 template <int MODE>
-__device__ __forceinline__ void put_elem(unsigned char* hi, unsigned char* lo, uint32_t off, float x) {
+__device__ __forceinline__ void pack16(const float* x, uint4& hi, uint4& lo) {
   using T = TcT<MODE>;
   if (T::ES == 4) {
-    *reinterpret_cast<uint32_t*>(hi + off) = to_tf32(x);
+    hi = make_uint4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
   } else {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
-    if (T::SPLIT == 2) *reinterpret_cast<__nv_bfloat16*>(lo + off) = __float2bfloat16_rn(x - __bfloat162float(h));
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
+      h[i] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
+      if (T::SPLIT == 2) {
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
+        l[i] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
+      }
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    if (T::SPLIT == 2) lo = make_uint4(l[0], l[1], l[2], l[3]);
   }
 }
 
+// Block-diagonal packing: NS = min(128 / nb, 32 / groups) slots, each a different run of KT points.  Row
+// s*nb + b of A holds bin b of slot s, row s*nb + b of B holds delta * bin b of slot s, so the
+// diagonal nb x nb blocks of D = A B^T are the Gram contributions of the NS runs (the other
+// blocks are discarded); no operand row is padding unless 128 % nb != 0.
 template <int MODE>
-__global__ void __launch_bounds__(kTcThreads) k_gram_node_tc(const float* __restrict__ delta, const float4* __restrict__ f4,
+__global__ void __launch_bounds__(kTcThreads, 2) k_gram_node_tc(const float* __restrict__ delta, const float4* __restrict__ f4,
                                                              long long ng, int nb, double* __restrict__ partials,
                                                              int* __restrict__ status) {
   using T = TcT<MODE>;
-  constexpr uint32_t ABYTES = kM * kKT * T::ES;  // one operand tile of A
-  constexpr uint32_t BBYTES = kN * kKT * T::ES;
-  constexpr uint32_t SBO = kKT * T::ES * 8;
-  constexpr uint32_t STAGE = T::SPLIT * (ABYTES + BBYTES);
+  constexpr int KT = T::KT;
+  constexpr uint32_t TILE = kM * KT * T::ES;  // one operand tile (A and B have 128 rows each)
+  constexpr uint32_t SBO = KT * T::ES * 8;
+  constexpr uint32_t STAGE = T::SPLIT * 2 * TILE;
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int ngrp = (nb + 3) >> 2;
+  // slots: as many runs of KT points as fit in 128 rows and in one 16-byte task per thread
+  const int ns = (kM / nb) < (32 / ngrp) ? (kM / nb) : (32 / ngrp);
+  const int pts = ns * KT;            // points per stage
   for (uint32_t i = tid; i < 2 * STAGE / 16; i += kTcThreads) reinterpret_cast<uint4*>(smraw)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -186,53 +207,117 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_node_tc(const float* __rest
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = make_idesc<T::FMT>();
 
-  double acc[32];
+  // float64 accumulators of the nb x nb result: entry e = tid + 256 i
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  // flush: D (128 x 128 fp32) -> shared memory (the idle operand buffers) -> the diagonal
+  // blocks summed over the slots into the float64 accumulators
+  auto flush = [&]() {
+    float* dsm = reinterpret_cast<float*>(smraw);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp < 4) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) acc[i] = 0.0;
-
-  const long long nchunk = ng / kKT;
-  const int p = tid % kKT, qt = tid / kKT;  // point in chunk, group quarter
-  // register prefetch of one chunk: delta and up to two float4 groups (groups qt, qt + 4)
-  float dn = 0.f;
-  float4 vn0 = make_float4(0.f, 0.f, 0.f, 0.f), vn1 = vn0;
-  auto fetch = [&](long long ch) {
-    const long long gp = ch * kKT + p;
-    dn = __ldg(delta + gp);
-    vn0 = (qt < ngrp) ? __ldg(f4 + qt * ng + gp) : make_float4(0.f, 0.f, 0.f, 0.f);
-    vn1 = (qt + 4 < ngrp) ? __ldg(f4 + (qt + 4) * ng + gp) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < kN / 32; ++q) {
+        float v[32];
+        tmem_load32(tmem + (static_cast<uint32_t>(32 * warp) << 16) + 32 * q, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) dsm[tid * (kN + 1) + 32 * q + i] = v[i];
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + kTcThreads * i;
+      if (e < nb * nb) {
+        const int b1 = e / nb, b2 = e % nb;
+        float sum = 0.f;
+        for (int sl = 0; sl < ns; ++sl) sum += dsm[(sl * nb + b1) * (kN + 1) + sl * nb + b2];
+        acc[i] += static_cast<double>(sum);
+      }
+    }
+    __syncthreads();
   };
-  long long ch = blockIdx.x;
-  if (ch < nchunk) fetch(ch);
+
+  // This CTA's stages: full chunks ch = blockIdx.x + i * gridDim.x; the last CTA also takes the
+  // ragged tail (ng not a multiple of the stage size) as one more, partial stage.
+  const long long nchunk = ng / pts;
+  const long long tail = ng - nchunk * pts;
+  const long long nfull = (nchunk > blockIdx.x) ? (nchunk - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const long long nmine = nfull + ((tail > 0 && blockIdx.x == gridDim.x - 1) ? 1 : 0);
+  auto stage_at = [&](long long i, long long& p0, int& npts) {
+    if (i < nfull) {
+      p0 = (blockIdx.x + i * gridDim.x) * static_cast<long long>(pts);
+      npts = pts;
+    } else {
+      p0 = nchunk * static_cast<long long>(pts);
+      npts = static_cast<int>(tail);
+    }
+  };
+  // register prefetch of one stage: this thread's task (CP consecutive points of one slot and
+  // one bin group); one task per thread covers every configuration with nb <= 32
+  constexpr int CP = 16 / T::ES;
+  const int ntask = (pts / CP) * ngrp;
+  float4 pv[CP];
+  float pd[CP];
+  auto fetch = [&](long long p0, int npts) {
+    const int pc = tid % (pts / CP), g = tid / (pts / CP);
+#pragma unroll
+    for (int i = 0; i < CP; ++i) {
+      const int pt = pc * CP + i;
+      const bool in = tid < ntask && pt < npts;
+      pv[i] = in ? __ldg(f4 + g * ng + p0 + pt) : make_float4(0.f, 0.f, 0.f, 0.f);
+      pd[i] = in ? __ldg(delta + p0 + pt) : 0.f;
+    }
+  };
   int stage = 0;
-  bool started = false;
-  bool ok = true;
-  for (; ch < nchunk; ch += gridDim.x, ++stage) {
+  bool started = false, ok = true;
+  if (nmine > 0) {
+    long long p0;
+    int np0;
+    stage_at(0, p0, np0);
+    fetch(p0, np0);
+  }
+  for (long long it = 0; it < nmine; ++it) {
     const int b = stage & 1;
     unsigned char* base = smraw + b * STAGE;
     unsigned char* Ahi = base;
-    unsigned char* Bhi = base + ABYTES;
-    unsigned char* Alo = base + ABYTES + BBYTES;
-    unsigned char* Blo = Alo + ABYTES;
+    unsigned char* Bhi = base + TILE;
+    unsigned char* Alo = base + 2 * TILE;
+    unsigned char* Blo = base + 3 * TILE;
     if (stage >= 2 && ok) {
       if (!mbar_wait(&bar[b], ((stage - 2) >> 1) & 1)) ok = false;
     }
-    const float d = dn;
-    const float4 v0 = vn0, v1 = vn1;
-    if (ch + gridDim.x < nchunk) fetch(ch + gridDim.x);
-    const float a0[4] = {v0.x, v0.y, v0.z, v0.w};
-    const float a1[4] = {v1.x, v1.y, v1.z, v1.w};
+    if (tid < ntask) {
+      const int pc = tid % (pts / CP), g = tid / (pts / CP);
+      const int pt0 = pc * CP;
+      const int sl = pt0 / KT, k0 = pt0 % KT;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (qt < ngrp) {
-        const int r = 4 * qt + j;
-        put_elem<MODE>(Ahi, Alo, tile_off<T::ES>(r, p), a0[j]);
-        put_elem<MODE>(Bhi, Blo, tile_off<T::ES>(r, p), d * a0[j]);
+      for (int j = 0; j < 4; ++j) {
+        const int bin = 4 * g + j;
+        if (bin >= nb) break;
+        float av[CP], bv[CP];
+#pragma unroll
+        for (int i = 0; i < CP; ++i) {
+          const float x = j == 0 ? pv[i].x : j == 1 ? pv[i].y : j == 2 ? pv[i].z : pv[i].w;
+          av[i] = x;
+          bv[i] = pd[i] * x;
+        }
+        const uint32_t off = tile_off<T::ES, KT>(sl * nb + bin, k0);
+        uint4 hi, lo;
+        pack16<MODE>(av, hi, lo);
+        *reinterpret_cast<uint4*>(Ahi + off) = hi;
+        if (T::SPLIT == 2) *reinterpret_cast<uint4*>(Alo + off) = lo;
+        pack16<MODE>(bv, hi, lo);
+        *reinterpret_cast<uint4*>(Bhi + off) = hi;
+        if (T::SPLIT == 2) *reinterpret_cast<uint4*>(Blo + off) = lo;
       }
-      if (qt + 4 < ngrp) {
-        const int r = 4 * (qt + 4) + j;
-        put_elem<MODE>(Ahi, Alo, tile_off<T::ES>(r, p), a1[j]);
-        put_elem<MODE>(Bhi, Blo, tile_off<T::ES>(r, p), d * a1[j]);
-      }
+    }
+    if (it + 1 < nmine) {  // next stage's loads are in flight while this one is contracted
+      long long p1;
+      int np1;
+      stage_at(it + 1, p1, np1);
+      fetch(p1, np1);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (!ok) abort_flag = 1;
@@ -242,7 +327,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_node_tc(const float* __rest
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t aa = smem_u32(Ahi), ab = smem_u32(Bhi), la = smem_u32(Alo), lb = smem_u32(Blo);
 #pragma unroll
-      for (int k = 0; k < kKT / T::KI; ++k) {
+      for (int k = 0; k < KT * T::ES / 32; ++k) {
         const uint32_t koff = k * 2 * 128;  // two core matrices along K per instruction
         const uint64_t dA = make_desc(aa + koff, 128, SBO), dB = make_desc(ab + koff, 128, SBO);
         mma<MODE>(tmem, dA, dB, idesc, (started || k > 0) ? 1u : 0u);
@@ -255,36 +340,22 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_node_tc(const float* __rest
     }
     started = true;
     if ((stage + 1) % kFlushStages == 0) {
-      // drain: wait for this chunk's products, move D into float64, restart accumulation
       if (!mbar_wait(&bar[b], (stage >> 1) & 1)) ok = false;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (warp == 0 && ok) {
-        float v[32];
-        tmem_load32(tmem, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) acc[i] += static_cast<double>(v[i]);
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      if (ok) flush();
       started = false;
     }
+    ++stage;
   }
-  if (started && ok) {
+  if (started && ok && !abort_flag) {
     const int last = stage - 1;
     if (!mbar_wait(&bar[last & 1], (last >> 1) & 1)) ok = false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0 && ok) {
-      float v[32];
-      tmem_load32(tmem, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) acc[i] += static_cast<double>(v[i]);
-    }
+    if (ok) flush();
   }
   if (!ok || abort_flag) atomicOr(status, 2);
-  if (warp == 0 && lane < nb) {
-    double* part = partials + static_cast<long long>(blockIdx.x) * nb * nb + lane * nb;
 #pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < nb) part[c] = acc[c];
+  for (int i = 0; i < 4; ++i) {
+    const int e = tid + kTcThreads * i;
+    if (e < nb * nb) partials[static_cast<long long>(blockIdx.x) * nb * nb + e] = acc[i];
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -319,7 +390,10 @@ __global__ void k_wait_selftest(long long spins, int* __restrict__ status) {
 template <int MODE>
 int tc_impl(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
   using T = TcT<MODE>;
-  const size_t sm = 2 * T::SPLIT * static_cast<size_t>(kM + kN) * kKT * T::ES;
+  // two stages of operands; the flush also stages the 128 x 129 float D tile in the same bytes
+  const size_t ops = 2 * T::SPLIT * 2 * static_cast<size_t>(kM) * T::KT * T::ES;
+  const size_t dtile = static_cast<size_t>(kM) * (kN + 1) * sizeof(float);
+  const size_t sm = ops > dtile ? ops : dtile;
   if (ensure_smem(reinterpret_cast<const void*>(k_gram_node_tc<MODE>), sm) != ZETA_OK) return ZETA_ECUDA;
   k_gram_node_tc<MODE><<<gram_ctas(c, GK_TC), kTcThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
                                                             c->p.nbins, partials, c->d_status);

@@ -286,24 +286,30 @@ __global__ void __launch_bounds__(kThreads)
         for (int b = 4 * ngrp; b < NBP; ++b) vals[me * G::NBS + b] = 0.f;
       }
       __syncthreads();
-      // phase 2: (point, group) gathers
-      for (int task = threadIdx.x; task < cnt * ngrp; task += blockDim.x) {
-        const int p = task % cnt, q4 = task / cnt;
-        const int4 o = org[p];
-        const float* w = bw + p * 3 * D;
-        const float4* base = f4 + q4 * ng;
+      // phase 2: (point, group) gathers, D lanes per task (one per x offset of the stencil) so
+      // that a warp load covers 32/D tasks with D consecutive float4 (one row segment) each
+      // (the loop runs in whole warps so every lane reaches the shuffles; D divides 32)
+      const int total = cnt * ngrp * D;
+      const int lane = threadIdx.x & 31;
+      for (int tb = threadIdx.x - lane; tb < total; tb += blockDim.x) {
+        const int task = tb + lane;
+        const bool act = task < total;
+        const int ox = task % D, pg = task / D;
+        const int p = act ? pg % cnt : 0, q4 = act ? pg / cnt : 0;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
+          const int4 o = org[p];
+          const float* w = bw + p * 3 * D;
+          const float4* base = f4 + q4 * ng;
+          const int xo = (o.x + ox) & mask;
+          const float wx = w[ox];
 #pragma unroll
-        for (int oz = 0; oz < D; ++oz) {
-          const long long zrow = static_cast<long long>((o.z + oz) & mask) * n;
+          for (int oz = 0; oz < D; ++oz) {
+            const long long zrow = static_cast<long long>((o.z + oz) & mask) * n;
 #pragma unroll
-          for (int oy = 0; oy < D; ++oy) {
-            const float wyz = w[2 * D + oz] * w[D + oy];
-            const float4* row = base + (zrow + ((o.y + oy) & mask)) * n;
-#pragma unroll
-            for (int ox = 0; ox < D; ++ox) {
-              const float ww = wyz * w[ox];
-              const float4 v = __ldg(row + ((o.x + ox) & mask));
+            for (int oy = 0; oy < D; ++oy) {
+              const float ww = w[2 * D + oz] * w[D + oy] * wx;
+              const float4 v = __ldg(base + (zrow + ((o.y + oy) & mask)) * n + xo);
               acc.x = fmaf(ww, v.x, acc.x);
               acc.y = fmaf(ww, v.y, acc.y);
               acc.z = fmaf(ww, v.z, acc.z);
@@ -311,7 +317,14 @@ __global__ void __launch_bounds__(kThreads)
             }
           }
         }
-        *reinterpret_cast<float4*>(vals + p * G::NBS + 4 * q4) = acc;
+#pragma unroll
+        for (int off = 1; off < D; off <<= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off, D);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off, D);
+          acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off, D);
+          acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off, D);
+        }
+        if (act && ox == 0) *reinterpret_cast<float4*>(vals + p * G::NBS + 4 * q4) = acc;
       }
       __syncthreads();
       if (grp < G::NGRP) g.add(vals, wts, cnt, b1, b2, grp);
