@@ -207,12 +207,23 @@ int zeta_batch(zeta_ctx* ctx, const float* particles, const int64_t* offsets, in
 
 /* Autotuner: on this catalogue, times the Gram kernels that `forms` uses at persistent grid
  * sizes of 1, 2, 3, 4, 6 and 8 CTAs per SM and keeps the fastest for each kernel (used by all
- * later calls).  Synchronises the stream; overwrites the workspace. */
+ * later calls); with the particle form it then picks the staging threshold of
+ * zeta_set_staging the same way.  Synchronises the stream; overwrites the workspace. */
 int zeta_autotune(zeta_ctx* ctx, const float* particles, int64_t np, int forms, zeta_stream stream);
 
 /* The tuned persistent grid sizes in CTAs per SM: [node fp32, particle, Gamma, mass,
  * node tensor-core].  Returns 5. */
 int zeta_get_tuning(const zeta_ctx* ctx, int* ctas_per_sm, int n);
+
+/* Particle form: a batch of up to 256 particles of one 8x8x8-cell tile copies the tile's
+ * halo of the fields into shared memory when it holds at least `min_particles` particles
+ * (0: always; a value above 256: never) and otherwise reads each stencil from global memory.
+ * Both give the same sums up to float32 rounding order; the choice only moves time.
+ * Default 16; zeta_autotune also picks it.  min_particles < 0 -> ZETA_EINVAL.  No counterpart
+ * in the paper (an execution choice of this implementation). */
+int zeta_set_staging(zeta_ctx* ctx, int min_particles);
+/* The current threshold of zeta_set_staging (>= 0), or ZETA_EINVAL for a null context. */
+int zeta_get_staging(const zeta_ctx* ctx);
 
 /* Failure-detection self-test: launch one thread that waits, with the library's bounded
  * device wait of `spins` polls, on an mbarrier that nothing ever arrives on.  The wait runs

@@ -451,11 +451,48 @@ int zeta_autotune(zeta_ctx* c, const float* particles, int64_t np, int forms, ze
     }
     c->tune[kind] = best_c;
     if (rc != ZETA_OK) break;
+    if (kind == GK_PART) {  // then the halo-staging threshold at that grid size
+      const int thr[] = {0, 8, 16, 32, 64, 257};
+      float best_t = 1e30f;
+      int best_m = c->staged_min;
+      for (int m : thr) {
+        c->staged_min = m;
+        if ((rc = run(kind)) != ZETA_OK) break;
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < 3 && rc == ZETA_OK; ++r) rc = run(kind);
+        cudaEventRecord(e1, stream);
+        if (rc != ZETA_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = rc ? rc : ZETA_ECUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_t) {
+          best_t = ms;
+          best_m = m;
+        }
+      }
+      c->staged_min = best_m;
+      if (rc != ZETA_OK) break;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   drop_batch_graph(c);
   return rc;
+}
+
+int zeta_set_staging(zeta_ctx* c, int min_particles) {
+  ZK_TRY(check_ctx(c));
+  if (min_particles < 0) return ZETA_EINVAL;
+  c->staged_min = min_particles;
+  drop_batch_graph(c);
+  return ZETA_OK;
+}
+
+int zeta_get_staging(const zeta_ctx* c) {
+  if (!c) return ZETA_EINVAL;
+  return c->staged_min;
 }
 
 int zeta_get_tuning(const zeta_ctx* c, int* ctas_per_sm, int n) {

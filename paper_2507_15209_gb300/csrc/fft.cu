@@ -79,14 +79,14 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT) k_fft_axis(float2* 
   constexpr int NC = N / 2;
   constexpr int NT = RegThreads<N, T, 512>::NT;
   extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* ex = sm + N;  // [N][T]
+  float2* tw = sm;                     // per-stage twiddles
+  float2* ex = sm + StageTw<N>::SIZE;  // [N][T]
   const int x0 = blockIdx.x * T;
   const long long o = blockIdx.y;
   float2* d = data + blockIdx.z * fstride;
   const long long stride = (AXIS == 1) ? NC : static_cast<long long>(N) * NC;
   const long long base = (AXIS == 1) ? o * N * NC + x0 : o * NC + x0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  stage_tw_fill<N>(tw, twg, 1);
   auto load = [&](int col, int k) { return d[base + k * stride + col]; };
   auto store = [&](int col, int k, float2 v) { d[base + k * stride + col] = v; };
   __syncthreads();
@@ -176,14 +176,14 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
   constexpr int NC = N / 2, C = 4 * RB, PS = C + 1;
   constexpr int NT = RegThreads<NC, C, 256>::NT;
   extern __shared__ float2 sm[];
-  float2* tw = sm;          // W_N^e, e < N
-  float2* tw2 = sm + N;     // W_NC^e
-  float2* ex = tw2 + NC;    // [NC][PS] exchange
-  float2* res = ex + NC * PS;  // [NC][PS] outputs in natural order
+  float2* tw = sm;                      // W_N^e, e < N
+  float2* tw2 = sm + N;                 // per-stage twiddles of the length-NC transform
+  float2* ex = tw2 + StageTw<NC>::SIZE;  // [NC][PS] exchange, then the outputs in natural order
+  float2* res = ex;
   const int g = blockIdx.y;
   const long long r0 = static_cast<long long>(blockIdx.x) * RB;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-  for (int i = threadIdx.x; i < NC; i += blockDim.x) tw2[i] = twg[2 * i];
+  stage_tw_fill<NC>(tw2, twg, 2);
   __syncthreads();
   auto load = [&](int c, int k) -> float2 {
     const int f = 4 * g + c / RB;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
     return cadd(cadd(xk, cconj(xp)), mul_i(cmul(wk, csub(xk, cconj(xp)))));
   };
   auto store = [&](int c, int j, float2 v) { res[j * PS + c] = v; };
-  fft_reg<NC, C, NT, true, true>(ex, PS, tw2, load, store);
+  fft_reg<NC, C, NT, true, true, 0, true>(ex, PS, tw2, load, store);
   __syncthreads();
   for (int idx = threadIdx.x; idx < NC * RB; idx += blockDim.x) {
     const int r = idx / NC, j = idx % NC;
@@ -208,25 +208,43 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
 }
 
 // z-pass of the field reconstruction with the multipole window fused in.
-// grid (nc/T, n); each thread keeps, for its own stage-0 points, delta_hat, the angular
-// factor R_lm(n-hat) (with the real sign of i^l) and the |n|^2 index in registers.  Bins are
-// taken four at a time: one float4 gather of the window table [n2][bin] per point, then for
-// each of the four fields delta_hat * R * J_b(|n|^2) (* i for odd l) is transformed and the
-// z-transformed tile written to out + f * fstride (fields b0 + f, f < nf; b0 % 4 == 0).
+// grid (nc/T, n).  For its own stage-0 points each thread keeps delta_hat * R_lm(n-hat) (with
+// the real sign of i^l) and the window-table row of |n|^2 in shared memory.  Bins are taken
+// four at a time: one float4 gather of the window table [n2][nbp] per point gives the
+// values of four fields, and the gather of the next four is issued before the current four
+// are transformed, so its latency hides behind them.  Field f (bin b0 + f) is
+// delta_hat * R * J_f(|n|^2) (* i for odd l); its z-transformed tile goes to out + f * fstride.
 template <int N, int T>
-__global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
+struct AlmZ {
+  static constexpr int NT = RegThreads<N, T, 512>::NT;
+  static constexpr int PPT = N * T / NT;
+  static constexpr int PADR = 2;  // exchange padding (conflict-free last stage for T = 8)
+  static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;  // at least 16 warps per SM
+  static constexpr size_t smem() {
+    return (StageTw<N>::SIZE + static_cast<size_t>(PPT) * NT + static_cast<size_t>(N) * T + N / PADR) *
+               sizeof(float2) +
+           static_cast<size_t>(PPT) * NT * sizeof(int);
+  }
+};
+
+template <int N, int T>
+__global__ void __launch_bounds__(AlmZ<N, T>::NT, AlmZ<N, T>::MINB)
     k_alm_z(const float2* __restrict__ dhat, float2* __restrict__ out, long long fstride, int nf,
             const float4* __restrict__ jt4, int nbp4, int l, int m, const float2* __restrict__ twg) {
   constexpr int NC = N / 2;
-  constexpr int NT = RegThreads<N, T, 512>::NT;
-  constexpr int PPT = N * T / NT;
+  constexpr int NT = AlmZ<N, T>::NT;
+  constexpr int PPT = AlmZ<N, T>::PPT;
+  constexpr int PADR = AlmZ<N, T>::PADR;
   extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* ex = tw + N;  // [N][T] exchange
+  float2* tw = sm;                      // per-stage twiddles
+  float2* pd = tw + StageTw<N>::SIZE;   // [PPT][NT] delta_hat * angular factor
+  float2* ex = pd + PPT * NT;           // [N][T] exchange (+ padding)
+  int* pn = reinterpret_cast<int*>(ex + N * T + N / PADR);  // [PPT][NT] window-table rows
   const int x0 = blockIdx.x * T;
   const int iy = blockIdx.y;
-  const long long colbase = static_cast<long long>(iy) * NC + x0;
-  const long long zstride = static_cast<long long>(N) * NC;
+  // offsets within one field (n^3 / 2 < 2^31)
+  const int colbase = iy * NC + x0;
+  constexpr int zstride = N * NC;
   if (iy == N / 2) {  // y-Nyquist row: the window is zero
     for (int f = 0; f < nf; ++f)
       for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
@@ -235,26 +253,31 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
       }
     return;
   }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  stage_tw_fill<N>(tw, twg, 1);
   const float sgn = ((l & 3) < 2) ? 1.f : -1.f;  // real part of i^l (or of i^{l-1} for odd l)
   const int ny = signed_freq(iy, N);
-  float2 pd[PPT];
-  int pn[PPT];
+  float4 jn[PPT];
 #pragma unroll
   for (int s = 0; s < PPT; ++s) {
     int c, z;
     reg_slot<N, T, NT, false>(s, c, z);
     const int nz = signed_freq(z, N), nx = x0 + c;
     const bool nyq = (z == N / 2);
-    pn[s] = nyq ? 0 : nx * nx + ny * ny + nz * nz;
+    const int row = nyq ? 0 : (nx * nx + ny * ny + nz * nz) * nbp4;
+    pn[s * NT + threadIdx.x] = row;
     const float a = nyq ? 0.f : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz));
-    pd[s] = cscale(dhat[colbase + z * zstride + c], a);
+    pd[s * NT + threadIdx.x] = cscale(dhat[colbase + z * zstride + c], a);
+    jn[s] = __ldg(jt4 + row);
   }
   __syncthreads();
   for (int g = 0; 4 * g < nf; ++g) {
     float4 jv[PPT];
 #pragma unroll
-    for (int s = 0; s < PPT; ++s) jv[s] = __ldg(jt4 + static_cast<long long>(pn[s]) * nbp4 + g);
+    for (int s = 0; s < PPT; ++s) jv[s] = jn[s];
+    if (4 * (g + 1) < nf) {
+#pragma unroll
+      for (int s = 0; s < PPT; ++s) jn[s] = __ldg(jt4 + pn[s * NT + threadIdx.x] + g + 1);
+    }
     const int nj = (nf - 4 * g) < 4 ? (nf - 4 * g) : 4;
     for (int j = 0; j < nj; ++j) {
       const int f = 4 * g + j;
@@ -262,12 +285,12 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
 #pragma unroll
       for (int s = 0; s < PPT; ++s) {
         const float jj = j == 0 ? jv[s].x : j == 1 ? jv[s].y : j == 2 ? jv[s].z : jv[s].w;
-        v[s] = cscale(pd[s], jj);
+        v[s] = cscale(pd[s * NT + threadIdx.x], jj);
         if (l & 1) v[s] = mul_i(v[s]);
       }
       float2* of = out + f * fstride;
       auto store = [&](int c, int z, float2 val) { of[colbase + z * zstride + c] = val; };
-      fft_reg_v<N, T, NT, true, false>(v, ex, T, tw, store);
+      fft_reg_v<N, T, NT, true, false, PADR>(v, ex, T, tw, store);
     }
   }
 }
@@ -285,14 +308,14 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
   constexpr int NC = N / 2, C = 4 * RB, PS = C + 1;
   constexpr int NT = RegThreads<NC, C, 256>::NT;
   extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* tw2 = sm + N;
-  float2* ex = tw2 + NC;
-  float2* res = ex + NC * PS;
+  float2* tw = sm;                       // W_N^e, e < N
+  float2* tw2 = sm + N;                  // per-stage twiddles of the length-NC transform
+  float2* ex = tw2 + StageTw<NC>::SIZE;  // [NC][PS] exchange, then the outputs
+  float2* res = ex;
   const int g = blockIdx.y;
   const long long r0 = static_cast<long long>(blockIdx.x) * RB;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
-  for (int i = threadIdx.x; i < NC; i += blockDim.x) tw2[i] = twg[2 * i];
+  stage_tw_fill<NC>(tw2, twg, 2);
   __syncthreads();
   auto load = [&](int c, int k) -> float2 {
     const int j = c / RB, r = c % RB;
@@ -303,7 +326,7 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
     return make_float2(fa[j], fb[j]);
   };
   auto store = [&](int c, int k, float2 v) { res[k * PS + c] = v; };
-  fft_reg<NC, C, NT, false, true>(ex, PS, tw2, load, store);
+  fft_reg<NC, C, NT, false, true, 0, true>(ex, PS, tw2, load, store);
   __syncthreads();
   for (int idx = threadIdx.x; idx < NC * C; idx += blockDim.x) {
     const int c = idx / NC, k = idx % NC;
@@ -328,9 +351,9 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
   constexpr int NC = N / 2;
   constexpr int NT = RegThreads<N, T, 512>::NT;
   extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* ex = tw + N;              // [N][T]
-  float2* acc = ex + N * T;         // [N][T] sum over fields
+  float2* tw = sm;                      // per-stage twiddles
+  float2* ex = tw + StageTw<N>::SIZE;   // [N][T]
+  float2* acc = ex + N * T;             // [N][T] sum over fields
   float* ang = reinterpret_cast<float*>(acc + N * T);  // [N][T]
   int* n2 = reinterpret_cast<int*>(ang + N * T);        // [N][T]
   const int x0 = blockIdx.x * T;
@@ -338,7 +361,7 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
   if (iy == N / 2) return;  // the window vanishes on the y-Nyquist plane
   const long long colbase = static_cast<long long>(iy) * NC + x0;
   const long long zstride = static_cast<long long>(N) * NC;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  stage_tw_fill<N>(tw, twg, 1);
   // (-1)^l i^l = (-i)^l = sgn * (-i)^(l mod 2): sgn = +1 for l mod 4 in {0, 1}, -1 otherwise
   const float sgn = ((l & 3) < 2) ? 1.f : -1.f;
   const int ny = signed_freq(iy, N);
@@ -387,6 +410,17 @@ int set_smem(K kernel, size_t bytes) {
 
 inline int check_launch() { return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA; }
 
+// dynamic shared memory of the pencil pass (twiddles + [N][T] exchange)
+template <int N, int T>
+constexpr size_t axis_smem() {
+  return (StageTw<N>::SIZE + static_cast<size_t>(N) * T) * sizeof(float2);
+}
+// four-field x-pass: W_N, half-length twiddles, [N/2][4 RB + 1] exchange
+template <int N, int RB>
+constexpr size_t x4_smem() {
+  return (N + StageTw<N / 2>::SIZE + static_cast<size_t>(N / 2) * (4 * RB + 1)) * sizeof(float2);
+}
+
 template <int N>
 int r2c_impl(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t s) {
   constexpr int NC = N / 2;
@@ -395,7 +429,7 @@ int r2c_impl(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t s
   size_t smx = (N + NC + NC * (kRB + 1)) * sizeof(float2);
   if (set_smem(k_r2c_x<N, kRB>, smx)) return ZETA_ECUDA;
   k_r2c_x<N, kRB><<<N * N / kRB, 256, smx, s>>>(delta, dhat, c->d_tw);
-  size_t sma = (N + N * T) * sizeof(float2);
+  size_t sma = axis_smem<N, T>();
   if (set_smem(k_fft_axis<N, T, false, 1>, sma) || set_smem(k_fft_axis<N, T, false, 2>, sma)) return ZETA_ECUDA;
   k_fft_axis<N, T, false, 1><<<dim3(NC / T, N, 1), RegThreads<N, T, 512>::NT, sma, s>>>(dhat, 0, c->d_tw);
   k_fft_axis<N, T, false, 2><<<dim3(NC / T, N, 1), RegThreads<N, T, 512>::NT, sma, s>>>(dhat, 0, c->d_tw);
@@ -409,7 +443,7 @@ int c2r_impl(const zeta_ctx* c, float2* data, int nf, cudaStream_t s, bool do_y)
   const long long fstride = static_cast<long long>(N) * N * NC;
   if (do_y) {
     StageScope prof(c, ST_ALM_Y, 1, s);
-    size_t sma = (N + N * T) * sizeof(float2);
+    size_t sma = axis_smem<N, T>();
     if (set_smem(k_fft_axis<N, T, true, 1>, sma)) return ZETA_ECUDA;
     k_fft_axis<N, T, true, 1><<<dim3(NC / T, N, nf), RegThreads<N, T, 512>::NT, sma, s>>>(data, fstride, c->d_tw);
   }
@@ -429,24 +463,23 @@ int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf
   const long long fstride = static_cast<long long>(N) * N * NC;
   {
     StageScope prof(c, ST_ALM_Z, 1, s);
-    size_t smz = (N + static_cast<size_t>(N) * T) * sizeof(float2);
+    const size_t smz = AlmZ<N, T>::smem();
     if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
     const int nbp4 = (c->p.nbins + 3) / 4;
     const float4* jt4 = reinterpret_cast<const float4*>(c->d_jtab) + static_cast<long long>(l) * c->nn2 * nbp4 + b0 / 4;
-    k_alm_z<N, T><<<dim3(NC / T, N), RegThreads<N, T, 512>::NT, smz, s>>>(dhat, spec, fstride, nf, jt4, nbp4, l, m,
-                                                                     c->d_tw);
+    k_alm_z<N, T><<<dim3(NC / T, N), AlmZ<N, T>::NT, smz, s>>>(dhat, spec, fstride, nf, jt4, nbp4, l, m, c->d_tw);
     if (check_launch()) return ZETA_ECUDA;
   }
   {
     StageScope prof(c, ST_ALM_Y, 1, s);
-    size_t sma = (N + N * TY) * sizeof(float2);
+    size_t sma = axis_smem<N, TY>();
     if (set_smem(k_fft_axis<N, TY, true, 1>, sma)) return ZETA_ECUDA;
     k_fft_axis<N, TY, true, 1><<<dim3(NC / TY, N, nf), RegThreads<N, TY, 512>::NT, sma, s>>>(spec, fstride, c->d_tw);
     if (check_launch()) return ZETA_ECUDA;
   }
   StageScope prof(c, ST_ALM_X, 1, s);
   constexpr int RB = kRB4;
-  size_t smx = (N + NC + 2 * NC * (4 * RB + 1)) * sizeof(float2);
+  size_t smx = x4_smem<N, RB>();
   if (set_smem(k_c2r_x4<N, RB>, smx)) return ZETA_ECUDA;
   const int ng4 = (nf + 3) / 4;
   k_c2r_x4<N, RB><<<dim3(N * N / RB, ng4), RegThreads<N / 2, 4 * RB, 256>::NT, smx, s>>>(
@@ -460,7 +493,7 @@ int c2r_full(const zeta_ctx* c, float2* data, int nf, cudaStream_t s) {
   constexpr int NC = N / 2;
   constexpr int T = kTy < NC ? kTy : NC;
   const long long fstride = static_cast<long long>(N) * N * NC;
-  size_t sma = (N + N * T) * sizeof(float2);
+  size_t sma = axis_smem<N, T>();
   if (set_smem(k_fft_axis<N, T, true, 2>, sma)) return ZETA_ECUDA;
   StageScope prof(c, ST_ALM_Z, 1, s);
   k_fft_axis<N, T, true, 2><<<dim3(NC / T, N, nf), RegThreads<N, T, 512>::NT, sma, s>>>(data, fstride, c->d_tw);
@@ -502,14 +535,15 @@ int adj_impl(const zeta_ctx* c, const float* fields, int nf, float2* spec, int l
   constexpr int RB = kRB4;
   const long long fstride = static_cast<long long>(N) * N * NC;
   StageScope prof(c, ST_ADJ_FFT, 3, s);
-  const size_t smx = (N + NC + 2 * NC * (4 * RB + 1)) * sizeof(float2);
+  const size_t smx = x4_smem<N, RB>();
   if (set_smem(k_r2c_x4<N, RB>, smx)) return ZETA_ECUDA;
   k_r2c_x4<N, RB><<<dim3(N * N / RB, (nf + 3) / 4), RegThreads<N / 2, 4 * RB, 256>::NT, smx, s>>>(
       reinterpret_cast<const float4*>(fields), nf, spec, fstride, c->d_tw);
-  const size_t sma = (N + N * TY) * sizeof(float2);
+  const size_t sma = axis_smem<N, TY>();
   if (set_smem(k_fft_axis<N, TY, false, 1>, sma)) return ZETA_ECUDA;
   k_fft_axis<N, TY, false, 1><<<dim3(NC / TY, N, nf), RegThreads<N, TY, 512>::NT, sma, s>>>(spec, fstride, c->d_tw);
-  const size_t smz = (N + 2 * static_cast<size_t>(N) * TZ) * sizeof(float2) + 2 * static_cast<size_t>(N) * TZ * 4;
+  const size_t smz = (StageTw<N>::SIZE + 2 * static_cast<size_t>(N) * TZ) * sizeof(float2) +
+                     2 * static_cast<size_t>(N) * TZ * 4;
   if (set_smem(k_adj_z<N, TZ>, smz)) return ZETA_ECUDA;
   const int nbp4 = (c->p.nbins + 3) / 4;
   const float4* jt4 = reinterpret_cast<const float4*>(c->d_jtab) + static_cast<long long>(l) * c->nn2 * nbp4;

@@ -335,6 +335,285 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------------------
+// Particle form with the tile's halo staged in shared memory.
+//
+// Tiles are visited in Morton order (neighbouring CTAs work on neighbouring tiles, so halo
+// re-reads hit L2), in batches of up to kPBP particles.  A batch with at least `staged_min`
+// particles interpolates from shared-memory copies of its tile's halo -- the
+// (8 + D - 1)^3 nodes around the tile, one bin group (float4) at a time.  The halo copies are
+// the items of a KST-slot cp.async ring that runs KST - 1 items ahead of the interpolation,
+// across batch and tile boundaries, so the copy latency hides behind the work of earlier
+// items.  Each particle's D^3 stencil is read by 8 lanes; rows are padded so that the 8 lanes
+// of one shared-memory phase hit distinct banks.  Sparse batches, and any particle whose
+// cell is not inside its tile (only possible for inconsistent or non-finite input), read the
+// stencil from global memory.
+constexpr int kPBP = 128;  // particles per batch
+constexpr int kKST = 3;    // halo ring slots
+
+template <int D>
+struct Halo {
+  static constexpr int HD = kTile + D - 1;          // nodes per side
+  static constexpr int XP = D == 4 ? 12 : 10;       // row pitch (float4)
+  static constexpr int PP = D == 4 ? HD * XP : 92;  // plane pitch (float4)
+  static constexpr int SIZE = HD * PP;              // float4 per slot
+  static constexpr int NODES = HD * HD * HD;
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
+// Morton index -> one tile coordinate: keeps bits 0, 3, 6, ... of v, packed (nt a power of
+// two, at most 2^21)
+__device__ __forceinline__ int morton_compact(unsigned long long v) {
+  v &= 0x1249249249249249ULL;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ULL;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00fULL;
+  v = (v ^ (v >> 8)) & 0x001f0000ff0000ffULL;
+  v = (v ^ (v >> 16)) & 0x001f00000000ffffULL;
+  v = (v ^ (v >> 32)) & 0x00000000001fffffULL;
+  return static_cast<int>(v);
+}
+
+template <int NBP, int D>
+struct PartSmem {
+  using G = Gram<NBP>;
+  static constexpr size_t HALO = static_cast<size_t>(kKST) * Halo<D>::SIZE * sizeof(float4);
+  static constexpr size_t VALS = static_cast<size_t>(kPBP) * G::NBS * sizeof(float);
+  static constexpr size_t MAIN =
+      HALO + VALS + kPBP * sizeof(float) + kPBP * sizeof(int4) + kPBP * 3 * D * sizeof(float);
+};
+
+// The sequence of (tile, batch) units of one CTA: tile k of the CTA is Morton index
+// blockIdx.x + k * gridDim.x.
+struct TileWalk {
+  const long long* ts;
+  long long ntiles;
+  int nt;
+  __device__ __forceinline__ bool tile(long long k, long long& t, long long& s0, long long& s1, int& tx, int& ty,
+                                       int& tz) const {
+    const long long i = blockIdx.x + k * gridDim.x;
+    if (i >= ntiles) return false;
+    const unsigned long long u = static_cast<unsigned long long>(i);
+    tx = morton_compact(u);
+    ty = morton_compact(u >> 1);
+    tz = morton_compact(u >> 2);
+    t = (static_cast<long long>(tz) * nt + ty) * nt + tx;
+    s0 = ts[t];
+    s1 = ts[t + 1];
+    return true;
+  }
+};
+
+template <int NBP, int D>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_gram_part(const float4* __restrict__ sorted, const long long* __restrict__ tile_start,
+                const float4* __restrict__ f4, long long ng, int n, int nb, double inv_h, int staged_min,
+                double* __restrict__ partials) {
+  using G = Gram<NBP>;
+  using H = Halo<D>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float4* halo = reinterpret_cast<float4*>(smraw);                                   // [KST][SIZE]
+  float* vals = reinterpret_cast<float*>(smraw + kKST * H::SIZE * sizeof(float4));  // [kPBP][NBS]
+  float* wts = vals + kPBP * G::NBS;                                                  // [kPBP]
+  int4* org = reinterpret_cast<int4*>(wts + kPBP);  // [kPBP] global stencil origin; w = halo index or -1
+  float* bw = reinterpret_cast<float*>(org + kPBP);  // [kPBP][3*D] weights x, y, z
+  double* red = reinterpret_cast<double*>(smraw);    // reused after the main loop
+  const int pr = threadIdx.x % G::NPAIR, grp = threadIdx.x / G::NPAIR;
+  int b1 = 0, b2 = 0;
+  pair_blocks(pr, G::NBLK, b1, b2);
+  GramAcc<NBP> g;
+  g.init();
+  const int ngrp = (nb + 3) / 4;
+  const int nt = n / kTile;
+  const TileWalk walk{tile_start, static_cast<long long>(nt) * nt * nt, nt};
+  constexpr int OFF = D / 2 - 1;
+  const int mask = n - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l8 = lane & 7;
+  const double inv_n = 1.0 / n;
+
+  // ---- producer: the next staged (tile, batch, group) item, identical in every thread
+  long long pk = 0, pt = 0, ps0 = 0, ps1 = 0;
+  int ptx = 0, pty = 0, ptz = 0;
+  bool pvalid = walk.tile(0, pt, ps0, ps1, ptx, pty, ptz);
+  long long pbs = ps0;  // batch start
+  int pq = -1;          // group of the last item issued
+  auto p_advance = [&]() {
+    ++pq;
+    while (pvalid) {
+      if (pbs < ps1) {
+        const long long c = ps1 - pbs;
+        if ((c < kPBP ? c : kPBP) >= staged_min && pq < ngrp) return;
+        pbs += kPBP;  // batch done (or not staged)
+        pq = 0;
+      } else {
+        ++pk;
+        pvalid = walk.tile(pk, pt, ps0, ps1, ptx, pty, ptz);
+        pbs = ps0;
+        pq = 0;
+      }
+    }
+  };
+  long long pi = 0;  // items issued
+  // copy lanes: thread = (plane offset hz0, row y, node x) of an HD x HD plane; planes step by
+  // kPlanes (node indices fit in 32 bits: n^3 <= 2^27)
+  constexpr int kPlane = H::HD * H::HD;
+  constexpr int kPlanes = kThreads / kPlane;
+  const int cz0 = threadIdx.x / kPlane, cy = (threadIdx.x % kPlane) / H::HD, cx = threadIdx.x % H::HD;
+  const int n2 = n * n;
+  auto issue_next = [&]() {  // one commit group per call (empty once the sequence ends)
+    p_advance();
+    if (pvalid && cz0 < kPlanes) {
+      const float4* src = f4 + pq * ng + (((pty * kTile - OFF + cy) & mask) * n + ((ptx * kTile - OFF + cx) & mask));
+      float4* dst = halo + (pi % kKST) * H::SIZE + cy * H::XP + cx;
+      const int hz = ptz * kTile - OFF;
+#pragma unroll 2
+      for (int z = cz0; z < H::HD; z += kPlanes) cp_async16(dst + z * H::PP, src + ((hz + z) & mask) * n2);
+    }
+    ++pi;
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int j = 0; j < kKST - 1; ++j) issue_next();
+
+  // ---- consumer
+  long long ci = 0;  // staged items consumed
+  long long t, s0, s1;
+  int tx, ty, tz;
+  for (long long k = 0; walk.tile(k, t, s0, s1, tx, ty, tz); ++k) {
+    for (long long bs = s0; bs < s1; bs += kPBP) {
+      const int cnt = static_cast<int>((s1 - bs) < kPBP ? (s1 - bs) : kPBP);
+      const bool staged = cnt >= staged_min;
+      __syncthreads();  // previous batch's readers of vals and the per-point arrays are done
+      // phase 1: per particle
+      const int me = threadIdx.x;
+      if (me < cnt) {
+        float wx[D], wy[D], wz[D];
+        const float4 pp = sorted[bs + me];
+        const bool fin = isfinite(pp.x) && isfinite(pp.y) && isfinite(pp.z) && isfinite(pp.w);
+        const float pc[3] = {pp.x, pp.y, pp.z};
+        int cix[3];
+        float tt[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          double u = fin ? static_cast<double>(pc[d]) * inv_h : 0.0;
+          u -= floor(u * inv_n) * n;  // 1/n is exact (n a power of two): same as u / n
+          int c = static_cast<int>(floor(u));
+          const double fr = u - c;
+          if (c >= n) c -= n;
+          if (c < 0) c += n;
+          cix[d] = c;
+          tt[d] = static_cast<float>(fr);
+          if (tt[d] >= 1.f) tt[d] = 0.99999994f;
+        }
+        bsw<D>(tt[0], wx);
+        bsw<D>(tt[1], wy);
+        bsw<D>(tt[2], wz);
+        const int lx = cix[0] - tx * kTile, ly = cix[1] - ty * kTile, lz = cix[2] - tz * kTile;
+        const bool inside = lx >= 0 && lx < kTile && ly >= 0 && ly < kTile && lz >= 0 && lz < kTile;
+        org[me] = make_int4(cix[0] - OFF, cix[1] - OFF, cix[2] - OFF,
+                            (staged && inside) ? lz * H::PP + ly * H::XP + lx : -1);
+#pragma unroll
+        for (int o = 0; o < D; ++o) {
+          bw[me * 3 * D + o] = wx[o];
+          bw[me * 3 * D + D + o] = wy[o];
+          bw[me * 3 * D + 2 * D + o] = wz[o];
+        }
+        wts[me] = fin ? pp.w : 0.f;
+#pragma unroll
+        for (int b = 4 * ngrp; b < NBP; ++b) vals[me * G::NBS + b] = 0.f;
+      }
+      // phase 2: one bin group at a time, 8 lanes per particle
+      for (int q = 0; q < ngrp; ++q) {
+        if (staged) cp_async_wait<kKST - 2>();  // this item's copies (this thread's) are done
+        __syncthreads();  // ... and everyone's; phase 1 visible; the previous item's readers done
+        const float4* hb = halo + (ci % kKST) * H::SIZE;
+        if (staged) {
+          issue_next();  // into the slot read by the previous item
+          ++ci;
+        }
+        const float4* gsrc = f4 + q * ng;
+        for (int pb = warp * 4; pb < cnt; pb += (kThreads / 32) * 4) {  // warp-uniform
+          const int p = pb + (lane >> 3);
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (p < cnt) {
+            const int4 o = org[p];
+            const float* w = bw + p * 3 * D;
+            if (D == 4) {
+              const int ox = l8 & 3, oy0 = l8 >> 2;
+              const float wx = w[ox];
+              if (o.w >= 0) {
+                const float4* hp = hb + o.w + ox;
+#pragma unroll
+                for (int oz = 0; oz < 4; ++oz)
+#pragma unroll
+                  for (int j = 0; j < 2; ++j) {
+                    const int oy = oy0 + 2 * j;
+                    const float ww = w[2 * D + oz] * w[D + oy] * wx;
+                    const float4 v = hp[oz * H::PP + oy * H::XP];
+                    acc.x = fmaf(ww, v.x, acc.x);
+                    acc.y = fmaf(ww, v.y, acc.y);
+                    acc.z = fmaf(ww, v.z, acc.z);
+                    acc.w = fmaf(ww, v.w, acc.w);
+                  }
+              } else {
+                const int xo = (o.x + ox) & mask;
+#pragma unroll
+                for (int oz = 0; oz < 4; ++oz)
+#pragma unroll
+                  for (int j = 0; j < 2; ++j) {
+                    const int oy = oy0 + 2 * j;
+                    const float ww = w[2 * D + oz] * w[D + oy] * wx;
+                    const long long gi =
+                        (static_cast<long long>((o.z + oz) & mask) * n + ((o.y + oy) & mask)) * n + xo;
+                    const float4 v = __ldg(gsrc + gi);
+                    acc.x = fmaf(ww, v.x, acc.x);
+                    acc.y = fmaf(ww, v.y, acc.y);
+                    acc.z = fmaf(ww, v.z, acc.z);
+                    acc.w = fmaf(ww, v.w, acc.w);
+                  }
+              }
+            } else {  // D == 2: one node per lane
+              const int ox = l8 & 1, oy = (l8 >> 1) & 1, oz = l8 >> 2;
+              const float ww = w[2 * D + oz] * w[D + oy] * w[ox];
+              float4 v;
+              if (o.w >= 0) {
+                v = hb[o.w + oz * H::PP + oy * H::XP + ox];
+              } else {
+                const long long gi = (static_cast<long long>((o.z + oz) & mask) * n + ((o.y + oy) & mask)) * n +
+                                     ((o.x + ox) & mask);
+                v = __ldg(gsrc + gi);
+              }
+              acc = make_float4(ww * v.x, ww * v.y, ww * v.z, ww * v.w);
+            }
+          }
+#pragma unroll
+          for (int off = 1; off < 8; off <<= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off, 8);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off, 8);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off, 8);
+            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off, 8);
+          }
+          if (p < cnt && l8 == 0) *reinterpret_cast<float4*>(vals + p * G::NBS + 4 * q) = acc;
+        }
+      }
+      __syncthreads();
+      if (grp < G::NGRP) g.add(vals, wts, cnt, b1, b2, grp);
+    }
+  }
+  cp_async_wait<0>();  // only empty groups can remain; drain before the buffer is reused
+  __syncthreads();
+  cta_store<NBP>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb);
+}
+
+// ---------------------------------------------------------------------------------------
 // Mass (uniform) term: points = stored half-spectrum modes.
 template <int NBP>
 __global__ void __launch_bounds__(kThreads) k_gram_mass(const float2* __restrict__ dhat, const float* __restrict__ jt,
@@ -410,6 +689,12 @@ size_t smem_points() {
   return main > red_bytes<NBP>() ? main : red_bytes<NBP>();
 }
 
+template <int NBP, int D>
+size_t smem_part() {
+  const size_t main = PartSmem<NBP, D>::MAIN;
+  return main > red_bytes<NBP>() ? main : red_bytes<NBP>();
+}
+
 template <typename K>
 int prep(K kernel, size_t bytes) {
   return ensure_smem(reinterpret_cast<const void*>(kernel), bytes);
@@ -435,6 +720,18 @@ int points_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_sta
       sorted, reinterpret_cast<const long long*>(tile_start), delta, reinterpret_cast<const float4*>(alm), c->ng,
       c->n, c->p.nbins, c->n / c->p.box,
       c->d_gq, c->gamma_q, partials);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
+template <int NBP, int D>
+int part_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, const float* alm, double* partials,
+              cudaStream_t s) {
+  StageScope prof(c, ST_GRAM_PART, 1, s);
+  const size_t sm = smem_part<NBP, D>();
+  if (prep(k_gram_part<NBP, D>, sm)) return ZETA_ECUDA;
+  k_gram_part<NBP, D><<<gram_ctas(c, GK_PART), kThreads, sm, s>>>(
+      sorted, reinterpret_cast<const long long*>(tile_start), reinterpret_cast<const float4*>(alm), c->ng, c->n,
+      c->p.nbins, c->n / c->p.box, c->staged_min, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
@@ -488,11 +785,11 @@ int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, d
 int launch_gram_particles(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, const float* alm,
                           double* partials, cudaStream_t s) {
   if (c->p.dsup == 2) {
-#define ZK_CALL(P) points_impl<P, 2, 0>(c, sorted, tile_start, nullptr, alm, partials, s)
+#define ZK_CALL(P) part_impl<P, 2>(c, sorted, tile_start, alm, partials, s)
     ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
 #undef ZK_CALL
   } else {
-#define ZK_CALL(P) points_impl<P, 4, 0>(c, sorted, tile_start, nullptr, alm, partials, s)
+#define ZK_CALL(P) part_impl<P, 4>(c, sorted, tile_start, alm, partials, s)
     ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
 #undef ZK_CALL
   }

@@ -60,6 +60,8 @@ _SIGS = {
     "zeta_backward_particles": ([_VP, _VP, _I64, _VP, _VP, _VP], _INT),
     "zeta_autotune": ([_VP, _VP, _I64, _INT, _VP], _INT),
     "zeta_get_tuning": ([_VP, _VP, _INT], _INT),
+    "zeta_set_staging": ([_VP, _INT], _INT),
+    "zeta_get_staging": ([_VP], _INT),
     "zeta_assign_noalloc": ([_INT, _DBL, _INT, _VP, _I64, _VP, _VP, _VP], _INT),
     "zeta_profile_enable": ([_VP, _INT], _INT),
     "zeta_profile_read": ([_VP, _VP, _VP, _VP, _INT], _INT),
@@ -283,6 +285,13 @@ class Context:
 
     def set_gram(self, gram: str):
         _check("zeta_set_gram", lib().zeta_set_gram(self._h, GRAM[gram]))
+
+    def set_staging(self, min_particles: int):
+        """zeta_set_staging: tile batches with >= min_particles particles stage their halo."""
+        _check("zeta_set_staging", lib().zeta_set_staging(self._h, int(min_particles)))
+
+    def staging(self) -> int:
+        return int(lib().zeta_get_staging(self._h))
 
     def _weights(self, w):
         if hasattr(w, "detach"):

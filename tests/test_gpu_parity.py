@@ -117,12 +117,17 @@ def _clustered(n_p, box, seed):
     return p
 
 
+@pytest.mark.parametrize("staging", [0, 16, 257])
 @pytest.mark.parametrize("n,dsup,nb", [(32, 4, 5), (32, 2, 12), (16, 4, 9)])
-def test_sort_and_particle_sum_match_oracle(Z, n, dsup, nb):
+def test_sort_and_particle_sum_match_oracle(Z, n, dsup, nb, staging):
+    # staging 0: every tile batch interpolates from its shared-memory halo; 257: every one
+    # from global memory; 16: both kinds in one launch (sparse and dense tiles)
     box = 120.0
     edges = np.linspace(5.0, 40.0, nb + 1)
     parts = _clustered(3001, box, 9)
     ctx = Z.Context(n, box, dsup, 1, edges, np_max=len(parts), forms=("particle",))
+    ctx.set_staging(staging)
+    assert ctx.staging() == staging
     pd = _dev(parts)
     srt, start = ctx.sort_particles(pd)
     srt, start = srt.cpu().numpy(), start.cpu().numpy()
@@ -139,6 +144,12 @@ def test_sort_and_particle_sum_match_oracle(Z, n, dsup, nb):
     got = ctx.sum_particles(_dev(srt), _dev(start), wsum, _dev(Z.interleave(a))).cpu().numpy()
     want = O.sum_particles(a.astype(np.float64), parts[:, :3], parts[:, 3], n, box, dsup)
     assert _rel(got, want) < 1e-5
+    # a particle listed under the wrong tile is still interpolated at its own position
+    moved = srt.copy()
+    moved[5, 0] = (moved[5, 0] + 8.5 * box / n) % box
+    got_m = ctx.sum_particles(_dev(moved), _dev(start), wsum, _dev(Z.interleave(a))).cpu().numpy()
+    want_m = O.sum_particles(a.astype(np.float64), moved[:, :3], moved[:, 3], n, box, dsup)
+    assert _rel(got_m, want_m) < 1e-5
 
 
 @pytest.mark.parametrize("dsup", [2, 4])
