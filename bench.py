@@ -386,9 +386,11 @@ def run_ours(args, w, rank, world, local_rank):
         # dominant memory-bound kernel
         rows = {k: v for k, v in prof.items() if v[1] > 0 and _alg_bytes(k, w, nb) is not None}
         dom = max(rows, key=lambda k: rows[k][0])
-        ms_k, launches_k, _ = rows[dom]
+        # per call of the stage (a stage is one kernel launch per call, except the particle
+        # form when its threshold splits tile batches between the staged and the L1 kernel)
+        ms_k, launches_k, calls_k = rows[dom]
         bytes_launch = _alg_bytes(dom, w, nb)
-        achieved = bytes_launch * launches_k / (ms_k / 1e3) / 1e9
+        achieved = bytes_launch * calls_k / (ms_k / 1e3) / 1e9
         src = {"alm_z": "fft.cu", "alm_y": "fft.cu", "alm_x": "fft.cu", "r2c": "fft.cu",
                "gram_particles": "sums.cu", "gram_node": "sums.cu", "mass": "sums.cu"}[dom]
         tr = NCU_TRAFFIC.get(dom)
@@ -409,8 +411,8 @@ def run_ours(args, w, rank, world, local_rank):
                        "parallelism": f"catalogue-per-gpu x{world}"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
-                         "alg_bytes_per_launch": bytes_launch, "launches": launches_k,
-                         "avg_launch_ms": ms_k / launches_k},
+                         "alg_bytes_per_call": bytes_launch, "calls": calls_k, "launches": launches_k,
+                         "avg_call_ms": ms_k / calls_k},
             "stages_ms_per_step": stages,
             "clocks": ck,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(parts.nbytes),

@@ -215,11 +215,16 @@ int zeta_autotune(zeta_ctx* ctx, const float* particles, int64_t np, int forms, 
  * node tensor-core].  Returns 5. */
 int zeta_get_tuning(const zeta_ctx* ctx, int* ctas_per_sm, int n);
 
-/* Particle form: a batch of up to 256 particles of one 8x8x8-cell tile copies the tile's
+/* Set the first n (<= 5) persistent grid sizes, same order as zeta_get_tuning, e.g. to
+ * restore a tuning saved from an earlier run.  Each value must be in [1, 16], else
+ * ZETA_EINVAL and nothing changes.  Drops a cached batch graph. */
+int zeta_set_tuning(zeta_ctx* ctx, const int* ctas_per_sm, int n);
+
+/* Particle form: a batch of up to 128 particles of one 8x8x8-cell tile copies the tile's
  * halo of the fields into shared memory when it holds at least `min_particles` particles
- * (0: always; a value above 256: never) and otherwise reads each stencil from global memory.
+ * (0: always; a value above 128: never) and otherwise reads each stencil through L1.
  * Both give the same sums up to float32 rounding order; the choice only moves time.
- * Default 16; zeta_autotune also picks it.  min_particles < 0 -> ZETA_EINVAL.  No counterpart
+ * Default 0; zeta_autotune also picks it.  min_particles < 0 -> ZETA_EINVAL.  No counterpart
  * in the paper (an execution choice of this implementation). */
 int zeta_set_staging(zeta_ctx* ctx, int min_particles);
 /* The current threshold of zeta_set_staging (>= 0), or ZETA_EINVAL for a null context. */

@@ -262,7 +262,7 @@ int zeta_sum_particles(zeta_ctx* c, const float* sorted, const int64_t* tile_sta
   const Layout L = layout(c, 0);
   double* part = at<double>(c, L.partials);
   ZK_TRY(launch_gram_particles(c, reinterpret_cast<const float4*>(sorted), tile_start, alm, part, stream));
-  return launch_reduce(c, part, gram_ctas(c, GK_PART), 1.0, wsum, gram, stream);
+  return launch_reduce(c, part, gram_particle_parts(c), 1.0, wsum, gram, stream);
 }
 
 int zeta_mass_term(zeta_ctx* c, const float* delta_hat, int l, double sign, double* gram, zeta_stream stream) {
@@ -333,7 +333,7 @@ int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* 
       }
       if (idx_part >= 0) {
         ZK_TRY(launch_gram_particles(c, sorted, tstart, fields, part, stream));
-        ZK_TRY(launch_reduce(c, part, gram_ctas(c, GK_PART), 1.0, wsum,
+        ZK_TRY(launch_reduce(c, part, gram_particle_parts(c), 1.0, wsum,
                              zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb, stream));
       }
     }
@@ -493,6 +493,16 @@ int zeta_set_staging(zeta_ctx* c, int min_particles) {
 int zeta_get_staging(const zeta_ctx* c) {
   if (!c) return ZETA_EINVAL;
   return c->staged_min;
+}
+
+int zeta_set_tuning(zeta_ctx* c, const int* ctas_per_sm, int n) {
+  ZK_TRY(check_ctx(c));
+  if (!ctas_per_sm || n < 0 || n > 5) return ZETA_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (ctas_per_sm[i] < 1 || ctas_per_sm[i] > 16) return ZETA_EINVAL;
+  for (int i = 0; i < n; ++i) c->tune[i] = ctas_per_sm[i];
+  drop_batch_graph(c);
+  return ZETA_OK;
 }
 
 int zeta_get_tuning(const zeta_ctx* c, int* ctas_per_sm, int n) {

@@ -25,11 +25,11 @@ constexpr int kPB = 256;  // points per batch (one per thread in the interpolati
 // arithmetic is a small fraction of float32 throughput on this part, so flushes are rare)
 constexpr int kFlush = 128;
 
-template <int NBP>
+template <int NBP, int NT = kThreads>
 struct Gram {
   static constexpr int NBLK = NBP / 4;
   static constexpr int NPAIR = NBLK * (NBLK + 1) / 2;
-  static constexpr int NGRP = kThreads / NPAIR;
+  static constexpr int NGRP = NT / NPAIR;
   static constexpr int NBS = NBP + 4;  // shared-memory row stride of the value table
 };
 
@@ -43,7 +43,7 @@ __device__ __forceinline__ void pair_blocks(int p, int nblk, int& b1, int& b2) {
   b2 = r + p;
 }
 
-template <int NBP>
+template <int NBP, int NT = kThreads>
 struct GramAcc {
   float acc[4][4];
   double dacc[4][4];
@@ -70,7 +70,7 @@ struct GramAcc {
   }
   // vals: [npts][NBS] shared, wts: [npts] shared
   __device__ __forceinline__ void add(const float* vals, const float* wts, int npts, int b1, int b2, int grp) {
-    for (int pt = grp; pt < npts; pt += Gram<NBP>::NGRP) {
+    for (int pt = grp; pt < npts; pt += Gram<NBP, NT>::NGRP) {
       const float w = wts[pt];
       const float4 x = *reinterpret_cast<const float4*>(vals + pt * Gram<NBP>::NBS + 4 * b1);
       const float4 y = *reinterpret_cast<const float4*>(vals + pt * Gram<NBP>::NBS + 4 * b2);
@@ -87,9 +87,9 @@ struct GramAcc {
 
 // Reduce the per-thread accumulators of a CTA (fixed order) and write its partial
 // [NB][NB] (upper triangle valid) to part.  red: shared double buffer NGRP*NPAIR*16.
-template <int NBP>
-__device__ void cta_store(GramAcc<NBP>& g, double* red, int nb, double* part) {
-  using G = Gram<NBP>;
+template <int NBP, int NT = kThreads>
+__device__ void cta_store(GramAcc<NBP, NT>& g, double* red, int nb, double* part) {
+  using G = Gram<NBP, NT>;
   g.flush();
   const int tid = threadIdx.x;
   const int pr = tid % G::NPAIR, grp = tid / G::NPAIR;
@@ -185,7 +185,6 @@ __global__ void __launch_bounds__(kThreads)
                   const float* __restrict__ delta, const float4* __restrict__ f4, long long ng, int n, int nb,
                   double inv_h, const float* __restrict__ gq, int q, double* __restrict__ partials) {
   using G = Gram<NBP>;
-  constexpr int GMAX = NBP / 4;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* vals = reinterpret_cast<float*>(smraw);    // [kPB][NBS]
   float* wts = vals + kPB * G::NBS;                  // [kPB]
@@ -344,9 +343,9 @@ __global__ void __launch_bounds__(kThreads)
 // the items of a KST-slot cp.async ring that runs KST - 1 items ahead of the interpolation,
 // across batch and tile boundaries, so the copy latency hides behind the work of earlier
 // items.  Each particle's D^3 stencil is read by 8 lanes; rows are padded so that the 8 lanes
-// of one shared-memory phase hit distinct banks.  Sparse batches, and any particle whose
-// cell is not inside its tile (only possible for inconsistent or non-finite input), read the
-// stencil from global memory.
+// of one shared-memory phase hit distinct banks.  Sparser batches are left to
+// k_gram_part_l1; a particle whose cell is not inside its tile (only possible for
+// inconsistent or non-finite input) reads its stencil from global memory.
 constexpr int kPBP = 128;  // particles per batch
 constexpr int kKST = 3;    // halo ring slots
 
@@ -356,7 +355,6 @@ struct Halo {
   static constexpr int XP = D == 4 ? 12 : 10;       // row pitch (float4)
   static constexpr int PP = D == 4 ? HD * XP : 92;  // plane pitch (float4)
   static constexpr int SIZE = HD * PP;              // float4 per slot
-  static constexpr int NODES = HD * HD * HD;
 };
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -386,25 +384,57 @@ struct PartSmem {
   using G = Gram<NBP>;
   static constexpr size_t HALO = static_cast<size_t>(kKST) * Halo<D>::SIZE * sizeof(float4);
   static constexpr size_t VALS = static_cast<size_t>(kPBP) * G::NBS * sizeof(float);
+  // per-particle weights: D = 4: the 16 products wz * wy in lane order, then wx[4];
+  // D = 2: the 8 node weights
+  static constexpr int PW = D == 4 ? 20 : 8;
   static constexpr size_t MAIN =
-      HALO + VALS + kPBP * sizeof(float) + kPBP * sizeof(int4) + kPBP * 3 * D * sizeof(float);
+      HALO + VALS + kPBP * sizeof(float) + kPBP * sizeof(int4) + static_cast<size_t>(kPBP) * PW * sizeof(float);
 };
 
-// The sequence of (tile, batch) units of one CTA: tile k of the CTA is Morton index
-// blockIdx.x + k * gridDim.x.
+// Sum a float4 over the 8 lanes of an aligned lane group (reduce-scatter): afterwards lanes
+// with bit 0 clear hold component 2*bit2 + bit1 of the total in the return value.
+__device__ __forceinline__ float sum8_scatter(float4 a, int l8) {
+  const bool b2 = l8 & 4, b1 = l8 & 2;
+  const float s0 = b2 ? a.x : a.z, s1 = b2 ? a.y : a.w;
+  float k0 = b2 ? a.z : a.x, k1 = b2 ? a.w : a.y;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 4);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 4);
+  const float s = b1 ? k0 : k1;
+  float k = b1 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, s, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
+// Cell of a coordinate and the offset in it, wrapped into [0, n): u = x / H in float64, the
+// cell floor(u) and t = u - floor(u) in [0, 1).  The periodic reduction of u is applied only
+// when u is outside [0, n) -- for u inside it is the identity -- and 1/n is exact for n a
+// power of two, so the result equals that of the assignment kernel's u - floor(u / n) n.
+__device__ __forceinline__ int cell_frac(float x, double inv_h, int n, double inv_n, float& t) {
+  double u = static_cast<double>(x) * inv_h;
+  if (!(u >= 0.0 && u < n)) u -= floor(u * inv_n) * n;
+  const double fl = floor(u);
+  int c = static_cast<int>(fl);
+  t = static_cast<float>(u - fl);
+  if (c >= n) c -= n;
+  if (c < 0) c += n;
+  if (t >= 1.f) t = 0.99999994f;
+  return c;
+}
+
+// The tiles of one CTA in order: tile k is Morton index blockIdx.x + k * gridDim.x.
 struct TileWalk {
   const long long* ts;
   long long ntiles;
   int nt;
-  __device__ __forceinline__ bool tile(long long k, long long& t, long long& s0, long long& s1, int& tx, int& ty,
-                                       int& tz) const {
+  __device__ __forceinline__ bool tile(long long k, long long& s0, long long& s1, int& tx, int& ty, int& tz) const {
     const long long i = blockIdx.x + k * gridDim.x;
     if (i >= ntiles) return false;
     const unsigned long long u = static_cast<unsigned long long>(i);
     tx = morton_compact(u);
     ty = morton_compact(u >> 1);
     tz = morton_compact(u >> 2);
-    t = (static_cast<long long>(tz) * nt + ty) * nt + tx;
+    const long long t = (static_cast<long long>(tz) * nt + ty) * nt + tx;
     s0 = ts[t];
     s1 = ts[t + 1];
     return true;
@@ -423,7 +453,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   float* vals = reinterpret_cast<float*>(smraw + kKST * H::SIZE * sizeof(float4));  // [kPBP][NBS]
   float* wts = vals + kPBP * G::NBS;                                                  // [kPBP]
   int4* org = reinterpret_cast<int4*>(wts + kPBP);  // [kPBP] global stencil origin; w = halo index or -1
-  float* bw = reinterpret_cast<float*>(org + kPBP);  // [kPBP][3*D] weights x, y, z
+  constexpr int PW = PartSmem<NBP, D>::PW;
+  float* bw = reinterpret_cast<float*>(org + kPBP);  // [kPBP][PW] stencil weights
   double* red = reinterpret_cast<double*>(smraw);    // reused after the main loop
   const int pr = threadIdx.x % G::NPAIR, grp = threadIdx.x / G::NPAIR;
   int b1 = 0, b2 = 0;
@@ -432,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   g.init();
   const int ngrp = (nb + 3) / 4;
   const int nt = n / kTile;
-  const TileWalk walk{tile_start, static_cast<long long>(nt) * nt * nt, nt};
+  const long long ntiles = static_cast<long long>(nt) * nt * nt;
   constexpr int OFF = D / 2 - 1;
   const int mask = n - 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -440,9 +471,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   const double inv_n = 1.0 / n;
 
   // ---- producer: the next staged (tile, batch, group) item, identical in every thread
-  long long pk = 0, pt = 0, ps0 = 0, ps1 = 0;
+  const TileWalk walk{tile_start, ntiles, nt};
+  long long pk = 0, ps0 = 0, ps1 = 0;
   int ptx = 0, pty = 0, ptz = 0;
-  bool pvalid = walk.tile(0, pt, ps0, ps1, ptx, pty, ptz);
+  bool pvalid = walk.tile(0, ps0, ps1, ptx, pty, ptz);
   long long pbs = ps0;  // batch start
   int pq = -1;          // group of the last item issued
   auto p_advance = [&]() {
@@ -454,14 +486,17 @@ __global__ void __launch_bounds__(kThreads, 2)
         pbs += kPBP;  // batch done (or not staged)
         pq = 0;
       } else {
-        ++pk;
-        pvalid = walk.tile(pk, pt, ps0, ps1, ptx, pty, ptz);
+        pvalid = walk.tile(++pk, ps0, ps1, ptx, pty, ptz);
         pbs = ps0;
         pq = 0;
       }
     }
   };
   long long pi = 0;  // items issued
+  // this thread's particle of the next batch, loaded when that batch's first item is issued
+  // (at least kKST - 1 items before the batch starts when every batch has >= 2 groups)
+  const bool pf = ngrp >= kKST - 1;
+  float4 ppn = make_float4(0.f, 0.f, 0.f, 0.f);
   // copy lanes: thread = (plane offset hz0, row y, node x) of an HD x HD plane; planes step by
   // kPlanes (node indices fit in 32 bits: n^3 <= 2^27)
   constexpr int kPlane = H::HD * H::HD;
@@ -470,6 +505,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int n2 = n * n;
   auto issue_next = [&]() {  // one commit group per call (empty once the sequence ends)
     p_advance();
+    if (pf && pvalid && pq == 0 && threadIdx.x < ps1 - pbs) ppn = __ldg(sorted + pbs + threadIdx.x);
     if (pvalid && cz0 < kPlanes) {
       const float4* src = f4 + pq * ng + (((pty * kTile - OFF + cy) & mask) * n + ((ptx * kTile - OFF + cx) & mask));
       float4* dst = halo + (pi % kKST) * H::SIZE + cy * H::XP + cx;
@@ -485,34 +521,25 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   // ---- consumer
   long long ci = 0;  // staged items consumed
-  long long t, s0, s1;
+  long long s0, s1;
   int tx, ty, tz;
-  for (long long k = 0; walk.tile(k, t, s0, s1, tx, ty, tz); ++k) {
+  for (long long k = 0; walk.tile(k, s0, s1, tx, ty, tz); ++k) {
     for (long long bs = s0; bs < s1; bs += kPBP) {
       const int cnt = static_cast<int>((s1 - bs) < kPBP ? (s1 - bs) : kPBP);
-      const bool staged = cnt >= staged_min;
+      if (cnt < staged_min) continue;  // k_gram_part_l1 takes this batch
+      constexpr bool staged = true;
       __syncthreads();  // previous batch's readers of vals and the per-point arrays are done
       // phase 1: per particle
       const int me = threadIdx.x;
       if (me < cnt) {
         float wx[D], wy[D], wz[D];
-        const float4 pp = sorted[bs + me];
+        const float4 pp = pf ? ppn : sorted[bs + me];
         const bool fin = isfinite(pp.x) && isfinite(pp.y) && isfinite(pp.z) && isfinite(pp.w);
         const float pc[3] = {pp.x, pp.y, pp.z};
         int cix[3];
         float tt[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          double u = fin ? static_cast<double>(pc[d]) * inv_h : 0.0;
-          u -= floor(u * inv_n) * n;  // 1/n is exact (n a power of two): same as u / n
-          int c = static_cast<int>(floor(u));
-          const double fr = u - c;
-          if (c >= n) c -= n;
-          if (c < 0) c += n;
-          cix[d] = c;
-          tt[d] = static_cast<float>(fr);
-          if (tt[d] >= 1.f) tt[d] = 0.99999994f;
-        }
+        for (int d = 0; d < 3; ++d) cix[d] = cell_frac(fin ? pc[d] : 0.f, inv_h, n, inv_n, tt[d]);
         bsw<D>(tt[0], wx);
         bsw<D>(tt[1], wy);
         bsw<D>(tt[2], wz);
@@ -520,11 +547,19 @@ __global__ void __launch_bounds__(kThreads, 2)
         const bool inside = lx >= 0 && lx < kTile && ly >= 0 && ly < kTile && lz >= 0 && lz < kTile;
         org[me] = make_int4(cix[0] - OFF, cix[1] - OFF, cix[2] - OFF,
                             (staged && inside) ? lz * H::PP + ly * H::XP + lx : -1);
+        float* pw = bw + me * PW;
+        if (D == 4) {  // lane (ox, oy0) takes nodes (oz, oy0 + 2 j): products [oy0][oz][j]
 #pragma unroll
-        for (int o = 0; o < D; ++o) {
-          bw[me * 3 * D + o] = wx[o];
-          bw[me * 3 * D + D + o] = wy[o];
-          bw[me * 3 * D + 2 * D + o] = wz[o];
+          for (int oy0 = 0; oy0 < 2; ++oy0)
+#pragma unroll
+            for (int oz = 0; oz < 4; ++oz)
+#pragma unroll
+              for (int j = 0; j < 2; ++j) pw[oy0 * 8 + oz * 2 + j] = wz[oz] * wy[oy0 + 2 * j];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) pw[16 + o] = wx[o];
+        } else {  // lane (ox, oy, oz) = bits (0, 1, 2)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) pw[e] = wz[(e >> 2) & 1] * wy[(e >> 1) & 1] * wx[e & 1];
         }
         wts[me] = fin ? pp.w : 0.f;
 #pragma unroll
@@ -545,23 +580,26 @@ __global__ void __launch_bounds__(kThreads, 2)
           float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
           if (p < cnt) {
             const int4 o = org[p];
-            const float* w = bw + p * 3 * D;
+            const float* w = bw + p * PW;
             if (D == 4) {
               const int ox = l8 & 3, oy0 = l8 >> 2;
-              const float wx = w[ox];
+              const float4 ya = *reinterpret_cast<const float4*>(w + oy0 * 8);
+              const float4 yb = *reinterpret_cast<const float4*>(w + oy0 * 8 + 4);
+              const float wx = w[16 + ox];
+              const float ww[8] = {ya.x * wx, ya.y * wx, ya.z * wx, ya.w * wx,
+                                   yb.x * wx, yb.y * wx, yb.z * wx, yb.w * wx};  // [oz][j]
               if (o.w >= 0) {
-                const float4* hp = hb + o.w + ox;
+                const float4* hp = hb + o.w + oy0 * H::XP + ox;
 #pragma unroll
                 for (int oz = 0; oz < 4; ++oz)
 #pragma unroll
                   for (int j = 0; j < 2; ++j) {
-                    const int oy = oy0 + 2 * j;
-                    const float ww = w[2 * D + oz] * w[D + oy] * wx;
-                    const float4 v = hp[oz * H::PP + oy * H::XP];
-                    acc.x = fmaf(ww, v.x, acc.x);
-                    acc.y = fmaf(ww, v.y, acc.y);
-                    acc.z = fmaf(ww, v.z, acc.z);
-                    acc.w = fmaf(ww, v.w, acc.w);
+                    const float4 v = hp[oz * H::PP + 2 * j * H::XP];
+                    const float c = ww[oz * 2 + j];
+                    acc.x = fmaf(c, v.x, acc.x);
+                    acc.y = fmaf(c, v.y, acc.y);
+                    acc.z = fmaf(c, v.z, acc.z);
+                    acc.w = fmaf(c, v.w, acc.w);
                   }
               } else {
                 const int xo = (o.x + ox) & mask;
@@ -570,19 +608,19 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                   for (int j = 0; j < 2; ++j) {
                     const int oy = oy0 + 2 * j;
-                    const float ww = w[2 * D + oz] * w[D + oy] * wx;
                     const long long gi =
                         (static_cast<long long>((o.z + oz) & mask) * n + ((o.y + oy) & mask)) * n + xo;
                     const float4 v = __ldg(gsrc + gi);
-                    acc.x = fmaf(ww, v.x, acc.x);
-                    acc.y = fmaf(ww, v.y, acc.y);
-                    acc.z = fmaf(ww, v.z, acc.z);
-                    acc.w = fmaf(ww, v.w, acc.w);
+                    const float c = ww[oz * 2 + j];
+                    acc.x = fmaf(c, v.x, acc.x);
+                    acc.y = fmaf(c, v.y, acc.y);
+                    acc.z = fmaf(c, v.z, acc.z);
+                    acc.w = fmaf(c, v.w, acc.w);
                   }
               }
             } else {  // D == 2: one node per lane
               const int ox = l8 & 1, oy = (l8 >> 1) & 1, oz = l8 >> 2;
-              const float ww = w[2 * D + oz] * w[D + oy] * w[ox];
+              const float c = w[l8];
               float4 v;
               if (o.w >= 0) {
                 v = hb[o.w + oz * H::PP + oy * H::XP + ox];
@@ -591,17 +629,11 @@ __global__ void __launch_bounds__(kThreads, 2)
                                      ((o.x + ox) & mask);
                 v = __ldg(gsrc + gi);
               }
-              acc = make_float4(ww * v.x, ww * v.y, ww * v.z, ww * v.w);
+              acc = make_float4(c * v.x, c * v.y, c * v.z, c * v.w);
             }
           }
-#pragma unroll
-          for (int off = 1; off < 8; off <<= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off, 8);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off, 8);
-            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off, 8);
-            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off, 8);
-          }
-          if (p < cnt && l8 == 0) *reinterpret_cast<float4*>(vals + p * G::NBS + 4 * q) = acc;
+          const float tot = sum8_scatter(acc, l8);
+          if (p < cnt && !(l8 & 1)) vals[p * G::NBS + 4 * q + (l8 >> 1)] = tot;
         }
       }
       __syncthreads();
@@ -611,6 +643,174 @@ __global__ void __launch_bounds__(kThreads, 2)
   cp_async_wait<0>();  // only empty groups can remain; drain before the buffer is reused
   __syncthreads();
   cta_store<NBP>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb);
+}
+
+// ---------------------------------------------------------------------------------------
+// Particle form from L1-cached global loads, for batches the staged kernel leaves out.
+//
+// One CTA of 512 threads works on one tile batch at a time, so the tile's halo of every
+// bin group (about 100 KB for 20 bins) stays resident in L1 while all warps read it.  A
+// particle's stencil is read by D * ngrp lanes at once -- lane (q, ox) accumulates the D^2
+// rows of bin group q at x offset ox, 16-byte loads, D^2 of them independent -- and the D
+// partial sums of a group are combined by a reduce-scatter over the x lanes, so no barrier
+// separates the bin groups.
+constexpr int kThreadsL1 = 512;
+constexpr int kPBL = 128;  // particles per batch
+
+template <int NBP, int D>
+struct PartL1Smem {
+  using G = Gram<NBP, kThreadsL1>;
+  static constexpr int PW = PartSmem<NBP, D>::PW;
+  static constexpr size_t MAIN = static_cast<size_t>(kPBL) * G::NBS * sizeof(float) + kPBL * sizeof(float) +
+                                 kPBL * sizeof(int4) + static_cast<size_t>(kPBL) * PW * sizeof(float);
+  static constexpr size_t RED = static_cast<size_t>(G::NGRP) * G::NPAIR * 16 * sizeof(double);
+  static constexpr size_t BYTES = MAIN > RED ? MAIN : RED;
+};
+
+template <int NBP, int D>
+__global__ void __launch_bounds__(kThreadsL1, 1)
+    k_gram_part_l1(const float4* __restrict__ sorted, const long long* __restrict__ tile_start,
+                   const float4* __restrict__ f4, long long ng, int n, int nb, double inv_h, int staged_min,
+                   double* __restrict__ partials) {
+  using G = Gram<NBP, kThreadsL1>;
+  constexpr int PW = PartL1Smem<NBP, D>::PW;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* vals = reinterpret_cast<float*>(smraw);  // [kPBL][NBS]
+  float* wts = vals + kPBL * G::NBS;              // [kPBL]
+  int4* org = reinterpret_cast<int4*>(wts + kPBL);  // [kPBL] stencil origin (cells, wrapped later)
+  float* bw = reinterpret_cast<float*>(org + kPBL);  // [kPBL][PW]
+  double* red = reinterpret_cast<double*>(smraw);    // reused after the main loop
+  const int pr = threadIdx.x % G::NPAIR, grp = threadIdx.x / G::NPAIR;
+  int b1 = 0, b2 = 0;
+  pair_blocks(pr, G::NBLK, b1, b2);
+  GramAcc<NBP, kThreadsL1> g;
+  g.init();
+  const int ngrp = (nb + 3) / 4;
+  const int nt = n / kTile;
+  const TileWalk walk{tile_start, static_cast<long long>(nt) * nt * nt, nt};
+  constexpr int OFF = D / 2 - 1;
+  const int mask = n - 1, n2 = n * n;
+  const double inv_n = 1.0 / n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = kThreadsL1 / 32;
+  // lane -> (particle slot, bin group, x offset)
+  const int LP = D * ngrp, PPW = 32 / LP;
+  const int ps = lane / LP, q = (lane % LP) / D, ox = lane % D;
+  const bool lane_on = ps < PPW;
+  const float4* gq4 = f4 + q * ng;
+  long long s0, s1;
+  int tx, ty, tz;
+  for (long long k = 0; walk.tile(k, s0, s1, tx, ty, tz); ++k) {
+    for (long long bs = s0; bs < s1; bs += kPBL) {
+      const int cnt = static_cast<int>((s1 - bs) < kPBL ? (s1 - bs) : kPBL);
+      if (cnt >= staged_min) continue;  // the staged kernel takes this batch
+      __syncthreads();  // previous batch's readers are done
+      const int me = threadIdx.x;
+      if (me < cnt) {
+        float wx[D], wy[D], wz[D];
+        const float4 pp = sorted[bs + me];
+        const bool fin = isfinite(pp.x) && isfinite(pp.y) && isfinite(pp.z) && isfinite(pp.w);
+        const float pc[3] = {pp.x, pp.y, pp.z};
+        int cix[3];
+        float tt[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cix[d] = cell_frac(fin ? pc[d] : 0.f, inv_h, n, inv_n, tt[d]);
+        bsw<D>(tt[0], wx);
+        bsw<D>(tt[1], wy);
+        bsw<D>(tt[2], wz);
+        org[me] = make_int4(cix[0] - OFF, cix[1] - OFF, cix[2] - OFF, 0);
+        float* pw = bw + me * PW;
+        if (D == 4) {  // [oz][oy] products wz * wy, then wx[4]
+#pragma unroll
+          for (int oz = 0; oz < 4; ++oz)
+#pragma unroll
+            for (int oy = 0; oy < 4; ++oy) pw[oz * 4 + oy] = wz[oz] * wy[oy];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) pw[16 + o] = wx[o];
+        } else {  // [oz][oy][ox] node weights
+#pragma unroll
+          for (int e = 0; e < 8; ++e) pw[e] = wz[(e >> 2) & 1] * wy[(e >> 1) & 1] * wx[e & 1];
+        }
+        wts[me] = fin ? pp.w : 0.f;
+#pragma unroll
+        for (int b = 4 * ngrp; b < NBP; ++b) vals[me * G::NBS + b] = 0.f;
+      }
+      __syncthreads();
+      for (int pb = warp * PPW; pb < cnt; pb += NW * PPW) {  // warp-uniform
+        const int p = pb + ps;
+        const bool act = lane_on && p < cnt;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
+          const int4 o = org[p];
+          const float* w = bw + p * PW;
+          const int xo = (o.x + ox) & mask;
+          int yr[D], zr[D];
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            yr[j] = ((o.y + j) & mask) * n;
+            zr[j] = ((o.z + j) & mask) * n2;
+          }
+          if (D == 4) {
+            const float wxo = w[16 + ox];
+#pragma unroll
+            for (int oz = 0; oz < 4; ++oz) {
+              const float4 wyz = *reinterpret_cast<const float4*>(w + oz * 4);
+              const float wr[4] = {wyz.x * wxo, wyz.y * wxo, wyz.z * wxo, wyz.w * wxo};
+#pragma unroll
+              for (int oy = 0; oy < 4; ++oy) {
+                const float4 v = __ldg(gq4 + (zr[oz] + yr[oy] + xo));
+                acc.x = fmaf(wr[oy], v.x, acc.x);
+                acc.y = fmaf(wr[oy], v.y, acc.y);
+                acc.z = fmaf(wr[oy], v.z, acc.z);
+                acc.w = fmaf(wr[oy], v.w, acc.w);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+              for (int oy = 0; oy < 2; ++oy) {
+                const float c = w[oz * 4 + oy * 2 + ox];
+                const float4 v = __ldg(gq4 + (zr[oz] + yr[oy] + xo));
+                acc.x = fmaf(c, v.x, acc.x);
+                acc.y = fmaf(c, v.y, acc.y);
+                acc.z = fmaf(c, v.z, acc.z);
+                acc.w = fmaf(c, v.w, acc.w);
+              }
+          }
+        }
+        // reduce-scatter over the D x lanes of (p, q): afterwards lane ox holds the total of
+        // component(s) ox (D = 4) or 2 ox, 2 ox + 1 (D = 2)
+        float* dst = vals + p * G::NBS + 4 * q;
+        if (D == 4) {
+          const bool hi = ox & 2;
+          const float sa = hi ? acc.x : acc.z, sb = hi ? acc.y : acc.w;
+          float ka = hi ? acc.z : acc.x, kb = hi ? acc.w : acc.y;
+          ka += __shfl_xor_sync(0xffffffffu, sa, 2);
+          kb += __shfl_xor_sync(0xffffffffu, sb, 2);
+          const bool odd = ox & 1;
+          const float s = odd ? ka : kb;
+          float kk = odd ? kb : ka;
+          kk += __shfl_xor_sync(0xffffffffu, s, 1);
+          if (act) dst[ox] = kk;
+        } else {
+          const bool odd = ox & 1;
+          const float sa = odd ? acc.x : acc.z, sb = odd ? acc.y : acc.w;
+          float ka = odd ? acc.z : acc.x, kb = odd ? acc.w : acc.y;
+          ka += __shfl_xor_sync(0xffffffffu, sa, 1);
+          kb += __shfl_xor_sync(0xffffffffu, sb, 1);
+          if (act) {
+            dst[2 * ox] = ka;
+            dst[2 * ox + 1] = kb;
+          }
+        }
+      }
+      __syncthreads();
+      if (grp < G::NGRP) g.add(vals, wts, cnt, b1, b2, grp);
+    }
+  }
+  __syncthreads();
+  cta_store<NBP, kThreadsL1>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -723,15 +923,34 @@ int points_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_sta
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
+// Which particle kernels run for the staging threshold: the staged one if some batch can
+// reach the threshold, the L1 one if some batch can fall below it.
+inline bool part_staged_on(const zeta_ctx* c) { return c->staged_min <= kPBP; }
+inline bool part_l1_on(const zeta_ctx* c) { return c->staged_min > 1; }
+
 template <int NBP, int D>
 int part_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, const float* alm, double* partials,
               cudaStream_t s) {
-  StageScope prof(c, ST_GRAM_PART, 1, s);
-  const size_t sm = smem_part<NBP, D>();
-  if (prep(k_gram_part<NBP, D>, sm)) return ZETA_ECUDA;
-  k_gram_part<NBP, D><<<gram_ctas(c, GK_PART), kThreads, sm, s>>>(
-      sorted, reinterpret_cast<const long long*>(tile_start), reinterpret_cast<const float4*>(alm), c->ng, c->n,
-      c->p.nbins, c->n / c->p.box, c->staged_min, partials);
+  StageScope prof(c, ST_GRAM_PART, part_staged_on(c) + part_l1_on(c), s);
+  const long long* ts = reinterpret_cast<const long long*>(tile_start);
+  const float4* f4 = reinterpret_cast<const float4*>(alm);
+  const double inv_h = c->n / c->p.box;
+  int off = 0;
+  if (part_staged_on(c)) {
+    const size_t sm = smem_part<NBP, D>();
+    if (prep(k_gram_part<NBP, D>, sm)) return ZETA_ECUDA;
+    const int g = gram_ctas(c, GK_PART);
+    k_gram_part<NBP, D><<<g, kThreads, sm, s>>>(sorted, ts, f4, c->ng, c->n, c->p.nbins, inv_h, c->staged_min,
+                                                partials);
+    off = g;
+  }
+  if (part_l1_on(c)) {
+    const size_t sm = PartL1Smem<NBP, D>::BYTES;
+    if (prep(k_gram_part_l1<NBP, D>, sm)) return ZETA_ECUDA;
+    k_gram_part_l1<NBP, D><<<c->num_sms, kThreadsL1, sm, s>>>(
+        sorted, ts, f4, c->ng, c->n, c->p.nbins, inv_h, c->staged_min,
+        partials + static_cast<long long>(off) * c->p.nbins * c->p.nbins);
+  }
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
@@ -748,6 +967,10 @@ int mass_impl(const zeta_ctx* c, const float2* dhat, int l, double* partials, cu
 inline int nbp_of(int nb) { return nb <= 8 ? 8 : nb <= 16 ? 16 : nb <= 24 ? 24 : 32; }
 
 }  // namespace
+
+int gram_particle_parts(const zeta_ctx* c) {
+  return (part_staged_on(c) ? gram_ctas(c, GK_PART) : 0) + (part_l1_on(c) ? c->num_sms : 0);
+}
 
 int gram_ctas(const zeta_ctx* c, int kind) {
   int per = c->tune[kind];

@@ -82,7 +82,7 @@ struct zeta_ctx {
   int tune[5] = {4, 2, 4, 4, 4};
   // particle Gram: batches with at least this many particles stage their tile's halo in
   // shared memory; sparser ones gather from global memory
-  int staged_min = 16;
+  int staged_min = 0;
   // CUDA graph of the last batch (zeta_batch)
   bool capturing = false;
   cudaStream_t cap_stream = nullptr;
@@ -158,6 +158,8 @@ int launch_gram_particles(const zeta_ctx* c, const float4* sorted, const int64_t
 int launch_gram_node_tc(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
 int launch_wait_selftest(const zeta_ctx* c, long long spins, cudaStream_t s);
 int launch_mass(const zeta_ctx* c, const float2* dhat, int l, double* partials, cudaStream_t s);
+// Number of per-CTA partial Grams launch_gram_particles writes.
+int gram_particle_parts(const zeta_ctx* c);
 // out[b1][b2] += scale * (1/ *wdiv if wdiv) * sum_cta partials[cta][b1][b2], symmetrised.
 int launch_reduce(const zeta_ctx* c, const double* partials, int nparts, double scale, const double* wdiv,
                   double* out, cudaStream_t s);

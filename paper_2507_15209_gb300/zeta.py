@@ -61,6 +61,7 @@ _SIGS = {
     "zeta_autotune": ([_VP, _VP, _I64, _INT, _VP], _INT),
     "zeta_get_tuning": ([_VP, _VP, _INT], _INT),
     "zeta_set_staging": ([_VP, _INT], _INT),
+    "zeta_set_tuning": ([_VP, _VP, _INT], _INT),
     "zeta_get_staging": ([_VP], _INT),
     "zeta_assign_noalloc": ([_INT, _DBL, _INT, _VP, _I64, _VP, _VP, _VP], _INT),
     "zeta_profile_enable": ([_VP, _INT], _INT),
@@ -345,6 +346,11 @@ class Context:
         t = np.zeros(5, np.int32)
         lib().zeta_get_tuning(self._h, t.ctypes.data, 5)
         return [int(x) for x in t]
+
+    def set_tuning(self, ctas_per_sm):
+        """zeta_set_tuning: persistent grid sizes [node, particle, Gamma, mass, node-tc]."""
+        t = np.ascontiguousarray(ctas_per_sm, dtype=np.int32)
+        _check("zeta_set_tuning", lib().zeta_set_tuning(self._h, t.ctypes.data, len(t)))
 
     def selftest_wait(self, spins: int = 1000):
         _check("zeta_selftest_wait", lib().zeta_selftest_wait(self._h, int(spins), _stream()))
