@@ -43,6 +43,21 @@ __device__ __forceinline__ void pair_blocks(int p, int nblk, int& b1, int& b2) {
   b2 = r + p;
 }
 
+// Asynchronous global -> shared copies (completion tracked per thread in commit groups).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
 template <int NBP, int NT = kThreads>
 struct GramAcc {
   float acc[4][4];
@@ -68,20 +83,43 @@ struct GramAcc {
       }
     pending = 0;
   }
-  // vals: [npts][NBS] shared, wts: [npts] shared
+  // vals: [npts][NBS] shared, wts: [npts] shared.  This thread takes points grp, grp + NGRP,
+  // ...; the float32 partials are flushed before a call that would take them past kFlush
+  // points (a call brings at most kPB / NGRP <= kFlush points), so the loop itself is
+  // flush-free and U points are in flight at a time.
+  template <int U = 2>
   __device__ __forceinline__ void add(const float* vals, const float* wts, int npts, int b1, int b2, int grp) {
-    for (int pt = grp; pt < npts; pt += Gram<NBP, NT>::NGRP) {
-      const float w = wts[pt];
-      const float4 x = *reinterpret_cast<const float4*>(vals + pt * Gram<NBP>::NBS + 4 * b1);
-      const float4 y = *reinterpret_cast<const float4*>(vals + pt * Gram<NBP>::NBS + 4 * b2);
-      const float xs[4] = {x.x * w, x.y * w, x.z * w, x.w * w};
-      const float ys[4] = {y.x, y.y, y.z, y.w};
+    constexpr int NG = Gram<NBP, NT>::NGRP;
+    constexpr int NBS = Gram<NBP, NT>::NBS;
+    const int count = grp < npts ? (npts - grp + NG - 1) / NG : 0;
+    if (pending + count > kFlush) flush();
+    pending += count;
+    int pt = grp;
+    for (; pt + (U - 1) * NG < npts; pt += U * NG) {
+      float w[U];
+      float4 x[U], y[U];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int u = 0; u < U; ++u) {
+        w[u] = wts[pt + u * NG];
+        x[u] = *reinterpret_cast<const float4*>(vals + (pt + u * NG) * NBS + 4 * b1);
+        y[u] = *reinterpret_cast<const float4*>(vals + (pt + u * NG) * NBS + 4 * b2);
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xs[i], ys[j], acc[i][j]);
-      if (++pending == kFlush) flush();
+      for (int u = 0; u < U; ++u) accum(x[u], y[u], w[u]);
     }
+    for (; pt < npts; pt += NG) {
+      const float4 x = *reinterpret_cast<const float4*>(vals + pt * NBS + 4 * b1);
+      const float4 y = *reinterpret_cast<const float4*>(vals + pt * NBS + 4 * b2);
+      accum(x, y, wts[pt]);
+    }
+  }
+  __device__ __forceinline__ void accum(float4 x, float4 y, float w) {
+    const float xs[4] = {x.x * w, x.y * w, x.z * w, x.w * w};
+    const float ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xs[i], ys[j], acc[i][j]);
   }
 };
 
@@ -357,15 +395,6 @@ struct Halo {
   static constexpr int SIZE = HD * PP;              // float4 per slot
 };
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
-}
 
 // Morton index -> one tile coordinate: keeps bits 0, 3, 6, ... of v, packed (nt a power of
 // two, at most 2^21)
@@ -964,7 +993,8 @@ int mass_impl(const zeta_ctx* c, const float2* dhat, int l, double* partials, cu
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
-inline int nbp_of(int nb) { return nb <= 8 ? 8 : nb <= 16 ? 16 : nb <= 24 ? 24 : 32; }
+// bins padded to whole groups of four: the Gram blocks cover no more than the next multiple of 4
+inline int nbp_of(int nb) { return 4 * ((nb + 3) / 4); }
 
 }  // namespace
 
@@ -981,9 +1011,13 @@ int gram_ctas(const zeta_ctx* c, int kind) {
 
 #define ZK_NBP_SWITCH(nb, CALL)       \
   switch (nbp_of(nb)) {               \
+    case 4: return CALL(4);           \
     case 8: return CALL(8);           \
+    case 12: return CALL(12);         \
     case 16: return CALL(16);         \
+    case 20: return CALL(20);         \
     case 24: return CALL(24);         \
+    case 28: return CALL(28);         \
     default: return CALL(32);         \
   }
 
