@@ -218,10 +218,10 @@ template <int N, int T>
 struct AlmZ {
   static constexpr int NT = RegThreads<N, T, 512>::NT;
   static constexpr int PPT = N * T / NT;
-  static constexpr int PADR = 2;  // exchange padding (conflict-free last stage for T = 8)
+  static constexpr int PADR = 2;  // exchange padding, 2 elements per 2 points (conflict-free for T = 8)
   static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;  // at least 16 warps per SM
   static constexpr size_t smem() {
-    return (StageTw<N>::SIZE + static_cast<size_t>(PPT) * NT + static_cast<size_t>(N) * T + N / PADR) *
+    return (StageTw<N>::SIZE + static_cast<size_t>(PPT) * NT + static_cast<size_t>(N) * T + N) *
                sizeof(float2) +
            static_cast<size_t>(PPT) * NT * sizeof(int);
   }
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(AlmZ<N, T>::NT, AlmZ<N, T>::MINB)
   float2* tw = sm;                      // per-stage twiddles
   float2* pd = tw + StageTw<N>::SIZE;   // [PPT][NT] delta_hat * angular factor
   float2* ex = pd + PPT * NT;           // [N][T] exchange (+ padding)
-  int* pn = reinterpret_cast<int*>(ex + N * T + N / PADR);  // [PPT][NT] window-table rows
+  int* pn = reinterpret_cast<int*>(ex + N * T + N);  // [PPT][NT] window-table rows
   const int x0 = blockIdx.x * T;
   const int iy = blockIdx.y;
   // offsets within one field (n^3 / 2 < 2^31)
@@ -352,8 +352,8 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
   constexpr int NT = RegThreads<N, T, 512>::NT;
   extern __shared__ float2 sm[];
   float2* tw = sm;                      // per-stage twiddles
-  float2* ex = tw + StageTw<N>::SIZE;   // [N][T]
-  float2* acc = ex + N * T;             // [N][T] sum over fields
+  float2* ex = tw + StageTw<N>::SIZE;   // [N][T] (+ N padding)
+  float2* acc = ex + N * T + N;         // [N][T] sum over fields
   float* ang = reinterpret_cast<float*>(acc + N * T);  // [N][T]
   int* n2 = reinterpret_cast<int*>(ang + N * T);        // [N][T]
   const int x0 = blockIdx.x * T;
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
       const float a = ang[idx] * __ldg(jt + static_cast<long long>(n2[idx]) * 4 * nbp4 + f);
       acc[idx] = cadd(acc[idx], cscale(v, a));
     };
-    fft_reg<N, T, NT, false, false>(ex, T, tw, load, store);
+    fft_reg<N, T, NT, false, false, 2>(ex, T, tw, load, store);
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
@@ -542,7 +542,7 @@ int adj_impl(const zeta_ctx* c, const float* fields, int nf, float2* spec, int l
   const size_t sma = axis_smem<N, TY>();
   if (set_smem(k_fft_axis<N, TY, false, 1>, sma)) return ZETA_ECUDA;
   k_fft_axis<N, TY, false, 1><<<dim3(NC / TY, N, nf), RegThreads<N, TY, 512>::NT, sma, s>>>(spec, fstride, c->d_tw);
-  const size_t smz = (StageTw<N>::SIZE + 2 * static_cast<size_t>(N) * TZ) * sizeof(float2) +
+  const size_t smz = (StageTw<N>::SIZE + 2 * static_cast<size_t>(N) * TZ + N) * sizeof(float2) +
                      2 * static_cast<size_t>(N) * TZ * 4;
   if (set_smem(k_adj_z<N, TZ>, smz)) return ZETA_ECUDA;
   const int nbp4 = (c->p.nbins + 3) / 4;

@@ -16,8 +16,8 @@
 // Twiddles come from a per-stage table in shared memory, [stage][j][3] = W_LS^j, W_LS^2j,
 // W_LS^4j (the odd powers formed by at most two multiplications), so that the lanes of a warp,
 // which hold consecutive j, read consecutive entries instead of strided ones.
-// The exchange buffer may be padded by one element every PADR points (PADR = 0: none), which
-// keeps the last stage of narrow (T = 8) pencils free of bank conflicts.
+// The exchange buffer may be padded by PADR elements every PADR points (PADR = 0: none),
+// which keeps the last stage of narrow (T = 8) pencils free of bank conflicts.
 #pragma once
 #include "fft.cuh"
 
@@ -102,10 +102,13 @@ __device__ __forceinline__ void twiddle(float2* y, int j, const float2* t) {
   }
 }
 
-// Exchange-buffer index of point pt of column col.
+// Exchange-buffer index of point pt of column col: PADR elements of padding after every
+// PADR points (PADR = 0: none).  For 8-byte elements the two half-warps are served
+// separately; with T = 8 columns the padded pitch puts the two points that a half-warp reads
+// in the last stage 16 banks apart.
 template <int PADR>
 __device__ __forceinline__ int ex_index(int pt, int col, int PS) {
-  return pt * PS + col + (PADR ? pt / PADR : 0);
+  return pt * PS + col + (PADR ? (pt / PADR) * PADR : 0);
 }
 
 template <int L, int T, int NT, bool INV, bool ROWS, int PADR, int S>
@@ -201,7 +204,7 @@ __device__ __forceinline__ void fft_reg_v(float2* v, float2* sm, int PS, const f
 
 // Full transform.  load(col, point) -> float2 gives the input; store(col, index, value)
 // receives each output at its natural index.  sm: [L][PS] float2 exchange buffer (PS >= T,
-// plus L / PADR elements of padding; odd PS in ROWS mode keeps the exchange conflict-free);
+// plus L elements of padding when PADR > 0; odd PS in ROWS mode keeps the exchange conflict-free);
 // tw: the per-stage table of StageTw<L> (forward sign) in shared memory.  No barrier after
 // the stores.
 template <int L, int T, int NT, bool INV, bool ROWS, int PADR = 0, bool SYNC_OUT = false, class Load, class Store>
