@@ -256,6 +256,37 @@ def _batch_sample(ncat, stream):
             "speedup": round(ms_seq / ms_batch, 4), "tuned_ctas_per_sm": tune}
 
 
+def _cufft_reference(w, nb, stages, stream):
+    """cuFFT (torch.fft, a library) on the inverse transforms of one (l, m) beside this
+    library's own passes, for reference only: batched irfftn of nb half spectra of the workload
+    grid.  Our side is the window pass + y-pass + x-pass time per (l, m) from the stage timers
+    (which also applies the window and writes bin-interleaved fields)."""
+    import torch
+    n = w["n"]
+    spec = torch.complex(torch.randn((nb, n, n, n // 2 + 1), device="cuda"),
+                         torch.randn((nb, n, n, n // 2 + 1), device="cuda"))
+    ms = _events_ms(lambda: torch.fft.irfftn(spec, s=(n, n, n), dim=(1, 2, 3)), 3, stream)
+    del spec
+    torch.cuda.empty_cache()
+    ours = sum(stages[k]["ms"] / stages[k]["launches"] for k in ("alm_z", "alm_y", "alm_x") if k in stages)
+    return {"fields": nb, "grid": n, "cufft_irfftn_ms": round(ms, 3), "ours_window_plus_c2r_ms": round(ours, 3)}
+
+
+def _catalogue_bytes(w, nb, forms):
+    """One-pass algorithmic HBM bytes of one catalogue (the survey's per-catalogue minimum):
+    assignment 16 N_p + 4 N_g, R2C 16 N_g, and per (l, m) the delta_hat read, each field written
+    once and read once after a single transpose round trip (16 N_g per field), the particles
+    (particle form) and the delta re-read plus a second field read (node form)."""
+    ng = w["n"] ** 3
+    n_p = w["n_p"]
+    per_lm = 4 * ng * (1 + 4 * nb)
+    if "particle" in forms:
+        per_lm += 16 * n_p
+    if "node" in forms:
+        per_lm += 4 * ng * (nb + 1)
+    return 16 * n_p + 4 * ng + 16 * ng + (w["lmax"] + 1) ** 2 * per_lm
+
+
 def _adjoint_ratio(stream):
     """Gradient cost on the adjoint workload (256^3 grid and 1M particles, lmax 6, 10 bins):
     backward / forward time of the node form (dL/d delta) and the particle form (dL/dx)."""
@@ -419,6 +450,11 @@ def run_ours(args, w, rank, world, local_rank):
                     "d2h_bytes_per_step": int(out.numel() * 8)},
             "gpu_launches": int(gpu_launches),
         }
+        cat_bytes = _catalogue_bytes(w, nb, forms)
+        line["catalogue_roofline"] = {"alg_bytes": cat_bytes, "achieved_gbs": cat_bytes / value / 1e9,
+                                      "peak_gbs": peak, "frac": cat_bytes / value / 1e9 / peak}
+        line["stage_gbs"] = {k: round(_alg_bytes(k, w, nb) * (v[1] if k == "r2c" else v[2]) / (v[0] / 1e3) / 1e9, 1)
+                             for k, v in prof.items() if v[1] > 0 and _alg_bytes(k, w, nb) is not None}
         extras = set() if args.no_extras else set(args.extras.split(","))
         if "variants" in extras:
             line["gram_variants"] = _gram_variants(ctx, dev, w, stream)
@@ -426,6 +462,8 @@ def run_ours(args, w, rank, world, local_rank):
             line["batch_sample"] = _batch_sample(8, stream)
         if "adjoint" in extras:
             line["adjoint"] = _adjoint_ratio(stream)
+        if "cufft" in extras:
+            line["cufft_reference"] = _cufft_reference(w, nb, stages, stream)
         if world == 1 and not args.no_cpu_baseline:
             total, sample = _oracle_sample(w, parts, _oracle_prepare(w, parts))
             line["cpu_baseline"] = {"value": total, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
@@ -446,7 +484,7 @@ def main():
     ap.add_argument("--forms", default="particle,node")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the Gram-variant, batch and adjoint extras")
-    ap.add_argument("--extras", default="variants,batch,adjoint", help="comma list of extras to measure")
+    ap.add_argument("--extras", default="variants,batch,adjoint,cufft", help="comma list of extras to measure")
     ap.add_argument("--lmax", type=int, default=None, help="override lmax (small profiling runs only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
