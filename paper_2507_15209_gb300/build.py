@@ -20,7 +20,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
-SOURCES = ["tables.cpp", "fft.cu", "assign.cu", "sums.cu", "gram_tc.cu", "adjoint.cu", "api.cu", "profile.cu"]
+SOURCES = ["tables.cpp", "fft.cu", "assign.cu", "sums.cu", "particles.cu", "gram_tc.cu", "adjoint.cu", "api.cu",
+           "profile.cu"]
 
 
 def _nvcc() -> str:

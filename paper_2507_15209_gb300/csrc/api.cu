@@ -15,7 +15,7 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t delta = 0, dhat = 0, spectra = 0, fields = 0, partials = 0, small = 0, sorted = 0, tstart = 0, counts = 0,
-         orig = 0;
+         orig = 0, pvals = 0;
   // backward (gradient) regions
   size_t gk = 0, q = 0, wts = 0, hfield = 0, direct = 0, sidx = 0;
   size_t total = 0;
@@ -42,6 +42,7 @@ Layout layout(const zeta_ctx* c, int64_t np, bool backward = false) {
   L.tstart = take(sizeof(int64_t) * static_cast<size_t>(c->ntiles + 1));
   L.counts = take(sizeof(int) * static_cast<size_t>(c->ntiles));
   L.orig = take(sizeof(int) * static_cast<size_t>(np));
+  L.pvals = take(particle_rows_bytes(c, np));  // interpolated particle rows of one (l, m)
   if (backward) {
     L.gk = take(g);
     L.q = take(g);
@@ -258,10 +259,11 @@ int zeta_sum_particles(zeta_ctx* c, const float* sorted, const int64_t* tile_sta
                        const float* alm, double* gram, zeta_stream stream) {
   ZK_TRY(check_ctx(c));
   if (!sorted || !tile_start || np < 1 || !wsum || !alm || !gram) return ZETA_EINVAL;
-  ZK_TRY(need_ws(c, 0));
-  const Layout L = layout(c, 0);
+  ZK_TRY(need_ws(c, np));
+  const Layout L = layout(c, np);
   double* part = at<double>(c, L.partials);
-  ZK_TRY(launch_gram_particles(c, reinterpret_cast<const float4*>(sorted), tile_start, alm, part, stream));
+  ZK_TRY(launch_gram_particles(c, reinterpret_cast<const float4*>(sorted), tile_start, np, alm, at<float>(c, L.pvals),
+                               part, stream));
   return launch_reduce(c, part, gram_particle_parts(c), 1.0, wsum, gram, stream);
 }
 
@@ -332,7 +334,7 @@ int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* 
                              zeta + idx_gamma * per_form + static_cast<size_t>(l) * nb * nb, stream));
       }
       if (idx_part >= 0) {
-        ZK_TRY(launch_gram_particles(c, sorted, tstart, fields, part, stream));
+        ZK_TRY(launch_gram_particles(c, sorted, tstart, np, fields, at<float>(c, L.pvals), part, stream));
         ZK_TRY(launch_reduce(c, part, gram_particle_parts(c), 1.0, wsum,
                              zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb, stream));
       }
@@ -416,7 +418,7 @@ int zeta_autotune(zeta_ctx* c, const float* particles, int64_t np, int forms, ze
       case GK_NODE: return launch_gram_node(c, dl, fields, part, stream);
       case GK_TC: return launch_gram_node_tc(c, dl, fields, part, stream);
       case GK_GAMMA: return launch_gram_gamma(c, dl, fields, part, stream);
-      case GK_PART: return launch_gram_particles(c, sorted, tstart, fields, part, stream);
+      case GK_PART: return launch_gram_particles(c, sorted, tstart, np, fields, at<float>(c, L.pvals), part, stream);
       default: return launch_mass(c, dhat, l, part, stream);
     }
   };

@@ -79,7 +79,7 @@ struct zeta_ctx {
   size_t ws_bytes = 0;
   mutable zk::Profiler prof;
   // persistent-grid size of each Gram kind, in CTAs per SM (set by zeta_autotune)
-  int tune[5] = {2, 2, 4, 4, 4};
+  int tune[5] = {2, 3, 4, 4, 4};
   // particle Gram: batches with at least this many particles stage their tile's halo in
   // shared memory; sparser ones gather from global memory
   int staged_min = 0;
@@ -152,8 +152,10 @@ int gram_ctas(const zeta_ctx* c, int kind);
 int launch_gram_node(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
 int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, double* partials,
                       cudaStream_t s);
-int launch_gram_particles(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, const float* alm,
-                          double* partials, cudaStream_t s);
+int launch_gram_particles(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, int64_t np,
+                          const float* alm, float* pvals, double* partials, cudaStream_t s);
+// Bytes of the interpolated particle rows [np][bins padded to 4] that launch_gram_particles uses.
+size_t particle_rows_bytes(const zeta_ctx* c, int64_t np);
 // tensor-core node Gram (gram_tc.cu), arithmetic chosen by c->p.gram
 int launch_gram_node_tc(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
 int launch_wait_selftest(const zeta_ctx* c, long long spins, cudaStream_t s);
