@@ -51,6 +51,33 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
 }
 
+constexpr long long kSpin = 1LL << 26;  // polls of a bounded mbarrier wait
+
+// ---- mbarriers --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// bounded wait for the completion of the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  for (long long it = 0; it < kSpin; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 template <int NBP, int NT = kThreads>
 struct GramAcc {
   float acc[4][4];
@@ -116,23 +143,31 @@ struct GramAcc {
   }
 };
 
-// Reduce the per-thread accumulators of a CTA (fixed order) and write its partial
-// [NB][NB] (upper triangle valid) to part.  red: shared double buffer NGRP*NPAIR*16.
-template <int NBP, int NT = kThreads>
-__device__ void cta_store(GramAcc<NBP, NT>& g, double* red, int nb, double* part) {
+// Reduce the per-thread accumulators of the NT threads that hold them (fixed order) and write
+// their partial [NB][NB] (upper triangle valid) to part.  red: shared double buffer
+// NGRP*NPAIR*16.  BAR = 0: the whole CTA takes part (tid = threadIdx.x); otherwise the NT
+// threads synchronise on named barrier BAR and pass their index among themselves.
+template <int NBP, int NT = kThreads, int BAR = 0>
+__device__ void cta_store(GramAcc<NBP, NT>& g, double* red, int nb, double* part, int tid = -1) {
   using G = Gram<NBP, NT>;
+  auto sync = [] {
+    if (BAR == 0)
+      __syncthreads();
+    else
+      asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+  };
   g.flush();
-  const int tid = threadIdx.x;
+  if (tid < 0) tid = threadIdx.x;
   const int pr = tid % G::NPAIR, grp = tid / G::NPAIR;
-  __syncthreads();
+  sync();
   if (grp < G::NGRP) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) red[(grp * G::NPAIR + pr) * 16 + i * 4 + j] = g.dacc[i][j];
   }
-  __syncthreads();
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
+  sync();
+  for (int e = tid; e < nb * nb; e += NT) {
     const int r = e / nb, cidx = e % nb;
     const int lo = r < cidx ? r : cidx, hi = r < cidx ? cidx : r;
     const int B1 = lo / 4, B2 = hi / 4;

@@ -14,7 +14,6 @@ namespace zk {
 namespace {
 
 constexpr int kPBP = 128;  // particles per tile batch
-constexpr long long kSpin = 1LL << 26;  // polls of a bounded mbarrier wait
 
 template <int D>
 struct Halo {
@@ -73,31 +72,6 @@ struct TileWalk {
   }
 };
 
-// ---- mbarriers --------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-// bounded wait for the completion of the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
-  const uint32_t a = smem_addr(bar);
-  for (long long it = 0; it < kSpin; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, P;\n\t}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
 // ---------------------------------------------------------------------------------------
 // Interpolation from the tile halo in shared memory.
 //

@@ -16,46 +16,88 @@ namespace zk {
 namespace {
 
 // ---------------------------------------------------------------------------------------
-// Node form: persistent CTAs over chunks of kPB grid points of the bin-interleaved fields;
-// the next chunk is loaded into registers while the current one is contracted.
+// Node form: persistent CTAs over chunks of kPB grid points of the bin-interleaved fields.
+// Warp 0 copies each chunk (delta and the float4 bin groups of every point) with cp.async into
+// the next slot of a kNKS-slot ring and arrives on the slot's `full` mbarrier when its copies
+// have landed; the other seven warps contract the chunk and arrive on the slot's `empty`
+// mbarrier, so the copies run up to kNKS chunks ahead and no CTA-wide barrier separates the
+// chunks.  Every wait is bounded and latches ZETA_ETIMEOUT in the status word.
+constexpr int kNodeCons = 224;  // consumer threads
+constexpr int kNKS = 2;         // chunk ring slots
+
+template <int NBP>
+struct NodeRing {
+  using G = Gram<NBP, kNodeCons>;
+  static constexpr int SLOTF = kPB * G::NBS + kPB;  // floats per slot: values, then weights
+  static constexpr size_t MAIN = static_cast<size_t>(kNKS) * SLOTF * sizeof(float) + 2 * kNKS * sizeof(unsigned long long);
+  static constexpr size_t RED = static_cast<size_t>(G::NGRP) * G::NPAIR * 16 * sizeof(double);
+  static constexpr size_t BYTES = MAIN > RED ? MAIN : RED;
+};
+
 template <int NBP>
 __global__ void __launch_bounds__(kThreads) k_gram_node(const float* __restrict__ delta, const float4* __restrict__ f4,
-                                                        long long ng, int nb, double* __restrict__ partials) {
-  using G = Gram<NBP>;
-  constexpr int GMAX = NBP / 4;
+                                                        long long ng, int nb, double* __restrict__ partials,
+                                                        int* __restrict__ status) {
+  using G = Gram<NBP, kNodeCons>;
+  using R = NodeRing<NBP>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float* vals = reinterpret_cast<float*>(smraw);
-  float* wts = vals + kPB * G::NBS;
+  float* ring = reinterpret_cast<float*>(smraw);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smraw + kNKS * R::SLOTF * sizeof(float));
+  unsigned long long* empty = full + kNKS;
   double* red = reinterpret_cast<double*>(smraw);  // reused after the main loop
-  const int pr = threadIdx.x % G::NPAIR, grp = threadIdx.x / G::NPAIR;
-  int b1 = 0, b2 = 0;
-  pair_blocks(pr, G::NBLK, b1, b2);
   const int ngrp = (nb + 3) / 4;
-  GramAcc<NBP> g;
-  g.init();
   const long long nchunk = ng / kPB;
-  float dnext = 0.f;
-  float4 vnext[GMAX];
-  long long ch = blockIdx.x;
-  auto fetch = [&](long long c) {
-    const long long p = c * kPB + threadIdx.x;
-    dnext = __ldg(delta + p);
-#pragma unroll
-    for (int q = 0; q < GMAX; ++q)
-      vnext[q] = (q < ngrp) ? __ldg(f4 + q * ng + p) : make_float4(0.f, 0.f, 0.f, 0.f);
-  };
-  if (ch < nchunk) fetch(ch);
-  for (; ch < nchunk; ch += gridDim.x) {
-    __syncthreads();
-    wts[threadIdx.x] = dnext;
-#pragma unroll
-    for (int q = 0; q < GMAX; ++q) *reinterpret_cast<float4*>(vals + threadIdx.x * G::NBS + 4 * q) = vnext[q];
-    __syncthreads();
-    if (ch + gridDim.x < nchunk) fetch(ch + gridDim.x);
-    if (grp < G::NGRP) g.add(vals, wts, kPB, b1, b2, grp);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kNKS; ++s) {
+      mbar_init(&full[s], 32);
+      mbar_init(&empty[s], kNodeCons / 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  cta_store<NBP>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb);
+  if (warp == 0) {  // ---- producer
+    long long i = 0;
+    bool ok = true;
+    for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x, ++i) {
+      const int s = static_cast<int>(i % kNKS);
+      const long long u = i / kNKS;
+      if (u > 0 && !mbar_wait(&empty[s], static_cast<uint32_t>((u - 1) & 1))) {
+        ok = false;
+        break;
+      }
+      float* v = ring + s * R::SLOTF;
+      const long long p0 = ch * kPB;
+      for (int j = lane; j < kPB; j += 32) {
+        cp_async4(v + kPB * G::NBS + j, delta + p0 + j);
+        for (int q = 0; q < ngrp; ++q) cp_async16(v + j * G::NBS + 4 * q, f4 + q * ng + p0 + j);
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(&full[s])) : "memory");
+    }
+    if (!ok && lane == 0) atomicOr(status, 2);
+    for (long long j = (i > kNKS ? i - kNKS : 0); j < i; ++j)
+      mbar_wait(&full[j % kNKS], static_cast<uint32_t>((j / kNKS) & 1));
+    return;
+  }
+  // ---- consumers
+  const int ct = threadIdx.x - 32;
+  const int pr = ct % G::NPAIR, grp = ct / G::NPAIR;
+  int b1 = 0, b2 = 0;
+  pair_blocks(pr, G::NBLK, b1, b2);
+  GramAcc<NBP, kNodeCons> g;
+  g.init();
+  long long i = 0;
+  bool ok = true;
+  for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x, ++i) {
+    const int s = static_cast<int>(i % kNKS);
+    if (ok && !mbar_wait(&full[s], static_cast<uint32_t>((i / kNKS) & 1))) ok = false;
+    const float* v = ring + s * R::SLOTF;
+    if (ok && grp < G::NGRP) g.add(v, v + kPB * G::NBS, kPB, b1, b2, grp);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  if (!ok && ct == 0) atomicOr(status, 2);
+  cta_store<NBP, kNodeCons, 1>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb, ct);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -241,9 +283,7 @@ __global__ void k_reduce(const double* __restrict__ part, int nparts, int nb, do
 
 template <int NBP>
 size_t smem_node() {
-  using G = Gram<NBP>;
-  const size_t main = (kPB * G::NBS + kPB) * sizeof(float);
-  return main > red_bytes<NBP>() ? main : red_bytes<NBP>();
+  return NodeRing<NBP>::BYTES;
 }
 template <int NBP>
 size_t smem_mass() {
@@ -263,7 +303,7 @@ int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* p
   const size_t sm = smem_node<NBP>();
   if (prep(k_gram_node<NBP>, sm)) return ZETA_ECUDA;
   k_gram_node<NBP><<<gram_ctas(c, GK_NODE), kThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
-                                                     c->p.nbins, partials);
+                                                                 c->p.nbins, partials, c->d_status);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 

@@ -79,7 +79,7 @@ struct zeta_ctx {
   size_t ws_bytes = 0;
   mutable zk::Profiler prof;
   // persistent-grid size of each Gram kind, in CTAs per SM (set by zeta_autotune)
-  int tune[5] = {2, 3, 4, 4, 4};
+  int tune[5] = {3, 3, 4, 4, 4};
   // particle Gram: batches with at least this many particles stage their tile's halo in
   // shared memory; sparser ones gather from global memory
   int staged_min = 0;
