@@ -104,6 +104,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_timings(ms_dev, ms_e2e, steps, world, dist=None, device="cuda"):
+    """Whole-job seconds per catalogue: the slowest rank's time (max over ranks) divided by all
+    ranks' catalogues (steps per rank x world).  Returns (value, e2e value, max device ms, max
+    end-to-end ms)."""
+    import torch
+    t = torch.tensor([ms_dev, ms_e2e], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    cats = steps * world
+    return float(t[0]) / 1e3 / cats, float(t[1]) / 1e3 / cats, float(t[0]), float(t[1])
+
+
 def _make_inputs(w, rank):
     rho = mocks.lognormal_density(w["n"], w["field_seed"] + 100 * rank)
     parts = mocks.sample_particles(rho, w["n_p"], w["box"], w["sample_seed"] + 100 * rank)
@@ -404,15 +416,9 @@ def run_ours(args, w, rank, world, local_rank):
     if ctx.get_status() != 0:
         raise RuntimeError("device status error in the timed region")
 
-    t = torch.tensor([ms_dev, ms_e2e], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_dev, ms_e2e = float(t[0]), float(t[1])
+    value, e2e_value, ms_dev, ms_e2e = reduce_timings(ms_dev, ms_e2e, args.steps, world, dist)
 
     if rank == 0:
-        cats = args.steps * world
-        value = ms_dev / 1e3 / cats
-        e2e_value = ms_e2e / 1e3 / cats
         peak, peak_src = _peaks()
         # dominant memory-bound kernel
         rows = {k: v for k, v in prof.items() if v[1] > 0 and _alg_bytes(k, w, nb) is not None}
