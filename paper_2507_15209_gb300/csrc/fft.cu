@@ -185,17 +185,54 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
   stage_tw_fill<NC>(tw2, twg, 2);
   __syncthreads();
-  auto load = [&](int c, int k) -> float2 {
-    const int f = 4 * g + c / RB;
-    if (f >= nf) return make_float2(0.f, 0.f);
-    const float2* row = spec + f * fstride + (r0 + c % RB) * NC;
-    const float2 xk = row[k];
-    const float2 xp = (k == 0) ? make_float2(0.f, 0.f) : row[NC - k];
+  auto store = [&](int c, int j, float2 v) { res[j * PS + c] = v; };
+  // z_k = (X_k + conj X_{NC-k}) + i conj(W_N^k) (X_k - conj X_{NC-k}), X_{NC} = 0
+  auto pack = [&](int k, float2 xk, float2 xp) -> float2 {
     const float2 wk = cconj(tw[k]);
     return cadd(cadd(xk, cconj(xp)), mul_i(cmul(wk, csub(xk, cconj(xp)))));
   };
-  auto store = [&](int c, int j, float2 v) { res[j * PS + c] = v; };
-  fft_reg<NC, C, NT, true, true, 0, true>(ex, PS, tw2, load, store);
+  constexpr int R0 = plan_radix<NC>(0);
+  constexpr int PPT = NC * C / NT;
+  constexpr int NTASK0 = PPT / R0;
+  constexpr int H = NC / R0 / 2;
+  constexpr bool MIRROR = (NTASK0 % 2 == 0) && H >= 1 && (NT % H == 0) && (NTASK0 / 2) * (NT / H) == C;
+  if constexpr (MIRROR) {
+    // each thread holds both points of every (k, NC - k) pair: one load per point
+    float2 xv[PPT];
+    int pts[PPT];
+#pragma unroll
+    for (int sl = 0; sl < PPT; ++sl) {
+      int c, p;
+      reg_slot<NC, C, NT, 2>(sl, c, p);
+      pts[sl] = p;
+      const int f = 4 * g + c / RB;
+      xv[sl] = (f < nf) ? spec[f * fstride + (r0 + c % RB) * NC + p] : make_float2(0.f, 0.f);
+    }
+    const bool u0 = (threadIdx.x % H) == 0;
+    float2 v[PPT];
+#pragma unroll
+    for (int i = 0; i < NTASK0; ++i)
+#pragma unroll
+      for (int q = 0; q < R0; ++q) {
+        const int sl = i * R0 + q;
+        const float2 other = xv[((i & 1) == 0 ? i + 1 : i - 1) * R0 + (R0 - 1 - q)];
+        float2 self_pair;  // k = 0 (even task) or k = NC / R0 / 2 (odd task) pairs within the task
+        if ((i & 1) == 0)
+          self_pair = (q == 0) ? make_float2(0.f, 0.f) : xv[i * R0 + (R0 - q)];
+        else
+          self_pair = xv[i * R0 + (R0 - 1 - q)];
+        v[sl] = pack(pts[sl], xv[sl], u0 ? self_pair : other);
+      }
+    fft_reg_v<NC, C, NT, true, 2, 0, true>(v, ex, PS, tw2, store);
+  } else {
+    auto load = [&](int c, int k) -> float2 {
+      const int f = 4 * g + c / RB;
+      if (f >= nf) return make_float2(0.f, 0.f);
+      const float2* row = spec + f * fstride + (r0 + c % RB) * NC;
+      return pack(k, row[k], (k == 0) ? make_float2(0.f, 0.f) : row[NC - k]);
+    };
+    fft_reg<NC, C, NT, true, true, 0, true>(ex, PS, tw2, load, store);
+  }
   __syncthreads();
   for (int idx = threadIdx.x; idx < NC * RB; idx += blockDim.x) {
     const int r = idx / NC, j = idx % NC;

@@ -34,12 +34,23 @@ __host__ __device__ constexpr int plan_span(int S) {
   return ls;
 }
 
-// ROWS applies to stage 0 only (coalesced loads along rows); later stages are always
-// column-fastest, which keeps every shared-memory exchange free of bank conflicts.
-template <int L, int T, int NT, bool ROWS, int R>
+// Stage-0 task mappings (MAP, later stages always column-fastest, which keeps every
+// shared-memory exchange free of bank conflicts):
+//   0  column-fastest (pencils: columns contiguous in global memory);
+//   1  rows: point-fastest, so that rows load coalesced;
+//   2  mirror-paired rows: thread u of a column takes tasks k = u and k = KC - u (u = 0: k = 0 and
+//      k = KC/2), KC = L / R, with its tasks alternating between the two; then the points
+//      p and L - p of a half-length real-to-complex packing sit in the same thread (task pairs
+//      (2j, 2j + 1), point q against R - 1 - q).  Needs an even number of tasks per thread.
+template <int L, int T, int NT, int MAP, int R>
 __device__ __forceinline__ void reg_task(int i, int& col, int& k) {
   const int t = threadIdx.x + i * NT;
-  if (ROWS) {
+  if constexpr (MAP == 2) {
+    constexpr int KC = L / R, H = KC / 2;
+    const int u = threadIdx.x % H, cidx = threadIdx.x / H;
+    col = cidx + (i >> 1) * (NT / H);
+    k = (i & 1) == 0 ? u : (u == 0 ? H : KC - u);
+  } else if constexpr (MAP == 1) {
     k = t % (L / R);
     col = t / (L / R);
   } else {
@@ -111,7 +122,7 @@ __device__ __forceinline__ int ex_index(int pt, int col, int PS) {
   return pt * PS + col + (PADR ? (pt / PADR) * PADR : 0);
 }
 
-template <int L, int T, int NT, bool INV, bool ROWS, int PADR, int S>
+template <int L, int T, int NT, bool INV, int ROWS, int PADR, int S>
 struct RegStage {
   static constexpr int R = plan_radix<L>(S);
   static constexpr int LS = plan_span<L>(S);
@@ -121,7 +132,7 @@ struct RegStage {
 
   __device__ __forceinline__ static int base_of(int k) { return (k / M) * LS + (k % M); }
 
-  static constexpr bool RM = ROWS && S == 0;  // row-fastest mapping for this stage?
+  static constexpr int RM = S == 0 ? ROWS : 0;  // task mapping of this stage
   // butterflies + twiddles of this stage on v (inputs in task order)
   __device__ __forceinline__ static void compute(float2* v, const float2* tw) {
 #pragma unroll
@@ -158,7 +169,7 @@ struct RegStage {
 
 // SYNC_OUT: barrier before the last stage hands out its outputs (lets the caller's store
 // reuse the exchange buffer).
-template <int L, int T, int NT, bool INV, bool ROWS, int PADR, bool SYNC_OUT, int S>
+template <int L, int T, int NT, bool INV, int ROWS, int PADR, bool SYNC_OUT, int S>
 struct RegRun {
   template <class Store>
   __device__ __forceinline__ static void run(float2* v, float2* sm, int PS, const float2* tw, Store& store) {
@@ -188,7 +199,7 @@ struct RegRun {
 
 // Stage-0 input slot of a thread: slot i*R0 + q holds point k + q*M0 of column col, where
 // (col, k) is the thread's task i.  Callers that precompute per-point data use this order.
-template <int L, int T, int NT, bool ROWS>
+template <int L, int T, int NT, int ROWS>
 __device__ __forceinline__ void reg_slot(int slot, int& col, int& point) {
   using S0 = RegStage<L, T, NT, false, ROWS, 0, 0>;
   int k;
@@ -197,7 +208,7 @@ __device__ __forceinline__ void reg_slot(int slot, int& col, int& point) {
 }
 
 // Full transform of inputs already in registers (slot order of reg_slot).
-template <int L, int T, int NT, bool INV, bool ROWS, int PADR = 0, bool SYNC_OUT = false, class Store>
+template <int L, int T, int NT, bool INV, int ROWS, int PADR = 0, bool SYNC_OUT = false, class Store>
 __device__ __forceinline__ void fft_reg_v(float2* v, float2* sm, int PS, const float2* tw, Store& store) {
   RegRun<L, T, NT, INV, ROWS, PADR, SYNC_OUT, 0>::run(v, sm, PS, tw, store);
 }
@@ -207,7 +218,7 @@ __device__ __forceinline__ void fft_reg_v(float2* v, float2* sm, int PS, const f
 // plus L elements of padding when PADR > 0; odd PS in ROWS mode keeps the exchange conflict-free);
 // tw: the per-stage table of StageTw<L> (forward sign) in shared memory.  No barrier after
 // the stores.
-template <int L, int T, int NT, bool INV, bool ROWS, int PADR = 0, bool SYNC_OUT = false, class Load, class Store>
+template <int L, int T, int NT, bool INV, int ROWS, int PADR = 0, bool SYNC_OUT = false, class Load, class Store>
 __device__ __forceinline__ void fft_reg(float2* sm, int PS, const float2* tw, Load& load, Store& store) {
   constexpr int PPT = L * T / NT;
   float2 v[PPT];
