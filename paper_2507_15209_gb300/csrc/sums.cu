@@ -268,17 +268,24 @@ __global__ void __launch_bounds__(kThreads) k_gram_mass(const float2* __restrict
   cta_store<NBP>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb);
 }
 
+// One warp per output entry: lane j sums the partials j, j + 32, ... in order, then a fixed
+// butterfly combines the lanes, so the result does not depend on scheduling.
 __global__ void k_reduce(const double* __restrict__ part, int nparts, int nb, double scale,
                          const double* __restrict__ wdiv, double* __restrict__ out) {
-  const int e = threadIdx.x;
-  if (e >= nb * nb) return;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= nb * nb) return;  // whole warps leave together
   const int r = e / nb, c = e % nb;
   const int lo = r < c ? r : c, hi = r < c ? c : r;
   double sum = 0.0;
-  for (int k = 0; k < nparts; ++k) sum += part[static_cast<long long>(k) * nb * nb + lo * nb + hi];
-  double sc = scale;
-  if (wdiv) sc /= *wdiv;
-  out[e] += sc * sum;
+  for (int k = lane; k < nparts; k += 32) sum += part[static_cast<long long>(k) * nb * nb + lo * nb + hi];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if (lane == 0) {
+    double sc = scale;
+    if (wdiv) sc /= *wdiv;
+    out[e] += sc * sum;
+  }
 }
 
 template <int NBP>
@@ -365,7 +372,7 @@ int launch_reduce(const zeta_ctx* c, const double* partials, int nparts, double 
                   double* out, cudaStream_t s) {
   StageScope prof(c, ST_REDUCE, 1, s);
   const int nb = c->p.nbins;
-  k_reduce<<<1, 1024, 0, s>>>(partials, nparts, nb, scale, wdiv, out);
+  k_reduce<<<(nb * nb + 7) / 8, 256, 0, s>>>(partials, nparts, nb, scale, wdiv, out);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
