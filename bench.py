@@ -38,9 +38,11 @@ METRIC = "zeta_l(r1,r2) s/catalog at Ng=512^3"
 UNIT = "s/catalog"
 FALLBACK_HBM_GBS = 6800.0
 
-# dram bytes per launch from one ncu capture of the kernel, and the sha of the source file
-# it was built from (the entry is ignored once that source changes)
-NCU_TRAFFIC = {}
+# dram bytes (read + write) per call of a stage from one ncu capture of its kernels on the
+# 512^3 / 16M-particle / 20-bin workload, and the sha of the source file they were built from
+# (the entry is ignored once that source changes).  gram_particles = k_interp_part
+# (18.081 + 1.279 GB) + k_gram_rows (1.536 + 0.0002 GB).
+NCU_TRAFFIC = {"gram_particles": {"bytes": 20896354816, "sha": "ef13c78e0f09dd54"}}
 
 
 def _sha(path):
@@ -429,7 +431,7 @@ def run_ours(args, w, rank, world, local_rank):
         bytes_launch = _alg_bytes(dom, w, nb)
         achieved = bytes_launch * calls_k / (ms_k / 1e3) / 1e9
         src = {"alm_z": "fft.cu", "alm_y": "fft.cu", "alm_x": "fft.cu", "r2c": "fft.cu",
-               "gram_particles": "sums.cu", "gram_node": "sums.cu", "mass": "sums.cu"}[dom]
+               "gram_particles": "particles.cu", "gram_node": "sums.cu", "mass": "sums.cu"}[dom]
         tr = NCU_TRAFFIC.get(dom)
         traffic = None
         if tr and tr["sha"] == _sha(os.path.join(ROOT, "paper_2507_15209_gb300", "csrc", src)):
