@@ -160,7 +160,9 @@ int zeta_sort_particles(zeta_ctx* ctx, const float* particles, int64_t np, float
 
 /* Step (6), particle form without the uniform term, one (l, m):
  * gram[b1][b2] += (1/W) sum_p w_p f_b1(x_p) f_b2(x_p), f_b(x) = sum_l beta(x/H - l) a_b(l).
- * sorted/tile_start: from zeta_sort_particles; wsum: device double[1] (W); alm as above. */
+ * sorted/tile_start: from zeta_sort_particles; wsum: device double[1] (W); alm as above.
+ * Uses the workspace, which must be sized for np particles (zeta_workspace_bytes with
+ * np_max >= np and ZETA_SUM_PARTICLE): the interpolated values f_b(x_p) are staged there. */
 int zeta_sum_particles(zeta_ctx* ctx, const float* sorted, const int64_t* tile_start, int64_t np,
                        const double* wsum, const float* alm, double* gram, zeta_stream stream);
 
