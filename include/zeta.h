@@ -169,7 +169,9 @@ int zeta_sum_particles(zeta_ctx* ctx, const float* sorted, const int64_t* tile_s
 /* Step (6), the uniform term of the particle form summed over m for one l:
  * gram[b1][b2] += sign * U_l, U_l = sum_m (1/V) int f_b1 f_b2 dx
  *   = (2l+1)/N_g^2 sum_{k non-Nyquist} |delta_hat|^2 jbar_l(k;b1) jbar_l(k;b2) Mhat(k),
- * Mhat the DFT of the B-spline mass matrix.  sign is +1 or -1. */
+ * Mhat the DFT of the B-spline mass matrix.  sign is +1 or -1.  The mode weights are summed per
+ * integer |n|^2 first (64-bit fixed point in units of their maximum x 2^-48, so the result does
+ * not depend on the order of the modes); uses the workspace. */
 int zeta_mass_term(zeta_ctx* ctx, const float* delta_hat, int l, double sign, double* gram,
                    zeta_stream stream);
 

@@ -14,8 +14,8 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t delta = 0, dhat = 0, spectra = 0, fields = 0, partials = 0, small = 0, sorted = 0, tstart = 0, counts = 0,
-         orig = 0, pvals = 0;
+  size_t delta = 0, dhat = 0, spectra = 0, fields = 0, partials = 0, small = 0, mhist = 0, sorted = 0, tstart = 0,
+         counts = 0, orig = 0, pvals = 0;
   // backward (gradient) regions
   size_t gk = 0, q = 0, wts = 0, hfield = 0, direct = 0, sidx = 0;
   size_t total = 0;
@@ -38,6 +38,7 @@ Layout layout(const zeta_ctx* c, int64_t np, bool backward = false) {
   L.fields = take(g * 4 * ((c->p.nbins + 3) / 4));     // bin-interleaved fields; also the assign accumulator
   L.partials = take(sizeof(double) * kMaxCtas * c->p.nbins * c->p.nbins);
   L.small = take(sizeof(double) * (kAssignScratchDoubles + 8));
+  L.mhist = take(sizeof(unsigned long long) * static_cast<size_t>(c->nn2 + 1));  // uniform-term sums per |n|^2
   L.sorted = take(sizeof(float4) * static_cast<size_t>(np));
   L.tstart = take(sizeof(int64_t) * static_cast<size_t>(c->ntiles + 1));
   L.counts = take(sizeof(int) * static_cast<size_t>(c->ntiles));
@@ -273,7 +274,9 @@ int zeta_mass_term(zeta_ctx* c, const float* delta_hat, int l, double sign, doub
   ZK_TRY(need_ws(c, 0));
   const Layout L = layout(c, 0);
   double* part = at<double>(c, L.partials);
-  ZK_TRY(launch_mass(c, reinterpret_cast<const float2*>(delta_hat), l, part, stream));
+  unsigned long long* hist = at<unsigned long long>(c, L.mhist);
+  ZK_TRY(launch_mass_hist(c, reinterpret_cast<const float2*>(delta_hat), hist, stream));
+  ZK_TRY(launch_mass(c, hist, l, part, stream));
   const double scale = sign * (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846);
   return launch_reduce(c, part, gram_ctas(c, GK_MASS), scale, nullptr, gram, stream);
 }
@@ -303,8 +306,11 @@ int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* 
   else if (want_p)
     ZK_TRY(launch_wsum(c, parts, np, wsum, small, stream));
   ZK_TRY(launch_r2c(c, dl, dhat, stream));
-  if (want_p)
+  unsigned long long* hist = at<unsigned long long>(c, L.mhist);
+  if (want_p) {
     ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream));
+    ZK_TRY(launch_mass_hist(c, dhat, hist, stream));
+  }
 
   int nforms = 0, idx_node = -1, idx_gamma = -1, idx_part = -1;
   if (forms & ZETA_SUM_NODE) idx_node = nforms++;
@@ -316,7 +322,7 @@ int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* 
   for (int l = 0; l <= lmax; ++l) {
     if (want_p) {
       double* out = zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb;
-      ZK_TRY(launch_mass(c, dhat, l, part, stream));
+      ZK_TRY(launch_mass(c, hist, l, part, stream));
       ZK_TRY(launch_reduce(c, part, gram_ctas(c, GK_MASS), -(2.0 * l + 1.0) / (4.0 * 3.14159265358979323846), nullptr,
                            out, stream));
     }
@@ -408,7 +414,11 @@ int zeta_autotune(zeta_ctx* c, const float* particles, int64_t np, int forms, ze
   // representative data: this catalogue's fields for one (l, m)
   ZK_TRY(launch_assign(c, parts, np, dl, wsum, reinterpret_cast<unsigned long long*>(fields), small, stream));
   ZK_TRY(launch_r2c(c, dl, dhat, stream));
-  if (want_p) ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream));
+  unsigned long long* hist = at<unsigned long long>(c, L.mhist);
+  if (want_p) {
+    ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream));
+    ZK_TRY(launch_mass_hist(c, dhat, hist, stream));
+  }
   const int l = c->p.lmax < 2 ? c->p.lmax : 2;
   ZK_TRY(launch_alm(c, dhat, l, 0, 0, c->p.nbins, at<float2>(c, L.spectra), fields, stream));
   cudaEvent_t e0, e1;
@@ -419,7 +429,7 @@ int zeta_autotune(zeta_ctx* c, const float* particles, int64_t np, int forms, ze
       case GK_TC: return launch_gram_node_tc(c, dl, fields, part, stream);
       case GK_GAMMA: return launch_gram_gamma(c, dl, fields, part, stream);
       case GK_PART: return launch_gram_particles(c, sorted, tstart, np, fields, at<float>(c, L.pvals), part, stream);
-      default: return launch_mass(c, dhat, l, part, stream);
+      default: return launch_mass(c, hist, l, part, stream);
     }
   };
   std::vector<int> kinds;

@@ -229,42 +229,100 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------------------
-// Mass (uniform) term: points = stored half-spectrum modes.
+// Uniform term of the particle form: U_l[b1][b2] = (2l+1)/(4 pi) sum_k w(k) J_l,b1(|n|^2)
+// J_l,b2(|n|^2), w = (1, or 2 off the ix = 0 plane) |delta_hat|^2 Mhat over the stored half
+// spectrum without its Nyquist planes.  The window depends on the mode only through the
+// integer |n|^2, so w is summed per |n|^2 once per catalogue and each l is then a Gram over
+// the 3 (n/2)^2 + 1 values of |n|^2.  The per-|n|^2 sums are 64-bit fixed point in units of
+// max(w) 2^-48: integer atomics, so the sums do not depend on the order of the modes, and a
+// value of |n|^2 holds far fewer than 2^16 modes, so no sum can overflow.
+constexpr double kMassUnit = 281474976710656.0;  // 2^48
+
+__device__ __forceinline__ bool mass_mode(long long i, int n, const float2* __restrict__ dhat,
+                                          const float* __restrict__ mhat, double& w, long long& n2) {
+  const int nc = n / 2;
+  const int ix = static_cast<int>(i % nc), iy = static_cast<int>((i / nc) % n),
+            iz = static_cast<int>(i / (static_cast<long long>(nc) * n));
+  if (iy == n / 2 || iz == n / 2) return false;
+  const int fy = iy < n / 2 ? iy : iy - n, fz = iz < n / 2 ? iz : iz - n;
+  n2 = static_cast<long long>(ix) * ix + fy * fy + fz * fz;
+  const float2 d = dhat[i];
+  w = (ix == 0 ? 1.0 : 2.0) * (static_cast<double>(d.x) * d.x + static_cast<double>(d.y) * d.y) *
+      (static_cast<double>(mhat[ix]) * mhat[iy] * mhat[iz]);
+  return true;
+}
+
+// max_k w(k) as the bits of a non-negative double (their unsigned order is the numeric order)
+__global__ void k_mass_max(const float2* __restrict__ dhat, const float* __restrict__ mhat, int n,
+                           unsigned long long* __restrict__ wmax_bits) {
+  const long long total = static_cast<long long>(n) * n * (n / 2);
+  unsigned long long m = 0;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(blockDim.x) * gridDim.x) {
+    double w;
+    long long n2;
+    if (mass_mode(i, n, dhat, mhat, w, n2)) {
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(w));
+      m = b > m ? b : m;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+    m = o > m ? o : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(wmax_bits, m);
+}
+
+__global__ void k_mass_hist(const float2* __restrict__ dhat, const float* __restrict__ mhat, int n,
+                            const unsigned long long* __restrict__ wmax_bits, unsigned long long* __restrict__ hist) {
+  const double wmax = __longlong_as_double(static_cast<long long>(*wmax_bits));
+  if (!(wmax > 0.0)) return;
+  const double scale = kMassUnit / wmax;
+  const long long total = static_cast<long long>(n) * n * (n / 2);
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(blockDim.x) * gridDim.x) {
+    double w;
+    long long n2;
+    if (mass_mode(i, n, dhat, mhat, w, n2)) {
+      const unsigned long long q = __double2ull_rn(w * scale);
+      if (q) atomicAdd(hist + n2, q);
+    }
+  }
+}
+
+// Gram of one l over the values of |n|^2: weight S(|n|^2), values J_l,b(|n|^2)
 template <int NBP>
-__global__ void __launch_bounds__(kThreads) k_gram_mass(const float2* __restrict__ dhat, const float* __restrict__ jt,
-                                                        long long nn2, const float* __restrict__ mhat, int n, int nb,
+__global__ void __launch_bounds__(kThreads) k_gram_mass(const unsigned long long* __restrict__ hist,
+                                                        const unsigned long long* __restrict__ wmax_bits,
+                                                        const float* __restrict__ jt, long long nn2, int nb,
                                                         double* __restrict__ partials) {
   using G = Gram<NBP>;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* vals = reinterpret_cast<float*>(smraw);
   float* wts = vals + kPB * G::NBS;
-  double* red = reinterpret_cast<double*>(wts + kPB);
+  double* red = reinterpret_cast<double*>(smraw);  // reused after the main loop
   const int pr = threadIdx.x % G::NPAIR, grp = threadIdx.x / G::NPAIR;
   int b1 = 0, b2 = 0;
   pair_blocks(pr, G::NBLK, b1, b2);
   GramAcc<NBP> g;
   g.init();
-  const int nc = n / 2;
-  const long long total = static_cast<long long>(n) * n * nc;
-  const long long nchunk = total / kPB;
+  const double unit = __longlong_as_double(static_cast<long long>(*wmax_bits)) / kMassUnit;
+  const int nbp = 4 * ((nb + 3) / 4);
+  const long long nchunk = (nn2 + kPB - 1) / kPB;
   for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-    const long long i = ch * kPB + threadIdx.x;
-    const int ix = static_cast<int>(i % nc), iy = static_cast<int>((i / nc) % n), iz = static_cast<int>(i / (static_cast<long long>(nc) * n));
-    const bool nyq = (iy == n / 2) || (iz == n / 2);
-    const int fy = iy < n / 2 ? iy : iy - n, fz = iz < n / 2 ? iz : iz - n;
-    const long long n2 = static_cast<long long>(ix) * ix + fy * fy + fz * fz;
+    const long long p = ch * kPB + threadIdx.x;
+    const long long left = nn2 - ch * kPB;
+    const int cnt = left < kPB ? static_cast<int>(left) : kPB;
     __syncthreads();
-    float w = 0.f;
-    if (!nyq) {
-      const float2 d = dhat[i];
-      w = (ix == 0 ? 1.f : 2.f) * (d.x * d.x + d.y * d.y) * mhat[ix] * mhat[iy] * mhat[iz];
+    if (threadIdx.x < cnt) {
+      wts[threadIdx.x] = static_cast<float>(static_cast<double>(hist[p]) * unit);
+      for (int b = 0; b < NBP; ++b) vals[threadIdx.x * G::NBS + b] = (b < nb) ? __ldg(jt + p * nbp + b) : 0.f;
     }
-    wts[threadIdx.x] = w;
-    const int nbp = 4 * ((nb + 3) / 4);
-    for (int b = 0; b < NBP; ++b) vals[threadIdx.x * G::NBS + b] = (b < nb && !nyq) ? __ldg(jt + n2 * nbp + b) : 0.f;
     __syncthreads();
-    if (grp < G::NGRP) g.add(vals, wts, kPB, b1, b2, grp);
+    if (grp < G::NGRP) g.add(vals, wts, cnt, b1, b2, grp);
   }
+  __syncthreads();
   cta_store<NBP>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb);
 }
 
@@ -295,7 +353,8 @@ size_t smem_node() {
 template <int NBP>
 size_t smem_mass() {
   using G = Gram<NBP>;
-  return (kPB * G::NBS + kPB) * sizeof(float) + red_bytes<NBP>();
+  const size_t main = (kPB * G::NBS + kPB) * sizeof(float);
+  return main > red_bytes<NBP>() ? main : red_bytes<NBP>();
 }
 template <int NBP, int D>
 size_t smem_gamma() {
@@ -326,12 +385,12 @@ int gamma_impl(const zeta_ctx* c, const float* delta, const float* alm, double* 
 }
 
 template <int NBP>
-int mass_impl(const zeta_ctx* c, const float2* dhat, int l, double* partials, cudaStream_t s) {
+int mass_impl(const zeta_ctx* c, const unsigned long long* hist, int l, double* partials, cudaStream_t s) {
   StageScope prof(c, ST_MASS, 1, s);
   const size_t sm = smem_mass<NBP>();
   if (prep(k_gram_mass<NBP>, sm)) return ZETA_ECUDA;
   const float* jt = c->d_jtab + static_cast<long long>(l) * c->nn2 * (4 * ((c->p.nbins + 3) / 4));
-  k_gram_mass<NBP><<<gram_ctas(c, GK_MASS), kThreads, sm, s>>>(dhat, jt, c->nn2, c->d_mhat, c->n, c->p.nbins, partials);
+  k_gram_mass<NBP><<<gram_ctas(c, GK_MASS), kThreads, sm, s>>>(hist, hist + c->nn2, jt, c->nn2, c->p.nbins, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
@@ -362,8 +421,18 @@ int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, d
   }
 }
 
-int launch_mass(const zeta_ctx* c, const float2* dhat, int l, double* partials, cudaStream_t s) {
-#define ZK_CALL(P) mass_impl<P>(c, dhat, l, partials, s)
+int launch_mass_hist(const zeta_ctx* c, const float2* dhat, unsigned long long* hist, cudaStream_t s) {
+  StageScope prof(c, ST_MASS, 2, s);
+  // hist[0 .. nn2) the fixed-point sums, hist[nn2] the bits of max w
+  if (cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (c->nn2 + 1), s) != cudaSuccess) return ZETA_ECUDA;
+  const int grid = c->num_sms * 8;
+  k_mass_max<<<grid, kThreads, 0, s>>>(dhat, c->d_mhat, c->n, hist + c->nn2);
+  k_mass_hist<<<grid, kThreads, 0, s>>>(dhat, c->d_mhat, c->n, hist + c->nn2, hist);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
+int launch_mass(const zeta_ctx* c, const unsigned long long* hist, int l, double* partials, cudaStream_t s) {
+#define ZK_CALL(P) mass_impl<P>(c, hist, l, partials, s)
   ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
 #undef ZK_CALL
 }

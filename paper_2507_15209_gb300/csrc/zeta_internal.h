@@ -159,7 +159,11 @@ size_t particle_rows_bytes(const zeta_ctx* c, int64_t np);
 // tensor-core node Gram (gram_tc.cu), arithmetic chosen by c->p.gram
 int launch_gram_node_tc(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
 int launch_wait_selftest(const zeta_ctx* c, long long spins, cudaStream_t s);
-int launch_mass(const zeta_ctx* c, const float2* dhat, int l, double* partials, cudaStream_t s);
+// Uniform term of the particle form: launch_mass_hist sums the mode weights of dhat per integer
+// |n|^2 into hist (nn2 + 1 words: the sums, then the scale), once per catalogue; launch_mass
+// writes the per-CTA partial Grams of one l from it.
+int launch_mass_hist(const zeta_ctx* c, const float2* dhat, unsigned long long* hist, cudaStream_t s);
+int launch_mass(const zeta_ctx* c, const unsigned long long* hist, int l, double* partials, cudaStream_t s);
 // Number of per-CTA partial Grams launch_gram_particles writes.
 int gram_particle_parts(const zeta_ctx* c);
 // out[b1][b2] += scale * (1/ *wdiv if wdiv) * sum_cta partials[cta][b1][b2], symmetrised.
