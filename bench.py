@@ -290,7 +290,7 @@ def _cufft_reference(w, nb, stages, stream):
 
 
 def _catalogue_bytes(w, nb, forms):
-    """One-pass algorithmic HBM bytes of one catalogue (the survey's per-catalogue minimum):
+    """One-pass algorithmic HBM bytes of one catalogue (the minimum traffic of the whole path):
     assignment 16 N_p + 4 N_g, R2C 16 N_g, and per (l, m) the delta_hat read, each field written
     once and read once after a single transpose round trip (16 N_g per field), the particles
     (particle form) and the delta re-read plus a second field read (node form)."""
