@@ -115,8 +115,9 @@ def assign_noalloc(n: int, box: float, dsup: int, particles, delta=None, wsum=No
         delta = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
     if wsum is None:
         wsum = torch.empty(1, dtype=torch.float64, device="cuda")
-    _check("zeta_assign_noalloc", lib().zeta_assign_noalloc(n, float(box), dsup, _ptr(particles), particles.shape[0],
-                                                            _ptr(delta), _ptr(wsum), _stream()))
+    _check("zeta_assign_noalloc", lib().zeta_assign_noalloc(n, float(box), dsup, _f32(particles, "particles", cols=4),
+                                                            particles.shape[0], _f32(delta, "delta", n ** 3),
+                                                            _f64(wsum, "wsum", 1), _stream()))
     return delta, wsum
 
 
@@ -143,6 +144,41 @@ def deinterleave(a, nb: int):
 
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _arg(t, name: str, dtype, numel: int = 0, cols: int | None = None):
+    """Device pointer of a tensor argument after checking it: a torch tensor of `dtype`,
+    contiguous, with at least `numel` elements (or of shape (N, cols)), on the current CUDA
+    device.  A host tensor or a short buffer would otherwise reach a kernel as a bad address.
+    None passes through (optional arguments)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor, got {type(t).__name__}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected dtype {dtype}, got {t.dtype}")
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"{name}: expected shape (N, {cols}), got {tuple(t.shape)}")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: needs at least {numel} elements, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor, got one on {t.device}")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on {t.device}, but the current device is cuda:{torch.cuda.current_device()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t, name, numel=0, cols=None):
+    import torch
+    return _arg(t, name, torch.float32, numel, cols)
+
+
+def _f64(t, name, numel=0):
+    import torch
+    return _arg(t, name, torch.float64, numel)
 
 
 def _stream():
@@ -198,28 +234,33 @@ class Context:
         import torch
         return torch.empty((self.n, self.n, self.n), dtype=dtype or torch.float32, device="cuda")
 
+    def _alm_numel(self) -> int:
+        """Floats in the bin-interleaved fields of all bins: ceil(nb / 4) groups of n^3 x 4."""
+        return 4 * ((self.nbins + 3) // 4) * self.ng
+
     # ---- the C-ABI calls ----
     def assign(self, particles):
         import torch
         delta = self._grid()
         wsum = torch.empty(1, dtype=torch.float64, device="cuda")
-        _check("zeta_assign", lib().zeta_assign(self._h, _ptr(particles), particles.shape[0], _ptr(delta),
-                                                _ptr(wsum), _stream()))
+        _check("zeta_assign", lib().zeta_assign(self._h, _f32(particles, "particles", cols=4), particles.shape[0],
+                                                _ptr(delta), _ptr(wsum), _stream()))
         return delta, wsum
 
     def fft_r2c(self, delta):
         import torch
         dhat = torch.empty((self.n, self.n, self.n // 2, 2), dtype=torch.float32, device="cuda")
-        _check("zeta_fft_r2c", lib().zeta_fft_r2c(self._h, _ptr(delta), _ptr(dhat), _stream()))
+        _check("zeta_fft_r2c", lib().zeta_fft_r2c(self._h, _f32(delta, "delta", self.ng), _ptr(dhat), _stream()))
         return dhat
 
     def reconstruct_alm(self, delta_hat, l: int, m: int, b0: int = 0, b1: int | None = None, out=None):
         import torch
         b1 = self.nbins if b1 is None else b1
+        g = max(0, (b1 - b0 + 3) // 4)
         if out is None:
-            g = (b1 - b0 + 3) // 4
             out = torch.empty((g, self.n, self.n, self.n, 4), dtype=torch.float32, device="cuda")
-        _check("zeta_reconstruct_alm", lib().zeta_reconstruct_alm(self._h, _ptr(delta_hat), l, m, b0, b1, _ptr(out),
+        _check("zeta_reconstruct_alm", lib().zeta_reconstruct_alm(self._h, _f32(delta_hat, "delta_hat", self.ng), l, m,
+                                                                  b0, b1, _f32(out, "out", 4 * g * self.ng),
                                                                   _stream()))
         return out
 
@@ -231,8 +272,9 @@ class Context:
 
     def sum_grid(self, delta, alm, form: str = "node", gram=None):
         gram = self._gram(gram)
-        _check("zeta_sum_grid", lib().zeta_sum_grid(self._h, _ptr(delta), _ptr(alm), FORM_BITS[form], _ptr(gram),
-                                                    _stream()))
+        _check("zeta_sum_grid", lib().zeta_sum_grid(self._h, _f32(delta, "delta", self.ng),
+                                                    _f32(alm, "alm", self._alm_numel()), FORM_BITS[form],
+                                                    _f64(gram, "gram", self.nbins ** 2), _stream()))
         return gram
 
     def sort_particles(self, particles):
@@ -241,21 +283,26 @@ class Context:
         sorted_ = torch.empty((np_, 4), dtype=torch.float32, device="cuda")
         ntile = lib().zeta_tile_count(self._h)
         start = torch.empty(ntile + 1, dtype=torch.int64, device="cuda")
-        _check("zeta_sort_particles", lib().zeta_sort_particles(self._h, _ptr(particles), np_, _ptr(sorted_),
-                                                                _ptr(start), _stream()))
+        _check("zeta_sort_particles", lib().zeta_sort_particles(self._h, _f32(particles, "particles", cols=4), np_,
+                                                                _ptr(sorted_), _ptr(start), _stream()))
         return sorted_, start
 
     def sum_particles(self, sorted_, tile_start, wsum, alm, gram=None):
         gram = self._gram(gram)
-        _check("zeta_sum_particles", lib().zeta_sum_particles(self._h, _ptr(sorted_), _ptr(tile_start),
-                                                              sorted_.shape[0], _ptr(wsum), _ptr(alm), _ptr(gram),
+        import torch
+        ntile = lib().zeta_tile_count(self._h)
+        _check("zeta_sum_particles", lib().zeta_sum_particles(self._h, _f32(sorted_, "sorted", cols=4),
+                                                              _arg(tile_start, "tile_start", torch.int64, ntile + 1),
+                                                              sorted_.shape[0], _f64(wsum, "wsum", 1),
+                                                              _f32(alm, "alm", self._alm_numel()),
+                                                              _f64(gram, "gram", self.nbins ** 2),
                                                               _stream()))
         return gram
 
     def mass_term(self, delta_hat, l: int, sign: float = 1.0, gram=None):
         gram = self._gram(gram)
-        _check("zeta_mass_term", lib().zeta_mass_term(self._h, _ptr(delta_hat), l, float(sign), _ptr(gram),
-                                                      _stream()))
+        _check("zeta_mass_term", lib().zeta_mass_term(self._h, _f32(delta_hat, "delta_hat", self.ng), l, float(sign),
+                                                      _f64(gram, "gram", self.nbins ** 2), _stream()))
         return gram
 
     def zeta_ell(self, particles=None, delta=None, forms=("particle",), out=None):
@@ -267,8 +314,10 @@ class Context:
             out = torch.empty((len(order), self.lmax + 1, self.nbins, self.nbins), dtype=torch.float64,
                               device="cuda")
         np_ = 0 if particles is None else particles.shape[0]
-        _check("zeta_zeta_ell", lib().zeta_zeta_ell(self._h, _ptr(particles), np_, _ptr(delta), bits, _ptr(out),
-                                                    _stream()))
+        per = (self.lmax + 1) * self.nbins ** 2
+        _check("zeta_zeta_ell", lib().zeta_zeta_ell(self._h, _f32(particles, "particles", cols=4), np_,
+                                                    _f32(delta, "delta", self.ng), bits,
+                                                    _f64(out, "out", len(order) * per), _stream()))
         return {f: out[i] for i, f in enumerate(order)}
 
     def profile_enable(self, on: bool = True):
@@ -306,7 +355,8 @@ class Context:
         w = self._weights(weights)
         if grad is None:
             grad = torch.empty((self.n, self.n, self.n), dtype=torch.float32, device="cuda")
-        _check("zeta_backward_node", lib().zeta_backward_node(self._h, _ptr(delta), w.ctypes.data, _ptr(grad), _stream()))
+        _check("zeta_backward_node", lib().zeta_backward_node(self._h, _f32(delta, "delta", self.ng), w.ctypes.data,
+                                                              _f32(grad, "grad", self.ng), _stream()))
         return grad
 
     def backward_particles(self, particles, weights, grad=None):
@@ -315,8 +365,10 @@ class Context:
         w = self._weights(weights)
         if grad is None:
             grad = torch.empty((particles.shape[0], 3), dtype=torch.float32, device="cuda")
-        _check("zeta_backward_particles", lib().zeta_backward_particles(self._h, _ptr(particles), particles.shape[0],
-                                                                        w.ctypes.data, _ptr(grad), _stream()))
+        _check("zeta_backward_particles", lib().zeta_backward_particles(self._h, _f32(particles, "particles", cols=4),
+                                                                        particles.shape[0], w.ctypes.data,
+                                                                        _f32(grad, "grad", 3 * particles.shape[0]),
+                                                                        _stream()))
         return grad
 
     def batch(self, particles, offsets, forms=("particle",), out=None):
@@ -333,12 +385,15 @@ class Context:
             out = torch.empty((ncat, nforms, self.lmax + 1, self.nbins, self.nbins), dtype=torch.float64,
                               device="cuda")
         self._batch_offsets = offs  # the library keeps a copy; hold ours for the caller's reuse
-        _check("zeta_batch", lib().zeta_batch(self._h, _ptr(particles), offs.ctypes.data, ncat, bits, _ptr(out),
-                                              _stream()))
+        if particles.shape[0] < int(offs[-1]):
+            raise ValueError(f"particles: offsets reach {int(offs[-1])} rows, got {particles.shape[0]}")
+        per = (self.lmax + 1) * self.nbins ** 2
+        _check("zeta_batch", lib().zeta_batch(self._h, _f32(particles, "particles", cols=4), offs.ctypes.data, ncat,
+                                              bits, _f64(out, "out", ncat * nforms * per), _stream()))
         return out
 
     def autotune(self, particles, forms=("particle",)) -> list:
-        _check("zeta_autotune", lib().zeta_autotune(self._h, _ptr(particles), particles.shape[0],
+        _check("zeta_autotune", lib().zeta_autotune(self._h, _f32(particles, "particles", cols=4), particles.shape[0],
                                                     self.form_bits(forms), _stream()))
         return self.tuning()
 
