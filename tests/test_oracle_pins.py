@@ -4,7 +4,6 @@ force.  Each test names the oracle function(s) it pins.  CPU only.
 """
 import math
 import os
-
 import warnings
 
 import numpy as np
