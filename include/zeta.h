@@ -283,6 +283,20 @@ int zeta_host_jbar(int l, double box, double r_lo, double r_hi, const int64_t* n
  * device uses (host copy of the constants). */
 double zeta_host_ylm(int l, int m, double vx, double vy, double vz);
 
+/* Mhat(k) = M(0) + 2 sum_{0<a<dsup} M(a) cos(2 pi k a / n) for 0 <= k < n, in float64: the 1-D
+ * factor of the B-spline mass matrix's DFT in the uniform term of the particle form (Sec. 2.2,
+ * Eq. DDD-sum-privertex); M(a) = int beta_D(u) beta_D(u - a) du.  The context's device table is
+ * its float32 rounding.  out: n doubles, caller-owned host memory.  2 <= n <= 2^20, dsup 2 or
+ * 4, else ZETA_EINVAL. */
+int zeta_host_mass_hat(int n, int dsup, double* out);
+
+/* The per-cell quadrature of the connection-coefficient (Gamma) form (Eqs. con-coeff,
+ * SFC-3PCF): q Gauss-Legendre nodes t[i] and weights wq[i] on [0, 1], and
+ * beta[i * dsup + o] = beta_D(t[i] + dsup/2 - 1 - o), the stencil weights at node i.  Host
+ * arrays of q, q and q * dsup doubles, caller-owned.  1 <= q <= 32, dsup 2 or 4, else
+ * ZETA_EINVAL. */
+int zeta_host_cell_quadrature(int q, int dsup, double* t, double* wq, double* beta);
+
 #ifdef __cplusplus
 }
 #endif

@@ -216,15 +216,21 @@ void host_mass_1d(int dsup, double* out) {
   for (int a = -(dsup - 1); a <= dsup - 1; ++a) out[a + dsup - 1] = cardinal_bspline(2 * dsup, a);
 }
 
-void host_mass_hat(int n, int dsup, std::vector<float>& out) {
+static void mass_hat_f64(int n, int dsup, double* out) {
   double m[16];
   host_mass_1d(dsup, m);
-  out.resize(n);
   for (int k = 0; k < n; ++k) {
     double v = m[dsup - 1];
     for (int a = 1; a < dsup; ++a) v += 2.0 * m[dsup - 1 + a] * std::cos(2.0 * kPi * k * a / n);
-    out[k] = static_cast<float>(v);
+    out[k] = v;
   }
+}
+
+void host_mass_hat(int n, int dsup, std::vector<float>& out) {
+  std::vector<double> v(n);
+  mass_hat_f64(n, dsup, v.data());
+  out.resize(n);
+  for (int k = 0; k < n; ++k) out[k] = static_cast<float>(v[k]);
 }
 
 void host_cell_quadrature(int q, int dsup, std::vector<double>& t, std::vector<double>& wq,
@@ -250,6 +256,24 @@ extern "C" int zeta_host_jbar(int l, double box, double r_lo, double r_hi, const
   for (int64_t i = 0; i < count; ++i)
     if (n2[i] < 0) return ZETA_EINVAL;
   zk::host_jbar_values(l, box, r_lo, r_hi, n2, count, out);
+  return ZETA_OK;
+}
+
+extern "C" int zeta_host_mass_hat(int n, int dsup, double* out) {
+  if (n < 2 || n > (1 << 20) || (dsup != 2 && dsup != 4) || !out) return ZETA_EINVAL;
+  zk::mass_hat_f64(n, dsup, out);
+  return ZETA_OK;
+}
+
+extern "C" int zeta_host_cell_quadrature(int q, int dsup, double* t, double* wq, double* beta) {
+  if (q < 1 || q > 32 || (dsup != 2 && dsup != 4) || !t || !wq || !beta) return ZETA_EINVAL;
+  std::vector<double> tv, wv, bv;
+  zk::host_cell_quadrature(q, dsup, tv, wv, bv);
+  for (int i = 0; i < q; ++i) {
+    t[i] = tv[i];
+    wq[i] = wv[i];
+  }
+  for (size_t i = 0; i < bv.size(); ++i) beta[i] = bv[i];
   return ZETA_OK;
 }
 

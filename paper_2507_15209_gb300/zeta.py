@@ -69,6 +69,8 @@ _SIGS = {
     "zeta_profile_stage_name": ([_INT], ctypes.c_char_p),
     "zeta_host_jbar": ([_INT, _DBL, _DBL, _DBL, _VP, _I64, _VP], _INT),
     "zeta_host_ylm": ([_INT, _INT, _DBL, _DBL, _DBL], _DBL),
+    "zeta_host_mass_hat": ([_INT, _INT, _VP], _INT),
+    "zeta_host_cell_quadrature": ([_INT, _INT, _VP, _VP, _VP], _INT),
 }
 
 
@@ -105,6 +107,22 @@ def host_jbar(l: int, box: float, r_lo: float, r_hi: float, n2) -> np.ndarray:
 
 def host_ylm(l: int, m: int, vx: float, vy: float, vz: float) -> float:
     return lib().zeta_host_ylm(l, m, vx, vy, vz)
+
+
+def host_mass_hat(n: int, dsup: int) -> np.ndarray:
+    out = np.empty(n, np.float64)
+    _check("zeta_host_mass_hat", lib().zeta_host_mass_hat(n, dsup, out.ctypes.data))
+    return out
+
+
+def host_cell_quadrature(q: int, dsup: int):
+    """(t, wq, beta[q, dsup]) of zeta_host_cell_quadrature."""
+    t = np.empty(q, np.float64)
+    wq = np.empty(q, np.float64)
+    beta = np.empty((q, dsup), np.float64)
+    _check("zeta_host_cell_quadrature", lib().zeta_host_cell_quadrature(q, dsup, t.ctypes.data, wq.ctypes.data,
+                                                                        beta.ctypes.data))
+    return t, wq, beta
 
 
 def assign_noalloc(n: int, box: float, dsup: int, particles, delta=None, wsum=None):

@@ -92,3 +92,38 @@ def test_host_ylm_matches_oracle(zmod):
             np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12)
     assert zmod.host_ylm(0, 0, 0.0, 0.0, 0.0) == pytest.approx(1 / math.sqrt(4 * math.pi), rel=1e-15)
     assert zmod.host_ylm(3, 1, 0.0, 0.0, 0.0) == 0.0
+
+
+@pytest.mark.parametrize("n,dsup", [(16, 2), (16, 4), (512, 4)])
+def test_host_mass_hat_matches_oracle(zmod, n, dsup):
+    got = zmod.host_mass_hat(n, dsup)
+    m = O.mass_1d(dsup)
+    k = np.arange(n)
+    want = sum(m[a] * np.cos(2 * math.pi * k * a / n) for a in m)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+    assert got[0] == pytest.approx(1.0, abs=1e-14)  # sum_a M(a) = (int beta)^2 = 1
+    np.testing.assert_allclose(got[1:], got[1:][::-1], rtol=0, atol=1e-15)  # Mhat(k) = Mhat(n - k)
+    assert np.all(got > 0)  # the sampled B-spline autocorrelation has a positive DFT
+
+
+@pytest.mark.parametrize("q,dsup", [(2, 2), (5, 4), (12, 4)])
+def test_host_cell_quadrature_matches_oracle(zmod, q, dsup):
+    t, wq, beta = zmod.host_cell_quadrature(q, dsup)
+    x, w = np.polynomial.legendre.leggauss(q)
+    np.testing.assert_allclose(t, 0.5 * (x + 1.0), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(wq, 0.5 * w, rtol=0, atol=1e-15)
+    for o in range(dsup):
+        np.testing.assert_allclose(beta[:, o], O.bspline(t + dsup // 2 - 1 - o, dsup), rtol=0, atol=4e-15)
+    np.testing.assert_allclose(beta.sum(1), 1.0, rtol=0, atol=1e-15)  # partition of unity
+    # exact for polynomials of degree 2q - 1 on the cell
+    for p in range(2 * q):
+        assert float(np.sum(wq * t ** p)) == pytest.approx(1.0 / (p + 1), abs=1e-14)
+
+
+def test_host_table_helpers_reject_bad_arguments(zmod):
+    lib = zmod.lib()
+    out = np.empty(64, np.float64)
+    assert lib.zeta_host_mass_hat(16, 3, out.ctypes.data) == -1
+    assert lib.zeta_host_mass_hat(1, 4, out.ctypes.data) == -1
+    assert lib.zeta_host_cell_quadrature(0, 4, out.ctypes.data, out.ctypes.data, out.ctypes.data) == -1
+    assert lib.zeta_host_cell_quadrature(5, 4, None, out.ctypes.data, out.ctypes.data) == -1
