@@ -283,6 +283,14 @@ int zeta_host_jbar(int l, double box, double r_lo, double r_hi, const int64_t* n
  * device uses (host copy of the constants). */
 double zeta_host_ylm(int l, int m, double vx, double vy, double vz);
 
+/* The window table a context uploads (Eq. 3PCF-multipole-window averaged over each radial
+ * bin, Fig. 1 step (3)): out[(l * N2 + n2) * nbp + b] = sqrt(4 pi) jbar_l(2 pi sqrt(n2) / box;
+ * [edges[b], edges[b+1])) / n^3 in float32, for l <= lmax, n2 < N2 = 3 (n/2 - 1)^2 + 1 and
+ * b < nbins, with nbp = 4 ceil(nbins / 4) and the padding bins zero.  out: caller-owned host
+ * memory of (lmax + 1) N2 nbp floats.  n a power of two in [4, 512], box > 0, lmax <= 14,
+ * 1 <= nbins <= 32, edges (nbins + 1 values) positive and increasing, else ZETA_EINVAL. */
+int zeta_host_jbar_table(int n, double box, int lmax, int nbins, const double* edges, float* out);
+
 /* Mhat(k) = M(0) + 2 sum_{0<a<dsup} M(a) cos(2 pi k a / n) for 0 <= k < n, in float64: the 1-D
  * factor of the B-spline mass matrix's DFT in the uniform term of the particle form (Sec. 2.2,
  * Eq. DDD-sum-privertex); M(a) = int beta_D(u) beta_D(u - a) du.  The context's device table is

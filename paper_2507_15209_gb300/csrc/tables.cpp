@@ -259,6 +259,19 @@ extern "C" int zeta_host_jbar(int l, double box, double r_lo, double r_hi, const
   return ZETA_OK;
 }
 
+extern "C" int zeta_host_jbar_table(int n, double box, int lmax, int nbins, const double* edges, float* out) {
+  if (n < 4 || n > 512 || (n & (n - 1)) || !(box > 0) || lmax < 0 || lmax > zk::kMaxL || nbins < 1 ||
+      nbins > zk::kMaxBins || !edges || !out)
+    return ZETA_EINVAL;
+  if (!(edges[0] > 0)) return ZETA_EINVAL;
+  for (int b = 0; b < nbins; ++b)
+    if (!(edges[b + 1] > edges[b])) return ZETA_EINVAL;
+  std::vector<float> t;
+  zk::host_jbar_table(n, box, lmax, nbins, edges, t);
+  for (size_t i = 0; i < t.size(); ++i) out[i] = t[i];
+  return ZETA_OK;
+}
+
 extern "C" int zeta_host_mass_hat(int n, int dsup, double* out) {
   if (n < 2 || n > (1 << 20) || (dsup != 2 && dsup != 4) || !out) return ZETA_EINVAL;
   zk::mass_hat_f64(n, dsup, out);

@@ -69,6 +69,7 @@ _SIGS = {
     "zeta_profile_stage_name": ([_INT], ctypes.c_char_p),
     "zeta_host_jbar": ([_INT, _DBL, _DBL, _DBL, _VP, _I64, _VP], _INT),
     "zeta_host_ylm": ([_INT, _INT, _DBL, _DBL, _DBL], _DBL),
+    "zeta_host_jbar_table": ([_INT, _DBL, _INT, _INT, _VP, _VP], _INT),
     "zeta_host_mass_hat": ([_INT, _INT, _VP], _INT),
     "zeta_host_cell_quadrature": ([_INT, _INT, _VP, _VP, _VP], _INT),
 }
@@ -107,6 +108,18 @@ def host_jbar(l: int, box: float, r_lo: float, r_hi: float, n2) -> np.ndarray:
 
 def host_ylm(l: int, m: int, vx: float, vy: float, vz: float) -> float:
     return lib().zeta_host_ylm(l, m, vx, vy, vz)
+
+
+def host_jbar_table(n: int, box: float, lmax: int, edges) -> np.ndarray:
+    """The context's window table, float32 (lmax + 1, 3 (n/2 - 1)^2 + 1, 4 ceil(nb / 4))."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = len(e) - 1
+    nbp = 4 * ((nb + 3) // 4)
+    h = n // 2 - 1
+    out = np.empty((lmax + 1, 3 * h * h + 1, nbp), np.float32)
+    _check("zeta_host_jbar_table", lib().zeta_host_jbar_table(n, float(box), lmax, nb, e.ctypes.data,
+                                                              out.ctypes.data))
+    return out
 
 
 def host_mass_hat(n: int, dsup: int) -> np.ndarray:

@@ -127,3 +127,22 @@ def test_host_table_helpers_reject_bad_arguments(zmod):
     assert lib.zeta_host_mass_hat(1, 4, out.ctypes.data) == -1
     assert lib.zeta_host_cell_quadrature(0, 4, out.ctypes.data, out.ctypes.data, out.ctypes.data) == -1
     assert lib.zeta_host_cell_quadrature(5, 4, None, out.ctypes.data, out.ctypes.data) == -1
+
+
+@pytest.mark.parametrize("n,box,lmax,edges", [
+    (16, 120.0, 14, [10.0, 20.0, 32.0, 45.0, 50.0, 55.0]),
+    (64, 500.0, 6, [10.0, 20.0, 30.0, 40.0, 50.0, 60.0, 70.0, 80.0, 90.0]),
+])
+def test_host_window_table_matches_oracle(zmod, n, box, lmax, edges):
+    # the exact float32 table a context uploads: layout [l][|n|^2][bin], bins padded to 4 with zeros
+    tab = zmod.host_jbar_table(n, box, lmax, edges)
+    nb = len(edges) - 1
+    h = n // 2 - 1
+    assert tab.shape == (lmax + 1, 3 * h * h + 1, 4 * ((nb + 3) // 4))
+    assert not np.any(tab[:, :, nb:])
+    k = 2 * math.pi / box * np.sqrt(np.arange(3 * h * h + 1, dtype=np.float64))
+    pref = math.sqrt(4 * math.pi) / n ** 3
+    for ell in range(lmax + 1):
+        for b in range(nb):
+            want = pref * O.jbar(ell, k, edges[b], edges[b + 1])
+            np.testing.assert_allclose(tab[ell, :, b], want, rtol=1e-6, atol=1e-9 * pref)
