@@ -58,3 +58,17 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = bench.argparse.Namespace(steps=1, warmup=3, workload="box500_n64_np20k")
     assert bench.run_reference(args, bench.WORKLOADS["box500_n64_np20k"], rank=1, world=2) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_algorithmic_byte_counts_of_the_headline_workload():
+    # the per-call and per-catalogue minimum bytes the roofline figures divide by
+    import bench
+    w = bench.WORKLOADS["box2000_n512_np16m"]
+    g = 4.0 * 512 ** 3
+    assert bench._alg_bytes("gram_particles", w, 20) == pytest.approx(20 * g + 16 * 16e6)   # 10.99 GB
+    assert bench._alg_bytes("gram_particles", w, 20) == pytest.approx(10.993418240e9)
+    assert bench._alg_bytes("alm_y", w, 20) == 2 * g * 20
+    assert bench._alg_bytes("gram_node", w, 20) == g * 21
+    assert bench._alg_bytes("no_such_stage", w, 20) is None
+    cat = bench._catalogue_bytes(w, 20, ("particle", "node"))
+    assert cat == pytest.approx(6.659977150464e12)                                       # 6.66 TB
