@@ -7,7 +7,8 @@
 //                  v = f_b = sum_l beta a_b(l), w = q-weight * n_rec(node); exact for the
 //                  piecewise-polynomial integrand, hence equal to the connection-coefficient
 //                  double sum of Eqs. (con-coeff) and (SFC-3PCF)
-//   mass term      points = half-spectrum modes, v = jbar_b(|k|), w = |delta_hat|^2 Mhat(k)
+//   mass term      points = the integer values of |n|^2, v = jbar_b(|k|), w = the sum of
+//                  (1 or 2) |delta_hat|^2 Mhat over the half-spectrum modes of that |n|^2
 // The particle form (Eq. DDD-sum-privertex) is in particles.cu.  The weighted-Gram machinery
 // shared by all of them is in gram.cuh.
 #include "gram.cuh"
