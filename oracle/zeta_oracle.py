@@ -47,7 +47,7 @@ __all__ = [
     "bspline", "stencil_base", "assign", "contrast", "fft_integers", "nyquist_mask",
     "jbar", "real_ylm", "window_kernel", "multipole_fields", "sum_node",
     "gamma_1d", "mass_1d", "sum_gamma", "interpolate", "sum_particles",
-    "mass_term", "zeta_multipoles", "zeta_from_delta", "brute_force_raw",
+    "mass_term", "mass_term_fourier", "zeta_multipoles", "zeta_from_delta", "brute_force_raw",
     "bspline_deriv", "interpolate_grad", "loss", "grad_node_delta", "grad_particle_positions",
 ]
 
@@ -339,6 +339,32 @@ def mass_term(a, dsup: int):
             for dx, mx in m1.items():
                 out += (mz * my * mx) * (af @ _shift(a, (dz, dy, dx)).reshape(nb, -1).T)
     return out / ng
+
+
+def mass_term_fourier(delta_hat, ell: int, n: int, box: float, edges, dsup: int, bins=None):
+    """U summed over m for one l, in Fourier space (reading R7 with the addition theorem).
+
+    The real-space form above is (1/N_g) a_b1^T M3 a_b2 with a_b = IDFT(delta_hat K_b); by
+    Parseval it is (1/N_g^2) sum_n conj(K_b1) K_b2 |delta_hat|^2 Mhat(n), Mhat the DFT of the
+    separable mass sequence M(a).  Summing R_lm R_lm over m gives (2l+1)/(4 pi) (the addition
+    theorem, Eq. double-e-expansion-sep of the appendix), so
+      U_l[b1][b2] = (2l+1)/N_g^2 sum_{n not Nyquist} |delta_hat(n)|^2 Mhat(n) jbar_l(k_n;b1) jbar_l(k_n;b2).
+    Returns (len(bins), len(bins)).
+    """
+    m1 = mass_1d(dsup)
+    iv = fft_integers(n)
+    mhat1 = np.array([sum(v * math.cos(2.0 * math.pi * k * a / n) for a, v in m1.items()) for k in iv])
+    nx, ny, nz = _grid_integers(n)
+    n2 = nx * nx + ny * ny + nz * nz
+    keep = ~nyquist_mask(n)
+    p = (np.abs(delta_hat) ** 2 * (mhat1[:, None, None] * mhat1[None, :, None] * mhat1[None, None, :]))[keep]
+    n2k = n2[keep]
+    uniq, inv = np.unique(n2k, return_inverse=True)
+    psum = np.bincount(inv.ravel(), weights=p, minlength=len(uniq))  # |delta_hat|^2 Mhat per |n|^2
+    kmag = 2.0 * math.pi / box * np.sqrt(uniq.astype(np.float64))
+    bins = list(range(len(edges) - 1)) if bins is None else list(bins)
+    jb = np.stack([jbar(ell, kmag, edges[b], edges[b + 1]) for b in bins])
+    return (2 * ell + 1) * (jb * psum[None, :]) @ jb.T / float(n) ** 6
 
 
 # ---------------------------------------------------------------------------

@@ -337,6 +337,7 @@ def test_mass_term_matches_fourier_space_form(dsup):
         want = np.array([[(2 * ell + 1) * np.sum((np.abs(dh) ** 2 * j[b1] * j[b2] * mh)[keep])
                           for b2 in range(2)] for b1 in range(2)]) / n ** 6
         np.testing.assert_allclose(u, want, rtol=1e-11, atol=1e-14)
+        np.testing.assert_allclose(O.mass_term_fourier(dh, ell, n, box, edges, dsup), u, rtol=1e-11, atol=1e-14)
 
 
 # --- whole pipeline: symmetries and invariances ---------------------------------------------
