@@ -259,6 +259,11 @@ int zeta_get_status(zeta_ctx* ctx, zeta_stream stream);
  *   - Every call reuses the same array and clears it itself; calls that can overlap on the
  *     GPU (different streams, or different host threads on one device) race on it and must be
  *     ordered by the caller.
+ *   - The looked-up address is kept for the life of the process: after cudaDeviceReset (or any
+ *     other teardown of the device's primary context) this entry point must not be called again.
+ *   - Non-finite input: zeta_assign reports a particle with a NaN or infinite component through
+ *     zeta_get_status; this call has no context and does not synchronise, so it reports it in
+ *     the result instead: if any particle is non-finite, every value of delta and *wsum is NaN.
  *   - Calls no cudaMalloc, cudaFree or allocating library routine. */
 int zeta_assign_noalloc(int n, double box, int dsup, const float* particles, int64_t np, float* delta,
                         double* wsum, zeta_stream stream);

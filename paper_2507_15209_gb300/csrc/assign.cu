@@ -297,6 +297,19 @@ constexpr long long kStaticWords = kStaticAcc + 2 * kRedCtas + 4 + 1;
 
 static __device__ __align__(256) unsigned long long g_assign_scratch[kStaticWords];
 
+// A non-finite particle latched the status word: make the whole result NaN, so that the
+// caller sees the bad input in the output itself (this entry point has no context to report
+// through and does not synchronise).
+__global__ void k_poison_if_bad(const int* __restrict__ status, float* __restrict__ delta, long long ng,
+                                double* __restrict__ wsum) {
+  if (*status == 0) return;
+  const float qnan = __int_as_float(0x7fc00000);
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < ng;
+       i += static_cast<long long>(blockDim.x) * gridDim.x)
+    delta[i] = qnan;
+  if (wsum && blockIdx.x == 0 && threadIdx.x == 0) *wsum = __longlong_as_double(0x7ff8000000000000LL);
+}
+
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 unsigned long long* g_static_ptr[kMaxDevices] = {};
@@ -346,6 +359,7 @@ extern "C" int zeta_assign_noalloc(int n, double box, int dsup, const float* par
   else
     k_assign_scatter<4><<<g, 256, 0, s>>>(p, np, n, inv_h, wstat, acc);
   k_assign_finalize<<<grid_for(ng, 256, sms), 256, 0, s>>>(acc, ng, wstat, delta);
+  k_poison_if_bad<<<grid_for(ng, 256, sms), 256, 0, s>>>(status, delta, ng, wsum);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 

@@ -140,7 +140,8 @@ def host_cell_quadrature(q: int, dsup: int):
 
 def assign_noalloc(n: int, box: float, dsup: int, particles, delta=None, wsum=None):
     """zeta_assign_noalloc: B-spline assignment with the library's fixed scratch (no allocation
-    inside the call; the caller may pass preallocated delta / wsum tensors)."""
+    inside the call; the caller may pass preallocated delta / wsum tensors).  A non-finite
+    particle makes every value of delta and wsum NaN."""
     import torch
     if delta is None:
         delta = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
