@@ -234,9 +234,10 @@ __global__ void __launch_bounds__(kThreads)
 // J_l,b2(|n|^2), w = (1, or 2 off the ix = 0 plane) |delta_hat|^2 Mhat over the stored half
 // spectrum without its Nyquist planes.  The window depends on the mode only through the
 // integer |n|^2, so w is summed per |n|^2 once per catalogue and each l is then a Gram over
-// the 3 (n/2)^2 + 1 values of |n|^2.  The per-|n|^2 sums are 64-bit fixed point in units of
-// max(w) 2^-48: integer atomics, so the sums do not depend on the order of the modes, and a
-// value of |n|^2 holds far fewer than 2^16 modes, so no sum can overflow.
+// the 3 (n/2 - 1)^2 + 1 values of |n|^2 (Nyquist planes excluded).  The per-|n|^2 sums are
+// 64-bit fixed point in units of max(w) 2^-48: integer atomics, so the sums do not depend on
+// the order of the modes, and a value of |n|^2 holds far fewer than 2^16 modes, so no sum can
+// overflow.
 constexpr double kMassUnit = 281474976710656.0;  // 2^48
 
 __device__ __forceinline__ bool mass_mode(long long i, int n, const float2* __restrict__ dhat,

@@ -292,12 +292,15 @@ extern "C" int zeta_host_cell_quadrature(int q, int dsup, double* t, double* wq,
 
 extern "C" double zeta_host_ylm(int l, int m, double vx, double vy, double vz) {
   if (l < 0 || l > zk::kMaxL || m < -l || m > l) return 0.0;
-  static double mm[zk::kMaxL + 1], a[(zk::kMaxL + 1) * (zk::kMaxL + 1)], b[(zk::kMaxL + 1) * (zk::kMaxL + 1)];
-  static bool init = false;
-  if (!init) {
-    zk::host_ylm_constants(mm, a, b);
-    init = true;
-  }
+  // constants built once; a function-local static is initialised thread-safely (C++11)
+  struct Consts {
+    double mm[zk::kMaxL + 1], a[(zk::kMaxL + 1) * (zk::kMaxL + 1)], b[(zk::kMaxL + 1) * (zk::kMaxL + 1)];
+    Consts() { zk::host_ylm_constants(mm, a, b); }
+  };
+  static const Consts k;
+  const double* mm = k.mm;
+  const double* a = k.a;
+  const double* b = k.b;
   const double r2 = vx * vx + vy * vy + vz * vz;
   if (r2 == 0.0) return l == 0 ? 1.0 / std::sqrt(4.0 * 3.14159265358979323846) : 0.0;
   const double rinv = 1.0 / std::sqrt(r2);
