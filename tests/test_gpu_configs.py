@@ -1,0 +1,102 @@
+"""zeta_l of whole named workloads through the C ABI against the FP64 oracle's result (GPU).
+
+The expected values are in tests/golden/zeta_<workload>.json, written by
+tests/golden/make_zeta_golden.py, which calls only the oracle.  Each file records the SHA-256 of
+the seeded catalogue it was computed on; the catalogue is regenerated here and must match it
+bit for bit (numpy's PCG64 draws are platform-independent).
+
+  box500_n64_np20k   64^3, 500 Mpc/h, 20,000 log-normal particles, lmax 4, 8 bins 10-90,
+                     linear B-spline: node, Gamma and particle forms, and the uniform null
+                     catalogue of 20,000 points (the paper's plain method, Sec. 2.2)
+  box1000_n256_np2m  256^3, 1000 Mpc/h, 2,000,000 log-normal particles, lmax 10, 15 bins
+                     5-150, cubic B-spline: particle form (with its uniform term) and node form
+
+Tolerance (float32 path): per l, ||zeta_gpu - zeta_oracle||_F <= 1e-5 ||zeta_oracle||_F.  Where
+the condition sum C_l (sum of absolute values of the summed terms) is more than 100 times
+||zeta_l||, float32 products cannot reach that (each term carries a relative rounding of about
+1e-7, and the fields themselves come out of sums with cancellation); there the bound is
+1e-6 ||C_l||_F, a few float32 roundings of the condition sum, and the measured value is printed.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2507_15209_gb300 import mocks
+from paper_2507_15209_gb300.workloads import WORKLOADS, edges as wl_edges
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def Z():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_15209_gb300 import build
+    build.build()
+    from paper_2507_15209_gb300 import zeta
+    return zeta
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, f"zeta_{name}.json")) as fh:
+        return json.load(fh)
+
+
+def _catalogue(w, null):
+    if null:
+        return mocks.uniform_particles(w["n_p"], w["box"], w["null_seed"])
+    return mocks.lognormal_catalogue(w["n"], w["n_p"], w["box"], w["field_seed"], w["sample_seed"])
+
+
+def _check(got, want, cond, label):
+    """Per-l Frobenius check; returns the measured relative errors for the report."""
+    errs = []
+    for ell in range(want.shape[0]):
+        err = float(np.linalg.norm(got[ell] - want[ell]))
+        zn = float(np.linalg.norm(want[ell]))
+        cn = float(np.linalg.norm(cond[ell])) if cond is not None else 0.0
+        rel = err / zn
+        errs.append(rel)
+        if cond is not None and cn > 100.0 * zn:
+            print(f"{label} l={ell}: C_l/zeta_l = {cn / zn:.0f}, error / C_l = {err / cn:.1e}")
+            assert err <= 1e-6 * cn, (label, ell, rel, err / cn)
+        else:
+            assert rel <= 1e-5, (label, ell, rel)
+    return errs
+
+
+def _run(Z, name, part, forms):
+    w = WORKLOADS[name]
+    n, box, lmax, dsup = w["n"], w["box"], w["lmax"], w["dsup"]
+    e = wl_edges(w)
+    gold = _golden(name)[part]
+    parts = _catalogue(w, part == "null")
+    assert hashlib.sha256(parts.tobytes()).hexdigest() == gold["catalogue_sha256"], \
+        "the seeded catalogue differs from the one the oracle result was computed on"
+    ctx = Z.Context(n, box, dsup, lmax, e, np_max=len(parts), forms=forms)
+    z = ctx.zeta_ell(particles=torch.from_numpy(parts).cuda(), forms=forms)
+    assert ctx.get_status() == 0
+    report = {}
+    for f in forms:
+        got = z[f].cpu().numpy()
+        np.testing.assert_array_equal(got, np.swapaxes(got, 1, 2))
+        want = np.array(gold["zeta"][f])
+        cond = np.array(gold["cond"][f]) if f in gold["cond"] else None
+        report[f] = _check(got, want, cond, (name, part, f))
+    ctx.close()
+    print(name, part, {f: [f"{v:.1e}" for v in r] for f, r in report.items()})
+
+
+def test_plain_method_64_all_forms(Z):
+    _run(Z, "box500_n64_np20k", "data", ("node", "gamma", "particle"))
+
+
+def test_plain_method_64_uniform_null(Z):
+    _run(Z, "box500_n64_np20k", "null", ("node", "gamma", "particle"))
