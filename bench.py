@@ -10,7 +10,9 @@ mass term and the float64 reduction.  Default workload: 512^3 grid, 2000 Mpc/h b
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 runs under torchrun, one catalogue per rank (weak scaling, no collective on
-the data path; only a barrier and a max-reduce of the timings).  --impl reference
+the data path; only a barrier and a max-reduce of the timings), or with --partition lm
+one catalogue whose (l, m) pairs are split round robin over the ranks, the per-pair
+float64 slots summed by one NCCL all-reduce (strong scaling).  --impl reference
 times the FP64 CPU oracle on a bounded sample of the same workload and scales it
 to one catalogue.  Prints one JSON line on rank 0.
 """
@@ -106,16 +108,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def reduce_timings(ms_dev, ms_e2e, steps, world, dist=None, device="cuda"):
+def reduce_timings(ms_dev, ms_e2e, steps, world, dist=None, device="cuda", shared=False):
     """Whole-job seconds per catalogue: the slowest rank's time (max over ranks) divided by all
-    ranks' catalogues (steps per rank x world).  Returns (value, e2e value, max device ms, max
-    end-to-end ms)."""
+    ranks' catalogues (steps per rank x world; steps alone when the ranks share one catalogue per
+    step, as in the (l, m) split).  Returns (value, e2e value, max device ms, max end-to-end ms)."""
     import torch
     t = torch.tensor([ms_dev, ms_e2e], dtype=torch.float64, device=device)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    cats = steps * world
+    cats = steps if shared else steps * world
     return float(t[0]) / 1e3 / cats, float(t[1]) / 1e3 / cats, float(t[0]), float(t[1])
+
+
+def allreduce_slots(slots, dist):
+    """Sum the ranks' per-(l, m) slot arrays (float64).  Every slot has one non-zero contributor
+    (its owner), so the sum is exact and the reduced zeta equals the one-GPU result bit for bit."""
+    if dist is not None:
+        dist.all_reduce(slots, op=dist.ReduceOp.SUM)
+    return slots
 
 
 def _make_inputs(w, rank):
@@ -143,58 +153,144 @@ def _alg_bytes(stage, w, nb):
     }.get(stage)
 
 
-def _oracle_prepare(w, parts, sub=16):
-    """Oracle assignment of every sub-th particle (timed, scaled by sub) and forward DFT."""
-    from oracle import zeta_oracle as O
-    ps = parts[::sub].astype(np.float64)
+SUB = 16  # fraction of a grid or a catalogue one sampled oracle step runs on
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _avail_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 16.0
+
+
+def _timed(fn, *a, **k):
     t0 = time.perf_counter()
-    eps, wsum = O.assign(ps[:, :3], ps[:, 3], w["n"], w["box"], w["dsup"])
-    t_assign = (time.perf_counter() - t0) * sub
+    r = fn(*a, **k)
+    return r, time.perf_counter() - t0
+
+
+def _oracle_prepare(w, parts, cache):
+    """The per-catalogue steps of the FP64 oracle, run whole once: the assignment of the whole
+    catalogue, the forward DFT (whose cost also stands for one inverse DFT of a field: the same
+    transform size) and the sort of the integer |n|^2 that every window build does.  The grid,
+    its DFT and the particles go to `cache` for the sample workers."""
+    from oracle import zeta_oracle as O
+    n = w["n"]
+    p64 = parts.astype(np.float64)
+    (eps, wsum), t_assign = _timed(O.assign, p64[:, :3], p64[:, 3], n, w["box"], w["dsup"])
     delta = O.contrast(eps, wsum)
     del eps
-    t0 = time.perf_counter()
-    dh = np.fft.fftn(delta)
-    t_fft = time.perf_counter() - t0
-    return {"assign": t_assign, "fft": t_fft, "dh": dh, "sub": sub}
+    dh, t_fft = _timed(np.fft.fftn, delta)
+    iv = O.fft_integers(n)
+    n2 = iv[:, None, None] ** 2 + iv[None, :, None] ** 2 + iv[None, None, :] ** 2
+    (uniq, _), t_uniq = _timed(np.unique, n2, return_inverse=True)
+    del n2, dh
+    paths = {"delta": os.path.join(cache, "delta.npy"), "parts": os.path.join(cache, "parts.npy"),
+             "kmag": os.path.join(cache, "kmag.npy")}
+    np.save(paths["delta"], delta)
+    np.save(paths["parts"], p64[::SUB])
+    np.save(paths["kmag"], 2.0 * np.pi / w["box"] * np.sqrt(uniq.astype(np.float64)))
+    return {"assign": t_assign, "fft": t_fft, "uniq": t_uniq, "paths": paths}
 
 
-def _oracle_sample(w, parts, prep):
-    """Time the FP64 oracle on a bounded slice of the workload and scale to one catalogue.
-
-    Slice: the prepared assignment (every 16th particle, x16) and full forward DFT, plus one
-    (l, m, b) = (2, 1, nbins/2) field: R_lm on 1/16 of the grid (x16), jbar of one bin and
-    the full inverse DFT, then interpolation and Gram at every 16th particle (x16).
-    """
+def _oracle_unit(job):
+    """Sampled per-(l, m, b) steps of the oracle (run in a worker process), each on 1/SUB of its
+    input: R_lm and the window assembly on a slab of n/SUB z-planes, jbar of the bin on every
+    |n|^2, the B-spline interpolation and weighted Gram at every SUB-th particle, and the node
+    Gram over a slab of the grid for all bins.  Returns the measured seconds of each step."""
     from oracle import zeta_oracle as O
-    n, box, lmax, dsup = w["n"], w["box"], w["lmax"], w["dsup"]
+    w, l, m, b, paths = job
+    n, box, dsup = w["n"], w["box"], w["dsup"]
     e = wl_edges(w)
     nb = len(e) - 1
-    sub = prep["sub"]
-    ell, m, b = 2, 1, nb // 2
+    delta = np.load(paths["delta"], mmap_mode="r")
+    ps = np.load(paths["parts"])
+    kmag = np.load(paths["kmag"])
     iv = O.fft_integers(n)
-    nz, ny, nx = np.meshgrid(iv[: max(1, n // sub)], iv, iv, indexing="ij")
-    t0 = time.perf_counter()
-    O.real_ylm(ell, m, nx, ny, nz)
-    t_ylm = (time.perf_counter() - t0) * sub
+    nz, ny, nx = np.meshgrid(iv[: n // SUB], iv, iv, indexing="ij")
+    t = {}
+    ang, t["ylm"] = _timed(O.real_ylm, l, m, nx, ny, nz)
+    n2 = nx * nx + ny * ny + nz * nz
     del nx, ny, nz
+    jb, t["jbar"] = _timed(O.jbar, l, kmag, e[b], e[b + 1])
     t0 = time.perf_counter()
-    a = O.multipole_fields(prep["dh"], ell, m, n, box, e, bins=[b])
-    t_field = time.perf_counter() - t0
-    ps = parts[::sub].astype(np.float64)
+    idx = np.searchsorted((kmag * box / (2.0 * np.pi)) ** 2, n2.astype(np.float64) - 0.5)
+    kern = np.sqrt(4.0 * np.pi) * (1j ** l) * jb[np.minimum(idx, len(jb) - 1)] * ang
+    t["kern"] = time.perf_counter() - t0
+    del kern, ang, n2, idx
+    slab = np.asarray(delta[: n // SUB])
+    field = np.asarray(delta)[None]
+    f, t["interp"] = _timed(O.interpolate, field, ps[:, :3], n, box, dsup)
     t0 = time.perf_counter()
-    f = O.interpolate(a, ps[:, :3], n, box, dsup)
-    _ = (f * ps[:, 3]) @ f.T
-    t_interp = (time.perf_counter() - t0) * sub
-    del a, f
-    n_lm = (lmax + 1) ** 2
-    # per (l, m): one R_lm, then per bin jbar + inverse DFT (the field call minus its R_lm) + interpolation
-    t_bin = max(t_field - t_ylm, 0.0) + t_interp
-    total = prep["assign"] + prep["fft"] + n_lm * (t_ylm + nb * t_bin)
-    sample = (f"FP64 oracle on one catalogue of the workload: assignment of every {sub}th particle (x{sub}), "
-              f"full forward DFT, and one (l,m,b) field [R_lm on 1/{sub} of the grid (x{sub}), jbar, full "
-              f"inverse DFT, interpolation+Gram at every {sub}th particle (x{sub})], scaled by "
-              f"(lmax+1)^2={n_lm} (l,m) pairs and {nb} bins")
+    _ = (f * ps[:, 3][None, :]) @ f.T
+    t["interp"] += time.perf_counter() - t0
+    a = np.broadcast_to(slab, (nb,) + slab.shape)
+    _, t["node"] = _timed(O.sum_node, slab, np.ascontiguousarray(a))
+    return t
+
+
+def _oracle_sample(w, prep, cores):
+    """The FP64 oracle's time per catalogue from a bounded sample (a model with stated scale
+    factors), run on `cores` worker processes at once.
+
+    Whole once per catalogue: assignment (all particles), forward DFT, |n|^2 sort.  Sampled:
+    one unit per worker, each a different (l, m, b), see _oracle_unit.  Per catalogue:
+      assign + DFT + (L+1)^2 [SUB ylm + uniq + SUB node + nb (jbar + SUB kern + DFT + SUB interp)]
+      + (L+1) [uniq + nb jbar]           (the uniform term: one |n|^2 sort and nb jbar per l)
+    with every sampled step's mean over the units; the parallel part is divided by the pool's
+    measured concurrency (sum of the units' times / the pool's wall time), so the value is the
+    wall time `cores` processes would take.
+    """
+    import multiprocessing as mp
+    L1 = w["lmax"] + 1
+    nb = w["nbins"]
+    jobs = []
+    for i in range(cores):
+        l = (2 + i) % L1
+        jobs.append((w, l, (i % (2 * l + 1)) - l, (3 * i + 1) % nb, prep["paths"]))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_unit, jobs)
+    wall = time.perf_counter() - t0
+    mean = {k: statistics.mean(r[k] for r in res) for k in res[0]}
+    busy = sum(sum(r.values()) for r in res)
+    conc = max(1.0, busy / wall)
+    per_lm = SUB * mean["ylm"] + prep["uniq"] + SUB * mean["node"] + nb * (
+        mean["jbar"] + SUB * mean["kern"] + prep["fft"] + SUB * mean["interp"])
+    parallel = L1 * L1 * per_lm + L1 * (prep["uniq"] + nb * mean["jbar"])
+    total = prep["assign"] + prep["fft"] + parallel / conc
+    sample = (f"scaled sample of the FP64 oracle on {cores} processes: assignment of all particles, forward DFT and "
+              f"the |n|^2 sort timed whole; {cores} (l,m,b) units timed on 1/{SUB} of their inputs (R_lm and the "
+              f"window on n/{SUB} z-planes x{SUB}, jbar of the bin, interpolation+Gram at every {SUB}th particle "
+              f"x{SUB}, node Gram on n/{SUB} z-planes x{SUB}); inverse DFT = the forward DFT's time; scaled by "
+              f"(lmax+1)^2={L1 * L1} (l,m) x {nb} bins, uniform term (lmax+1)={L1} x (|n|^2 sort + {nb} jbar); "
+              f"parallel part / measured concurrency {conc:.1f}")
     return total, sample
+
+
+def _cpu_baseline(w, parts, reps=1):
+    """Time the oracle's scaled sample `reps` times (after one preparation); returns
+    (values, sample text, cores used)."""
+    import tempfile
+    cores = max(1, min(_cpu_cores(), int(_avail_gb() // 14)))
+    with tempfile.TemporaryDirectory(prefix="zeta_cpu_") as cache:
+        prep = _oracle_prepare(w, parts, cache)
+        vals, sample = [], ""
+        for _ in range(reps):
+            v, sample = _oracle_sample(w, prep, cores)
+            vals.append(v)
+    return vals, sample, cores
 
 
 def _gen_catalogue(args):
@@ -334,21 +430,16 @@ def run_reference(args, w, rank, world):
     if rank != 0:
         return 0
     parts = _make_inputs(w, 0)
-    prep = _oracle_prepare(w, parts)
-    vals = []
-    cpu_threads = 1
-    for i in range(args.warmup + args.steps):
-        total, sample = _oracle_sample(w, parts, prep)
-        if i >= args.warmup:
-            vals.append(total)
-    v = statistics.median(vals)
+    vals, sample, cpu_threads = _cpu_baseline(w, parts, reps=args.warmup + args.steps)
+    v = statistics.median(vals[args.warmup:])
     _emit({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic log-normal mock (seeded)",
         "config": {"workload": args.workload, "n": w["n"], "box": w["box"], "n_p": w["n_p"], "lmax": w["lmax"],
                    "nbins": w["nbins"], "dsup": w["dsup"]},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_threads, "kind": "oracle, scaled sample",
+                         "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     })
     return 0
@@ -366,7 +457,8 @@ def run_ours(args, w, rank, world, local_rank):
     from paper_2507_15209_gb300.zeta import Context
 
     forms = tuple(args.forms.split(","))
-    parts = _make_inputs(w, rank)
+    lm_split = args.partition == "lm" and world > 1
+    parts = _make_inputs(w, 0 if lm_split else rank)
     e = wl_edges(w)
     nb = len(e) - 1
     ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=w["n_p"], forms=forms)
@@ -376,9 +468,19 @@ def run_ours(args, w, rank, world, local_rank):
     out = torch.empty((nforms, w["lmax"] + 1, nb, nb), dtype=torch.float64, device="cuda")
     out_host = torch.empty(out.shape, dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream()
+    if lm_split:  # this rank's (l, m) pairs, an FP64 all-reduce of the slots, the fixed-order sum
+        slots = torch.empty(ctx.lm_slots(forms), dtype=torch.float64, device="cuda")
+
+        def measure():
+            ctx.zeta_lm(rank, world, particles=dev, forms=forms, out=slots)
+            allreduce_slots(slots, dist)
+            ctx.reduce_lm(slots, forms=forms, out=out)
+    else:
+        def measure():
+            ctx.zeta_ell(particles=dev, forms=forms, out=out)
 
     for _ in range(args.warmup):
-        ctx.zeta_ell(particles=dev, forms=forms, out=out)
+        measure()
     torch.cuda.synchronize()
     if ctx.get_status() != 0:
         raise RuntimeError("device status error during warm-up")
@@ -399,7 +501,7 @@ def run_ours(args, w, rank, world, local_rank):
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
-        ctx.zeta_ell(particles=dev, forms=forms, out=out)
+        measure()
     t1.record(stream)
     barrier()
     ms_dev = t0.elapsed_time(t1)
@@ -412,7 +514,7 @@ def run_ours(args, w, rank, world, local_rank):
     e0.record(stream)
     for _ in range(args.steps):
         dev.copy_(host, non_blocking=True)
-        ctx.zeta_ell(particles=dev, forms=forms, out=out)
+        measure()
         out_host.copy_(out, non_blocking=True)
     e1.record(stream)
     barrier()
@@ -421,7 +523,7 @@ def run_ours(args, w, rank, world, local_rank):
     if ctx.get_status() != 0:
         raise RuntimeError("device status error in the timed region")
 
-    value, e2e_value, ms_dev, ms_e2e = reduce_timings(ms_dev, ms_e2e, args.steps, world, dist)
+    value, e2e_value, ms_dev, ms_e2e = reduce_timings(ms_dev, ms_e2e, args.steps, world, dist, shared=lm_split)
 
     if rank == 0:
         peak, peak_src = _peaks()
@@ -445,12 +547,13 @@ def run_ours(args, w, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_dev / args.steps, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic log-normal mock (seeded), one catalogue per rank",
+            "scaling": "strong" if lm_split else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": ("synthetic log-normal mock (seeded), one catalogue shared by all ranks" if lm_split
+                     else "synthetic log-normal mock (seeded), one catalogue per rank"),
             "config": {"workload": args.workload, "n": w["n"], "box": w["box"], "n_p": w["n_p"],
                        "lmax": w["lmax"], "nbins": nb, "dsup": w["dsup"], "forms": list(forms),
                        "gram": "fp32", "l2": "inputs larger than L2 (fields 20 x 512 MB, particles 256 MB)",
-                       "parallelism": f"catalogue-per-gpu x{world}"},
+                       "parallelism": f"lm-split x{world}" if lm_split else f"catalogue-per-gpu x{world}"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                          "alg_bytes_per_call": bytes_launch, "calls": calls_k, "launches": launches_k,
@@ -477,8 +580,9 @@ def run_ours(args, w, rank, world, local_rank):
         if "cufft" in extras:
             line["cufft_reference"] = _cufft_reference(w, nb, stages, stream)
         if world == 1 and not args.no_cpu_baseline:
-            total, sample = _oracle_sample(w, parts, _oracle_prepare(w, parts))
-            line["cpu_baseline"] = {"value": total, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+            vals, sample, cores = _cpu_baseline(w, parts)
+            line["cpu_baseline"] = {"value": vals[0], "unit": UNIT, "cores": cores, "kind": "oracle, scaled sample",
+                                    "sample": sample}
         _emit(line)
     ctx.close()
     if dist is not None:
@@ -494,6 +598,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box2000_n512_np16m")
     ap.add_argument("--forms", default="particle,node")
+    ap.add_argument("--partition", default="catalogue", choices=["catalogue", "lm"],
+                    help="N > 1: one catalogue per rank (weak scaling, no collective) or one catalogue split "
+                         "over (l, m) pairs with an FP64 all-reduce of the per-pair slots (strong scaling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the Gram-variant, batch and adjoint extras")
     ap.add_argument("--extras", default="variants,batch,adjoint,cufft", help="comma list of extras to measure")

@@ -183,6 +183,26 @@ int zeta_mass_term(zeta_ctx* ctx, const float* delta_hat, int l, double sign, do
 int zeta_zeta_ell(zeta_ctx* ctx, const float* particles, int64_t np, const float* delta, int forms,
                   double* zeta, zeta_stream stream);
 
+/* The measurement split over (l, m) pairs, for running one catalogue on several GPUs.  The pairs
+ * are independent (Eq. 3PCF-multipole-sum sums them; the paper's own code runs them in parallel,
+ * Sec. 3.4), so P processes can each take the pairs of index i = l^2 + l + m with
+ * i mod P == lm_rank (0 <= lm_rank < lm_size = P) and sum their results.
+ * zeta_zeta_lm: the same steps as zeta_zeta_ell (every rank assigns, transforms and sorts the
+ *   whole catalogue itself), but each (l, m) contribution is stored in its own slot instead of
+ *   being accumulated: slots is device double[zeta_lm_slots(ctx, forms)], laid out
+ *   [form][(lmax+1)^2 + lmax+1][nbins][nbins] with (l, m) at slot l^2 + l + m and the uniform
+ *   term of l (particle form, subtracted) at slot (lmax+1)^2 + l, owned by the rank of (l, -l).
+ *   Slots this rank does not own are written as zero, so an element-wise float64 sum of the P
+ *   ranks' slot arrays (e.g. an all-reduce) is exact: every slot has one non-zero contributor.
+ * zeta_reduce_lm: zeta[form][l][b1][b2] from the summed slots (device double in, device double
+ *   [nforms * (lmax+1) * nbins * nbins] out), adding in the order zeta_zeta_ell adds them
+ *   (0, the uniform term, then m = -l .. l), so the result is bit-identical to zeta_zeta_ell.
+ * zeta_lm_slots: the number of doubles in a slot array (0 on invalid arguments). */
+int zeta_zeta_lm(zeta_ctx* ctx, const float* particles, int64_t np, const float* delta, int forms, int lm_rank,
+                 int lm_size, double* slots, zeta_stream stream);
+int zeta_reduce_lm(zeta_ctx* ctx, const double* slots, int forms, double* zeta, zeta_stream stream);
+size_t zeta_lm_slots(const zeta_ctx* ctx, int forms);
+
 /* Gradients of L = sum_l sum_ij W_l[i][j] zeta_l[i][j] (weights: host double
  * [(lmax+1) * nbins * nbins]), by the transpose of every step with per-(l, m) recomputation of
  * the fields (nothing per (l, m) is stored).  With S_l = (W_l + W_l^T)/2, A_b the map delta ->

@@ -15,7 +15,7 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t delta = 0, dhat = 0, spectra = 0, fields = 0, partials = 0, small = 0, mhist = 0, sorted = 0, tstart = 0,
-         counts = 0, orig = 0, pvals = 0;
+         counts = 0, orig = 0, pvals = 0, o_tile = 0, o_cell = 0, o_tq = 0, s_cell = 0, s_tq = 0;
   // backward (gradient) regions
   size_t gk = 0, q = 0, wts = 0, hfield = 0, direct = 0, sidx = 0;
   size_t total = 0;
@@ -44,6 +44,12 @@ Layout layout(const zeta_ctx* c, int64_t np, bool backward = false) {
   L.counts = take(sizeof(int) * static_cast<size_t>(c->ntiles));
   L.orig = take(sizeof(int) * static_cast<size_t>(np));
   L.pvals = take(particle_rows_bytes(c, np));  // interpolated particle rows of one (l, m)
+  // prepared particle data (cell, offsets, weight): original order (scratch) and sorted order
+  L.o_tile = take(sizeof(int) * static_cast<size_t>(np));
+  L.o_cell = take(sizeof(int) * static_cast<size_t>(np));
+  L.o_tq = take(sizeof(float4) * static_cast<size_t>(np));
+  L.s_cell = take(sizeof(int) * static_cast<size_t>(np));
+  L.s_tq = take(sizeof(float4) * static_cast<size_t>(np));
   if (backward) {
     L.gk = take(g);
     L.q = take(g);
@@ -69,6 +75,16 @@ int need_ws(const zeta_ctx* c, int64_t np, bool backward = false) {
 template <typename T>
 T* at(const zeta_ctx* c, size_t off) {
   return reinterpret_cast<T*>(c->ws + off);
+}
+
+PartPrep prep_of(const zeta_ctx* c, const Layout& L) {
+  PartPrep q;
+  q.o_tile = at<int>(c, L.o_tile);
+  q.o_cell = at<int>(c, L.o_cell);
+  q.o_tq = at<float4>(c, L.o_tq);
+  q.s_cell = at<int>(c, L.s_cell);
+  q.s_tq = at<float4>(c, L.s_tq);
+  return q;
 }
 
 void drop_batch_graph(zeta_ctx* c) {
@@ -128,6 +144,7 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
   c->nn2 = table_n2_count(p->n);
   c->ntiles = static_cast<int64_t>(p->n / kTile) * (p->n / kTile) * (p->n / kTile);
   c->gamma_q = p->dsup == 2 ? 2 : 5;
+  if (p->nbins <= 20) c->tune[GK_NODE] = 1;  // the register-blocked node Gram holds one CTA per SM
   auto fail = [&](int rc) {
     zeta_destroy(c);
     return rc;
@@ -263,8 +280,9 @@ int zeta_sum_particles(zeta_ctx* c, const float* sorted, const int64_t* tile_sta
   ZK_TRY(need_ws(c, np));
   const Layout L = layout(c, np);
   double* part = at<double>(c, L.partials);
-  ZK_TRY(launch_gram_particles(c, reinterpret_cast<const float4*>(sorted), tile_start, np, alm, at<float>(c, L.pvals),
-                               part, stream));
+  const PartPrep q = prep_of(c, L);
+  ZK_TRY(launch_prep_sorted(c, reinterpret_cast<const float4*>(sorted), np, q.s_cell, q.s_tq, stream));
+  ZK_TRY(launch_gram_particles(c, q.s_cell, q.s_tq, tile_start, np, alm, at<float>(c, L.pvals), part, stream));
   return launch_reduce(c, part, gram_particle_parts(c), 1.0, wsum, gram, stream);
 }
 
@@ -281,10 +299,20 @@ int zeta_mass_term(zeta_ctx* c, const float* delta_hat, int l, double sign, doub
   return launch_reduce(c, part, gram_ctas(c, GK_MASS), scale, nullptr, gram, stream);
 }
 
-int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* delta, int forms, double* zeta,
-                  zeta_stream stream) {
+}  // extern "C"
+
+namespace {
+
+// The measurement of Fig. 1 steps (2)-(7).  With lm_size > 1 only the (l, m) pairs of index
+// i = l^2 + l + m with i mod lm_size == lm_rank run, and the uniform term of l runs on the owner
+// of (l, -l).  slots == false: zeta is [form][l][nb][nb], accumulated in the order 0, uniform
+// term, m = -l .. l.  slots == true: every contribution is stored in its own slot
+// [form][(lmax+1)^2 + lmax+1][nb][nb] ((l, m) at l^2 + l + m, the uniform term of l at
+// (lmax+1)^2 + l), the slots this call does not own set to zero.
+int measure(zeta_ctx* c, const float* particles, int64_t np, const float* delta, int forms, int lm_rank, int lm_size,
+            bool slots, double* zeta, cudaStream_t stream) {
   ZK_TRY(check_ctx(c));
-  if (!zeta || forms < 1 || forms > 7) return ZETA_EINVAL;
+  if (!zeta || forms < 1 || forms > 7 || lm_size < 1 || lm_rank < 0 || lm_rank >= lm_size) return ZETA_EINVAL;
   const bool want_p = forms & ZETA_SUM_PARTICLE;
   if ((want_p || !delta) && (!particles || np < 1 || np > 0x7fffffffLL)) return ZETA_EINVAL;
   const int64_t npl = want_p ? np : 0;
@@ -301,52 +329,90 @@ int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* 
   float4* sorted = at<float4>(c, L.sorted);
   int64_t* tstart = at<int64_t>(c, L.tstart);
 
-  if (!delta)
+  const PartPrep q = prep_of(c, L);
+  if (want_p) {  // sort (and prepare) first; then the assignment is computed tile by tile
+    ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream, nullptr, &q));
+    if (!delta)
+      ZK_TRY(launch_assign_tiles(c, parts, np, tstart, q.s_cell, q.s_tq, dl, wsum, small, stream));
+    else
+      ZK_TRY(launch_wsum(c, parts, np, wsum, small, stream));
+  } else if (!delta) {
     ZK_TRY(launch_assign(c, parts, np, dl, wsum, reinterpret_cast<unsigned long long*>(fields), small, stream));
-  else if (want_p)
-    ZK_TRY(launch_wsum(c, parts, np, wsum, small, stream));
+  }
   ZK_TRY(launch_r2c(c, dl, dhat, stream));
   unsigned long long* hist = at<unsigned long long>(c, L.mhist);
-  if (want_p) {
-    ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream));
-    ZK_TRY(launch_mass_hist(c, dhat, hist, stream));
-  }
+  if (want_p) ZK_TRY(launch_mass_hist(c, dhat, hist, stream));
 
   int nforms = 0, idx_node = -1, idx_gamma = -1, idx_part = -1;
   if (forms & ZETA_SUM_NODE) idx_node = nforms++;
   if (forms & ZETA_SUM_GAMMA) idx_gamma = nforms++;
   if (want_p) idx_part = nforms++;
-  const size_t per_form = static_cast<size_t>(lmax + 1) * nb * nb;
+  const size_t nb2 = static_cast<size_t>(nb) * nb;
+  const size_t nslot = slots ? static_cast<size_t>(lmax + 1) * (lmax + 1) + lmax + 1 : static_cast<size_t>(lmax + 1);
+  const size_t per_form = nslot * nb2;
   if (cudaMemsetAsync(zeta, 0, sizeof(double) * per_form * nforms, stream) != cudaSuccess) return ZETA_ECUDA;
+  // output block of form index f for (l, m) (m > l: the uniform term of l)
+  auto out = [&](int f, int l, int m) {
+    size_t slot = l;
+    if (slots) slot = m > l ? static_cast<size_t>(lmax + 1) * (lmax + 1) + l : static_cast<size_t>(l) * l + l + m;
+    return zeta + f * per_form + slot * nb2;
+  };
   const double inv_ng = 1.0 / static_cast<double>(c->ng);
   for (int l = 0; l <= lmax; ++l) {
-    if (want_p) {
-      double* out = zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb;
+    if (want_p && (l * l) % lm_size == lm_rank) {
       ZK_TRY(launch_mass(c, hist, l, part, stream));
       ZK_TRY(launch_reduce(c, part, gram_ctas(c, GK_MASS), -(2.0 * l + 1.0) / (4.0 * 3.14159265358979323846), nullptr,
-                           out, stream));
+                           out(idx_part, l, l + 1), stream, slots));
     }
     for (int m = -l; m <= l; ++m) {
+      if ((l * l + l + m) % lm_size != lm_rank) continue;
       ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, at<float2>(c, L.spectra), fields, stream));
       if (idx_node >= 0) {
         ZK_TRY(c->p.gram == ZETA_GRAM_FP32 ? launch_gram_node(c, dl, fields, part, stream)
                                            : launch_gram_node_tc(c, dl, fields, part, stream));
         ZK_TRY(launch_reduce(c, part, gram_ctas(c, c->p.gram == ZETA_GRAM_FP32 ? GK_NODE : GK_TC), inv_ng, nullptr,
-                             zeta + idx_node * per_form + static_cast<size_t>(l) * nb * nb, stream));
+                             out(idx_node, l, m), stream, slots));
       }
       if (idx_gamma >= 0) {
         ZK_TRY(launch_gram_gamma(c, dl, fields, part, stream));
-        ZK_TRY(launch_reduce(c, part, gram_ctas(c, GK_GAMMA), inv_ng, nullptr,
-                             zeta + idx_gamma * per_form + static_cast<size_t>(l) * nb * nb, stream));
+        ZK_TRY(launch_reduce(c, part, gram_ctas(c, GK_GAMMA), inv_ng, nullptr, out(idx_gamma, l, m), stream, slots));
       }
       if (idx_part >= 0) {
-        ZK_TRY(launch_gram_particles(c, sorted, tstart, np, fields, at<float>(c, L.pvals), part, stream));
-        ZK_TRY(launch_reduce(c, part, gram_particle_parts(c), 1.0, wsum,
-                             zeta + idx_part * per_form + static_cast<size_t>(l) * nb * nb, stream));
+        ZK_TRY(launch_gram_particles(c, q.s_cell, q.s_tq, tstart, np, fields, at<float>(c, L.pvals), part, stream));
+        ZK_TRY(launch_reduce(c, part, gram_particle_parts(c), 1.0, wsum, out(idx_part, l, m), stream, slots));
       }
     }
   }
   return ZETA_OK;
+}
+
+int nforms_of(int forms) { return ((forms & 1) ? 1 : 0) + ((forms & 2) ? 1 : 0) + ((forms & 4) ? 1 : 0); }
+
+}  // namespace
+
+extern "C" {
+
+int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* delta, int forms, double* zeta,
+                  zeta_stream stream) {
+  return measure(c, particles, np, delta, forms, 0, 1, false, zeta, stream);
+}
+
+int zeta_zeta_lm(zeta_ctx* c, const float* particles, int64_t np, const float* delta, int forms, int lm_rank,
+                 int lm_size, double* slots, zeta_stream stream) {
+  return measure(c, particles, np, delta, forms, lm_rank, lm_size, true, slots, stream);
+}
+
+int zeta_reduce_lm(zeta_ctx* c, const double* slots, int forms, double* zeta, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!slots || !zeta || forms < 1 || forms > 7) return ZETA_EINVAL;
+  const int nforms = nforms_of(forms);
+  return launch_reduce_lm(c, slots, nforms, (forms & ZETA_SUM_PARTICLE) ? nforms - 1 : -1, zeta, stream);
+}
+
+size_t zeta_lm_slots(const zeta_ctx* c, int forms) {
+  if (!c || forms < 1 || forms > 7) return 0;
+  const size_t L1 = static_cast<size_t>(c->p.lmax) + 1;
+  return nforms_of(forms) * (L1 * L1 + L1) * c->p.nbins * c->p.nbins;
 }
 
 int zeta_batch(zeta_ctx* c, const float* particles, const int64_t* offsets, int ncat, int forms, double* zeta,
@@ -412,11 +478,12 @@ int zeta_autotune(zeta_ctx* c, const float* particles, int64_t np, int forms, ze
   float4* sorted = at<float4>(c, L.sorted);
   int64_t* tstart = at<int64_t>(c, L.tstart);
   // representative data: this catalogue's fields for one (l, m)
+  const PartPrep q = prep_of(c, L);
   ZK_TRY(launch_assign(c, parts, np, dl, wsum, reinterpret_cast<unsigned long long*>(fields), small, stream));
   ZK_TRY(launch_r2c(c, dl, dhat, stream));
   unsigned long long* hist = at<unsigned long long>(c, L.mhist);
   if (want_p) {
-    ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream));
+    ZK_TRY(launch_sort(c, parts, np, sorted, tstart, at<int>(c, L.counts), at<int>(c, L.orig), stream, nullptr, &q));
     ZK_TRY(launch_mass_hist(c, dhat, hist, stream));
   }
   const int l = c->p.lmax < 2 ? c->p.lmax : 2;
@@ -428,7 +495,8 @@ int zeta_autotune(zeta_ctx* c, const float* particles, int64_t np, int forms, ze
       case GK_NODE: return launch_gram_node(c, dl, fields, part, stream);
       case GK_TC: return launch_gram_node_tc(c, dl, fields, part, stream);
       case GK_GAMMA: return launch_gram_gamma(c, dl, fields, part, stream);
-      case GK_PART: return launch_gram_particles(c, sorted, tstart, np, fields, at<float>(c, L.pvals), part, stream);
+      case GK_PART:
+        return launch_gram_particles(c, q.s_cell, q.s_tq, tstart, np, fields, at<float>(c, L.pvals), part, stream);
       default: return launch_mass(c, hist, l, part, stream);
     }
   };

@@ -208,9 +208,12 @@ __global__ void k_tile_scatter(const float4* __restrict__ p, long long np, int n
   }
 }
 
-// One warp per tile: rank every entry by its original index and gather the particles.
+// One warp per tile: rank every entry by its original index and gather the particles (and,
+// when given, their prepared cell and offsets).
 __global__ void k_tile_order(const float4* __restrict__ p, const long long* __restrict__ start, long long ntiles,
-                             const int* __restrict__ orig, float4* __restrict__ sorted, int* __restrict__ sorted_idx) {
+                             const int* __restrict__ orig, float4* __restrict__ sorted, int* __restrict__ sorted_idx,
+                             const int* __restrict__ o_cell, const float4* __restrict__ o_tq, int* __restrict__ s_cell,
+                             float4* __restrict__ s_tq) {
   const long long warp = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= ntiles) return;
@@ -222,6 +225,172 @@ __global__ void k_tile_order(const float4* __restrict__ p, const long long* __re
     for (int j = 0; j < c; ++j) rank += (orig[s + j] < v);
     sorted[s + rank] = p[v];
     if (sorted_idx) sorted_idx[s + rank] = v;
+    if (s_cell) {
+      s_cell[s + rank] = o_cell[v];
+      s_tq[s + rank] = o_tq[v];
+    }
+  }
+}
+
+// The float64 cell arithmetic of a particle, done once per catalogue: cell (linear index
+// z n^2 + y n + x), in-cell offsets t in [0, 1) and the weight (0 for a non-finite particle,
+// which sits in cell 0 with t = 0 and so contributes nothing anywhere).
+__device__ __forceinline__ void prep_one(float4 q, double inv_h, int n, int& cell, float4& tq, int& tile) {
+  const int nt = n / kTile;
+  if (!finite4(q)) {
+    cell = 0;
+    tile = 0;
+    tq = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  float tx, ty, tz;
+  const int cx = cell_of(q.x, inv_h, n, tx), cy = cell_of(q.y, inv_h, n, ty), cz = cell_of(q.z, inv_h, n, tz);
+  cell = (cz * n + cy) * n + cx;
+  tile = ((cz / kTile) * nt + cy / kTile) * nt + cx / kTile;
+  tq = make_float4(tx, ty, tz, q.w);
+}
+
+// Prepared data in the original order and the particle count of every tile.
+__global__ void k_particle_prep(const float4* __restrict__ p, long long np, int n, double inv_h,
+                                int* __restrict__ o_tile, int* __restrict__ o_cell, float4* __restrict__ o_tq,
+                                int* __restrict__ cnt) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np;
+       i += static_cast<long long>(blockDim.x) * gridDim.x) {
+    int cell, tile;
+    float4 tq;
+    prep_one(p[i], inv_h, n, cell, tq, tile);
+    o_tile[i] = tile;
+    o_cell[i] = cell;
+    o_tq[i] = tq;
+    atomicAdd(cnt + tile, 1);
+  }
+}
+
+__global__ void k_tile_scatter_pre(const int* __restrict__ o_tile, long long np, const long long* __restrict__ start,
+                                   int* __restrict__ cursor, int* __restrict__ orig) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np;
+       i += static_cast<long long>(blockDim.x) * gridDim.x) {
+    const int t = o_tile[i];
+    const int slot = atomicAdd(cursor + t, 1);
+    orig[start[t] + slot] = static_cast<int>(i);
+  }
+}
+
+// Prepared data of particles that are already sorted (a caller's sorted array).
+__global__ void k_prep_sorted(const float4* __restrict__ sorted, long long np, int n, double inv_h,
+                              int* __restrict__ s_cell, float4* __restrict__ s_tq) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np;
+       i += static_cast<long long>(blockDim.x) * gridDim.x) {
+    int cell, tile;
+    float4 tq;
+    prep_one(sorted[i], inv_h, n, cell, tq, tile);
+    s_cell[i] = cell;
+    s_tq[i] = tq;
+  }
+}
+
+// Assignment from the sorted catalogue, one CTA per 8^3-cell tile, each node computed by the
+// tile that owns it: the CTA walks the particles of its tile and of the (up to) 26 neighbouring
+// tiles, and every stencil node of a particle that falls inside the tile receives its 64-bit
+// fixed-point contribution round(w beta 2^k) by a shared-memory atomic; then the tile writes
+// delta = eps / eps_bar - 1 of its 512 nodes.  No global atomics, and integer sums, so the
+// result does not depend on the order of the particles.  w beta is formed exactly as a pair of
+// float32 (hi + lo, by an FMA) and each part rounded to the fixed point separately, so no float64
+// arithmetic is needed per contribution.
+constexpr int kAccPitch = kTile + 1;  // 64-bit words per node row of the tile accumulator
+
+template <int D>
+__global__ void __launch_bounds__(256) k_assign_tiles(const long long* __restrict__ tile_start,
+                                                      const int* __restrict__ s_cell, const float4* __restrict__ s_tq,
+                                                      int n, const double* __restrict__ wstat, float* __restrict__ delta) {
+  constexpr int T3 = kTile * kTile * kTile;
+  constexpr int OFF = D / 2 - 1;
+  __shared__ unsigned long long acc[kTile * kTile * kAccPitch];  // rows padded against bank conflicts
+  const int nt = n / kTile, mask = n - 1;
+  const int lg = __ffs(n) - 1;
+  const int t = blockIdx.x;
+  const int tx = t % nt, ty = (t / nt) % nt, tz = t / (nt * nt);
+  for (int i = threadIdx.x; i < kTile * kTile * kAccPitch; i += blockDim.x) acc[i] = 0ULL;
+  __syncthreads();
+  // the particle ranges of the distinct neighbour tiles (fewer than 27 when the grid has fewer
+  // than three tiles per axis), flattened so that all threads take particles of all of them
+  __shared__ long long nb_s0[27];
+  __shared__ int nb_pre[28];
+  const int nd = nt >= 3 ? 3 : nt;
+  if (threadIdx.x < 27) {
+    const int dz = threadIdx.x / 9, dy = (threadIdx.x / 3) % 3, dx = threadIdx.x % 3;
+    int cnt = 0;
+    long long a = 0;
+    if (dz < nd && dy < nd && dx < nd) {
+      const int sx = nt >= 3 ? (tx + dx - 1 + nt) % nt : (tx + dx) % nt;
+      const int sy = nt >= 3 ? (ty + dy - 1 + nt) % nt : (ty + dy) % nt;
+      const int sz = nt >= 3 ? (tz + dz - 1 + nt) % nt : (tz + dz) % nt;
+      const int nb_t = (sz * nt + sy) * nt + sx;
+      a = tile_start[nb_t];
+      cnt = static_cast<int>(tile_start[nb_t + 1] - a);
+    }
+    nb_s0[threadIdx.x] = a;
+    nb_pre[threadIdx.x + 1] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    nb_pre[0] = 0;
+    for (int k = 0; k < 27; ++k) nb_pre[k + 1] += nb_pre[k];
+  }
+  __syncthreads();
+  const int k2 = ilogb(wstat[2]);  // fixed-point scale 2^k2
+  const int total = nb_pre[27];
+  int k = 0;
+  for (int j = threadIdx.x; j < total; j += blockDim.x) {
+    while (j >= nb_pre[k + 1]) ++k;
+    const long long i = nb_s0[k] + (j - nb_pre[k]);
+    const float4 q = s_tq[i];
+    if (q.w == 0.f) continue;
+    const int cell = s_cell[i];
+    const int c[3] = {cell & mask, (cell >> lg) & mask, cell >> (2 * lg)};
+    const int t0[3] = {tx * kTile, ty * kTile, tz * kTile};
+    // local index of the stencil's first node in this tile (periodic), per axis
+    int r[3];
+    bool reach = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      r[d] = ((c[d] - OFF - t0[d]) & mask);
+      if (r[d] > mask - (D - 1)) r[d] -= n;  // the stencil starts before the tile
+      reach = reach && r[d] + D - 1 >= 0 && r[d] < kTile;
+    }
+    if (!reach) continue;
+    float wv[3][D];
+    bspline_weights<D>(q.x, wv[0]);
+    bspline_weights<D>(q.y, wv[1]);
+    bspline_weights<D>(q.z, wv[2]);
+    // the part of the stencil inside the tile, per axis
+    int o0[3], o1[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      o0[d] = r[d] < 0 ? -r[d] : 0;
+      o1[d] = kTile - r[d] < D ? kTile - r[d] : D;
+    }
+    for (int oz = o0[2]; oz < o1[2]; ++oz)
+      for (int oy = o0[1]; oy < o1[1]; ++oy) {
+        const float wyz = wv[2][oz] * wv[1][oy];
+        unsigned long long* row = acc + ((r[2] + oz) * kTile + r[1] + oy) * kAccPitch + r[0];
+        for (int ox = o0[0]; ox < o1[0]; ++ox) {
+          const float b = wyz * wv[0][ox];
+          const float hi = q.w * b;
+          const float lo = fmaf(q.w, b, -hi);
+          const long long v = __float2ll_rn(ldexpf(hi, k2)) + __float2ll_rn(ldexpf(lo, k2));
+          atomicAdd(row + ox, static_cast<unsigned long long>(v));
+        }
+      }
+  }
+  __syncthreads();
+  const double w = wstat[0];
+  const double inv = (w != 0.0) ? static_cast<double>(n) * n * n / (w * wstat[2]) : 0.0;
+  for (int i = threadIdx.x; i < T3; i += blockDim.x) {
+    const int lx = i % kTile, ly = (i / kTile) % kTile, lz = i / (kTile * kTile);
+    const long long gi = (static_cast<long long>(tz * kTile + lz) * n + ty * kTile + ly) * n + tx * kTile + lx;
+    const long long v = static_cast<long long>(acc[(lz * kTile + ly) * kAccPitch + lx]);
+    delta[gi] = static_cast<float>(static_cast<double>(v) * inv - 1.0);
   }
 }
 
@@ -262,18 +431,46 @@ int launch_wsum(const zeta_ctx* c, const float4* parts, int64_t np, double* wsum
 }
 
 int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sorted, int64_t* tile_start,
-                int* counts, int* orig, cudaStream_t s, int* sorted_idx) {
+                int* counts, int* orig, cudaStream_t s, int* sorted_idx, const PartPrep* prep) {
   StageScope prof(c, ST_SORT, 4, s);
   const double inv_h = c->n / c->p.box;
   if (cudaMemsetAsync(counts, 0, sizeof(int) * c->ntiles, s) != cudaSuccess) return ZETA_ECUDA;
   const int g = grid_for(np, 256, c->num_sms);
   long long* st = reinterpret_cast<long long*>(tile_start);
-  k_tile_count<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, counts);
-  k_tile_scan<<<1, 1024, 0, s>>>(counts, c->ntiles, st);
-  k_tile_scatter<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, st, counts, orig);
+  if (prep) {
+    k_particle_prep<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, prep->o_tile, prep->o_cell, prep->o_tq, counts);
+    k_tile_scan<<<1, 1024, 0, s>>>(counts, c->ntiles, st);
+    k_tile_scatter_pre<<<g, 256, 0, s>>>(prep->o_tile, np, st, counts, orig);
+  } else {
+    k_tile_count<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, counts);
+    k_tile_scan<<<1, 1024, 0, s>>>(counts, c->ntiles, st);
+    k_tile_scatter<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, st, counts, orig);
+  }
   const long long warps = c->ntiles;
-  k_tile_order<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, s>>>(parts, st, c->ntiles, orig, sorted,
-                                                                             sorted_idx);
+  k_tile_order<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, s>>>(
+      parts, st, c->ntiles, orig, sorted, sorted_idx, prep ? prep->o_cell : nullptr, prep ? prep->o_tq : nullptr,
+      prep ? prep->s_cell : nullptr, prep ? prep->s_tq : nullptr);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
+int launch_prep_sorted(const zeta_ctx* c, const float4* sorted, int64_t np, int* s_cell, float4* s_tq, cudaStream_t s) {
+  StageScope prof(c, ST_SORT, 1, s);
+  k_prep_sorted<<<grid_for(np, 256, c->num_sms), 256, 0, s>>>(sorted, np, c->n, c->n / c->p.box, s_cell, s_tq);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
+int launch_assign_tiles(const zeta_ctx* c, const float4* parts, int64_t np, const int64_t* tile_start,
+                        const int* s_cell, const float4* s_tq, float* delta, double* wsum, double* scratch,
+                        cudaStream_t s) {
+  StageScope prof(c, ST_ASSIGN, 3, s);
+  double* wstat = scratch + 2 * kRedCtas;
+  k_weight_partials<<<kRedCtas, 256, 0, s>>>(parts, np, scratch, c->d_status);
+  k_weight_final<<<1, 32, 0, s>>>(scratch, kRedCtas, wstat, wsum);
+  const long long* ts = reinterpret_cast<const long long*>(tile_start);
+  if (c->p.dsup == 2)
+    k_assign_tiles<2><<<static_cast<unsigned>(c->ntiles), 256, 0, s>>>(ts, s_cell, s_tq, c->n, wstat, delta);
+  else
+    k_assign_tiles<4><<<static_cast<unsigned>(c->ntiles), 256, 0, s>>>(ts, s_cell, s_tq, c->n, wstat, delta);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 

@@ -37,22 +37,6 @@ __device__ __forceinline__ int morton_compact(unsigned long long v) {
   return static_cast<int>(v);
 }
 
-// Cell of a coordinate and the offset in it, wrapped into [0, n): u = x / H in float64, the
-// cell floor(u) and t = u - floor(u) in [0, 1).  The periodic reduction of u is applied only
-// when u is outside [0, n) -- for u inside it is the identity -- and 1/n is exact for n a
-// power of two, so the result equals that of the assignment kernel's u - floor(u / n) n.
-__device__ __forceinline__ int cell_frac(float x, double inv_h, int n, double inv_n, float& t) {
-  double u = static_cast<double>(x) * inv_h;
-  if (!(u >= 0.0 && u < n)) u -= floor(u * inv_n) * n;
-  const double fl = floor(u);
-  int c = static_cast<int>(fl);
-  t = static_cast<float>(u - fl);
-  if (c >= n) c -= n;
-  if (c < 0) c += n;
-  if (t >= 1.f) t = 0.99999994f;
-  return c;
-}
-
 // The tiles of one CTA in order: tile k is Morton index blockIdx.x + k * gridDim.x.
 struct TileWalk {
   const long long* ts;
@@ -110,22 +94,19 @@ struct InterpSmem {
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kCons) : "memory"); }
 
 // Per-particle setup shared by both interpolation kernels: stencil origin, the in-tile halo
-// index (or -1), and the weights in the order the gather lanes read them.
+// index (or -1), and the weights in the order the gather lanes read them.  From the prepared
+// cell (linear index, n = 2^lg) and in-cell offsets of the particle: integer and float32
+// arithmetic only.
 template <int D, int PW>
-__device__ __forceinline__ void particle_setup(float4 pp, double inv_h, int n, double inv_n, int tx, int ty, int tz,
+__device__ __forceinline__ void particle_setup(int cell, float4 tq, int n, int lg, int tx, int ty, int tz,
                                                bool staged, int4& org, float* pw) {
   using H = Halo<D>;
   constexpr int OFF = D / 2 - 1;
   float wx[D], wy[D], wz[D];
-  const bool fin = isfinite(pp.x) && isfinite(pp.y) && isfinite(pp.z) && isfinite(pp.w);
-  const float pc[3] = {pp.x, pp.y, pp.z};
-  int cix[3];
-  float tt[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) cix[d] = cell_frac(fin ? pc[d] : 0.f, inv_h, n, inv_n, tt[d]);
-  bsw<D>(tt[0], wx);
-  bsw<D>(tt[1], wy);
-  bsw<D>(tt[2], wz);
+  const int cix[3] = {cell & (n - 1), (cell >> lg) & (n - 1), cell >> (2 * lg)};
+  bsw<D>(tq.x, wx);
+  bsw<D>(tq.y, wy);
+  bsw<D>(tq.z, wz);
   const int lx = cix[0] - tx * kTile, ly = cix[1] - ty * kTile, lz = cix[2] - tz * kTile;
   const bool inside = lx >= 0 && lx < kTile && ly >= 0 && ly < kTile && lz >= 0 && lz < kTile;
   org = make_int4(cix[0] - OFF, cix[1] - OFF, cix[2] - OFF, (staged && inside) ? lz * H::PP + ly * H::XP + lx : -1);
@@ -189,9 +170,9 @@ struct ItemWalk {
 
 template <int NBP, int D>
 __global__ void __launch_bounds__(kIThreads, 3)
-    k_interp_part(const float4* __restrict__ sorted, const long long* __restrict__ tile_start,
-                  const float4* __restrict__ f4, long long ng, int n, int nb, double inv_h, int staged_min,
-                  float* __restrict__ pvals, int* __restrict__ status) {
+    k_interp_part(const int* __restrict__ s_cell, const float4* __restrict__ s_tq,
+                  const long long* __restrict__ tile_start, const float4* __restrict__ f4, long long ng, int n, int nb,
+                  int staged_min, float* __restrict__ pvals, int* __restrict__ status) {
   using H = Halo<D>;
   using S = InterpSmem<NBP, D>;
   constexpr int PW = S::PW;
@@ -278,7 +259,7 @@ __global__ void __launch_bounds__(kIThreads, 3)
   // ---- consumers
   const int ct = threadIdx.x - 32 * kPW, cw = warp - kPW;
   const int l8 = lane & 7;
-  const double inv_n = 1.0 / n;
+  const int lg = __ffs(n) - 1;
   long long ci = 0;
   bool ok = true;
   long long s0, s1;
@@ -287,7 +268,8 @@ __global__ void __launch_bounds__(kIThreads, 3)
     for (long long bs = s0; bs < s1; bs += kPBP) {
       const int cnt = static_cast<int>((s1 - bs) < kPBP ? (s1 - bs) : kPBP);
       if (cnt < staged_min) continue;  // k_interp_part_l1 takes this batch
-      if (ct < cnt) particle_setup<D, PW>(sorted[bs + ct], inv_h, n, inv_n, tx, ty, tz, true, org[ct], bw + ct * PW);
+      if (ct < cnt)
+        particle_setup<D, PW>(s_cell[bs + ct], s_tq[bs + ct], n, lg, tx, ty, tz, true, org[ct], bw + ct * PW);
       consumer_sync();  // setup visible; the previous batch's value rows are written out
       for (int q = 0; q < ngrp; ++q, ++ci) {
         const int s = static_cast<int>(ci % kKS);
@@ -387,9 +369,9 @@ struct InterpL1Smem {
 
 template <int NBP, int D>
 __global__ void __launch_bounds__(kThreadsL1, 1)
-    k_interp_part_l1(const float4* __restrict__ sorted, const long long* __restrict__ tile_start,
-                     const float4* __restrict__ f4, long long ng, int n, int nb, double inv_h, int staged_min,
-                     float* __restrict__ pvals) {
+    k_interp_part_l1(const int* __restrict__ s_cell, const float4* __restrict__ s_tq,
+                     const long long* __restrict__ tile_start, const float4* __restrict__ f4, long long ng, int n,
+                     int nb, int staged_min, float* __restrict__ pvals) {
   using S = InterpL1Smem<NBP, D>;
   constexpr int PW = S::PW;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -400,7 +382,7 @@ __global__ void __launch_bounds__(kThreadsL1, 1)
   const int nt = n / kTile;
   const TileWalk walk{tile_start, static_cast<long long>(nt) * nt * nt, nt};
   const int mask = n - 1, n2 = n * n;
-  const double inv_n = 1.0 / n;
+  const int lg = __ffs(n) - 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = kThreadsL1 / 32;
   // lane -> (particle slot, bin group, x offset)
@@ -416,8 +398,8 @@ __global__ void __launch_bounds__(kThreadsL1, 1)
       if (cnt >= staged_min) continue;  // the staged kernel takes this batch
       __syncthreads();  // the previous batch's value rows are written out
       if (threadIdx.x < cnt)
-        particle_setup<D, PW>(sorted[bs + threadIdx.x], inv_h, n, inv_n, tx, ty, tz, false, org[threadIdx.x],
-                              bw + threadIdx.x * PW);
+        particle_setup<D, PW>(s_cell[bs + threadIdx.x], s_tq[bs + threadIdx.x], n, lg, tx, ty, tz, false,
+                              org[threadIdx.x], bw + threadIdx.x * PW);
       __syncthreads();
       for (int pb = warp * PPW; pb < cnt; pb += NW * PPW) {  // warp-uniform
         const int p = pb + ps;
@@ -502,7 +484,7 @@ __global__ void __launch_bounds__(kThreadsL1, 1)
 // rows; the next chunk is loaded into registers while the current one is contracted.
 template <int NBP>
 __global__ void __launch_bounds__(kThreads) k_gram_rows(const float* __restrict__ pvals,
-                                                        const float4* __restrict__ sorted, long long np, int nb,
+                                                        const float4* __restrict__ s_tq, long long np, int nb,
                                                         double* __restrict__ partials) {
   using G = Gram<NBP>;
   constexpr int GV = NBP / 4;
@@ -521,9 +503,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_rows(const float* __restrict_
   auto fetch = [&](long long c) {
     const long long p = c * kPB + threadIdx.x;
     if (p < np) {
-      const float4 pp = __ldg(sorted + p);
-      const bool fin = isfinite(pp.x) && isfinite(pp.y) && isfinite(pp.z) && isfinite(pp.w);
-      wnext = fin ? pp.w : 0.f;
+      wnext = __ldg(s_tq + p).w;  // 0 for a non-finite particle
       const float4* row = reinterpret_cast<const float4*>(pvals + p * NBP);
 #pragma unroll
       for (int j = 0; j < GV; ++j) vnext[j] = __ldg(row + j);
@@ -564,27 +544,26 @@ inline bool part_l1_on(const zeta_ctx* c) { return c->staged_min > 1; }
 constexpr int kRowsCtasPerSm = 2;
 
 template <int NBP, int D>
-int part_impl(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, int64_t np, const float* alm,
-              float* pvals, double* partials, cudaStream_t s) {
+int part_impl(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int64_t* tile_start, int64_t np,
+              const float* alm, float* pvals, double* partials, cudaStream_t s) {
   StageScope prof(c, ST_GRAM_PART, part_staged_on(c) + part_l1_on(c) + 1, s);
   const long long* ts = reinterpret_cast<const long long*>(tile_start);
   const float4* f4 = reinterpret_cast<const float4*>(alm);
-  const double inv_h = c->n / c->p.box;
   if (part_staged_on(c)) {
     const size_t sm = InterpSmem<NBP, D>::BYTES;
     if (prep(k_interp_part<NBP, D>, sm)) return ZETA_ECUDA;
-    k_interp_part<NBP, D><<<gram_ctas(c, GK_PART), kIThreads, sm, s>>>(sorted, ts, f4, c->ng, c->n, c->p.nbins,
-                                                                       inv_h, c->staged_min, pvals, c->d_status);
+    k_interp_part<NBP, D><<<gram_ctas(c, GK_PART), kIThreads, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n,
+                                                                       c->p.nbins, c->staged_min, pvals, c->d_status);
   }
   if (part_l1_on(c)) {
     const size_t sm = InterpL1Smem<NBP, D>::BYTES;
     if (prep(k_interp_part_l1<NBP, D>, sm)) return ZETA_ECUDA;
-    k_interp_part_l1<NBP, D><<<c->num_sms, kThreadsL1, sm, s>>>(sorted, ts, f4, c->ng, c->n, c->p.nbins, inv_h,
+    k_interp_part_l1<NBP, D><<<c->num_sms, kThreadsL1, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n, c->p.nbins,
                                                                 c->staged_min, pvals);
   }
   const size_t sm = smem_rows<NBP>();
   if (prep(k_gram_rows<NBP>, sm)) return ZETA_ECUDA;
-  k_gram_rows<NBP><<<c->num_sms * kRowsCtasPerSm, kThreads, sm, s>>>(pvals, sorted, np, c->p.nbins, partials);
+  k_gram_rows<NBP><<<c->num_sms * kRowsCtasPerSm, kThreads, sm, s>>>(pvals, s_tq, np, c->p.nbins, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
@@ -596,14 +575,14 @@ size_t particle_rows_bytes(const zeta_ctx* c, int64_t np) {
   return sizeof(float) * static_cast<size_t>(np) * nbp_of(c->p.nbins);
 }
 
-int launch_gram_particles(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, int64_t np,
-                          const float* alm, float* pvals, double* partials, cudaStream_t s) {
+int launch_gram_particles(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int64_t* tile_start,
+                          int64_t np, const float* alm, float* pvals, double* partials, cudaStream_t s) {
   if (c->p.dsup == 2) {
-#define ZK_CALL(P) part_impl<P, 2>(c, sorted, tile_start, np, alm, pvals, partials, s)
+#define ZK_CALL(P) part_impl<P, 2>(c, s_cell, s_tq, tile_start, np, alm, pvals, partials, s)
     ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
 #undef ZK_CALL
   } else {
-#define ZK_CALL(P) part_impl<P, 4>(c, sorted, tile_start, np, alm, pvals, partials, s)
+#define ZK_CALL(P) part_impl<P, 4>(c, s_cell, s_tq, tile_start, np, alm, pvals, partials, s)
     ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
 #undef ZK_CALL
   }

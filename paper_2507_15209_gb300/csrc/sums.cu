@@ -11,6 +11,8 @@
 //                  (1 or 2) |delta_hat|^2 Mhat over the half-spectrum modes of that |n|^2
 // The particle form (Eq. DDD-sum-privertex) is in particles.cu.  The weighted-Gram machinery
 // shared by all of them is in gram.cuh.
+#include <utility>
+
 #include "gram.cuh"
 
 namespace zk {
@@ -99,6 +101,227 @@ __global__ void __launch_bounds__(kThreads) k_gram_node(const float* __restrict_
   }
   if (!ok && ct == 0) atomicOr(status, 2);
   cta_store<NBP, kNodeCons, 1>(g, red, nb, partials + static_cast<long long>(blockIdx.x) * nb * nb, ct);
+}
+
+// ---------------------------------------------------------------------------------------
+// Node form, register-blocked (nbins <= 20).  Persistent CTAs over chunks of kRbChunk grid
+// points.  Warp 0 streams each chunk (delta, then the float4 bin groups: 1 + NBP/4 contiguous
+// runs of global memory) into the next slot of a kRbSlots-slot ring with bulk asynchronous
+// copies whose completion the slot's `full` mbarrier counts in bytes; eight consumer warps wait
+// on `full`, each takes 32-point sub-chunks (one point per lane) and accumulates, in float32
+// registers, its share of the whole upper triangle of the bin Gram -- the NP = NBP (NBP + 1) / 2
+// pairs are split into PARTS halves taken by different warps -- and arrives on the slot's
+// `empty` mbarrier, which the producer waits on before refilling it.  A point costs a lane
+// NBP / 4 + 1 shared-memory loads and NBP + NP / PARTS multiplies and FMAs, so the contraction
+// runs at the pace of the copies.  Every kRbFlush points per lane the warp sums each accumulator
+// over its lanes with a fixed butterfly into its float64 row in shared memory; at the end the
+// warps of a part are summed in warp order.  Deterministic; every wait is bounded and latches
+// ZETA_ETIMEOUT in the status word.
+constexpr int kRbCons = 8;                       // consumer warps
+constexpr int kRbThreads = 32 * (kRbCons + 1);   // plus one producer warp
+constexpr int kRbChunk = 256;                    // points per ring slot
+constexpr int kRbSlots = 8;
+constexpr int kRbFlush = 128;                    // points per lane between float64 flushes
+
+template <int NBP>
+struct Tri {
+  static constexpr int NP = NBP * (NBP + 1) / 2;
+  static constexpr int PARTS = NP > 120 ? 2 : 1;
+  static constexpr int NPH = (NP + PARTS - 1) / PARTS;
+  static constexpr int G4 = NBP / 4;
+  static constexpr int SLOT = kRbChunk * 4 * (1 + 4 * G4);  // bytes: delta, then G4 runs of float4
+  // pair index k (row-major over b1 <= b2) -> b1, b2
+  __host__ __device__ static constexpr int b1_of(int k) {
+    int r = 0;
+    while (k >= NBP - r) {
+      k -= NBP - r;
+      ++r;
+    }
+    return r;
+  }
+  __host__ __device__ static constexpr int b2_of(int k) {
+    int r = 0;
+    while (k >= NBP - r) {
+      k -= NBP - r;
+      ++r;
+    }
+    return r + k;
+  }
+};
+
+// acc[k] += (w v[b1]) v[b2] for the pairs K0 + k of half H; the pair indices are template
+// arguments, so every register index is a compile-time constant.
+template <int NBP, int H, int... K>
+__device__ __forceinline__ void rb_accum_seq(float (&acc)[Tri<NBP>::NPH], const float (&v)[NBP], float w,
+                                             std::integer_sequence<int, K...>) {
+  using T = Tri<NBP>;
+  constexpr int K0 = H * T::NPH;
+  float xs[NBP];
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) xs[b] = v[b] * w;  // unused rows are dead code
+  ((K0 + K < T::NP ? (acc[K] = fmaf(xs[T::b1_of(K0 + K < T::NP ? K0 + K : 0)],
+                                    v[T::b2_of(K0 + K < T::NP ? K0 + K : 0)], acc[K]))
+                   : 0.f),
+   ...);
+}
+
+// Sum each accumulator over the warp's lanes (fixed butterfly); lane j keeps the totals of the
+// pairs k = j, j + 32, ... and adds them to its own float64 accumulators, so a flush costs
+// NPH / 32 float64 additions per lane instead of NPH predicated ones per warp.
+template <int NBP>
+__device__ __forceinline__ void rb_flush(float (&acc)[Tri<NBP>::NPH], double (&dacc)[(Tri<NBP>::NPH + 31) / 32],
+                                         int lane) {
+  constexpr int NR = (Tri<NBP>::NPH + 31) / 32;
+  float mine[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) mine[i] = 0.f;
+#pragma unroll
+  for (int k = 0; k < Tri<NBP>::NPH; ++k) {
+    float x = acc[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    mine[k >> 5] = lane == (k & 31) ? x : mine[k >> 5];
+    acc[k] = 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < NR; ++i) dacc[i] += static_cast<double>(mine[i]);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// one contiguous global -> shared copy (16-byte aligned, size a multiple of 16) whose bytes the
+// mbarrier counts on completion
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+template <int NBP, int H>
+__device__ __forceinline__ bool rb_consume(const unsigned char* ring, unsigned long long* full,
+                                           unsigned long long* empty, long long nmine, int sub, int nsub,
+                                           double* drow, int lane) {
+  using T = Tri<NBP>;
+  constexpr int NR = (T::NPH + 31) / 32;
+  float acc[T::NPH];
+  double dacc[NR];
+#pragma unroll
+  for (int k = 0; k < T::NPH; ++k) acc[k] = 0.f;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) dacc[i] = 0.0;
+  int pending = 0;
+  bool ok = true;
+  for (long long i = 0; i < nmine; ++i) {
+    const int s = static_cast<int>(i % kRbSlots);
+    if (!mbar_wait(&full[s], static_cast<uint32_t>((i / kRbSlots) & 1))) {
+      ok = false;
+      break;
+    }
+    const unsigned char* slot = ring + s * T::SLOT;
+    const float* dl = reinterpret_cast<const float*>(slot);
+    const float4* g4 = reinterpret_cast<const float4*>(slot + kRbChunk * 4);
+    for (int j = sub; j < kRbChunk / 32; j += nsub) {
+      const int p = j * 32 + lane;
+      float v[NBP];
+#pragma unroll
+      for (int q = 0; q < T::G4; ++q) {
+        const float4 x = g4[q * kRbChunk + p];
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+      }
+      rb_accum_seq<NBP, H>(acc, v, dl[p], std::make_integer_sequence<int, T::NPH>{});
+      if (++pending == kRbFlush) {
+        rb_flush<NBP>(acc, dacc, lane);
+        pending = 0;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  rb_flush<NBP>(acc, dacc, lane);
+#pragma unroll
+  for (int i = 0; i < NR; ++i)
+    if (32 * i + lane < T::NPH) drow[32 * i + lane] = dacc[i];
+  return ok;
+}
+
+template <int NBP>
+__global__ void __launch_bounds__(kRbThreads, 1)
+    k_gram_node_rb(const float* __restrict__ delta, const float4* __restrict__ f4, long long ng, int nb,
+                   double* __restrict__ partials, int* __restrict__ status) {
+  using T = Tri<NBP>;
+  extern __shared__ __align__(128) unsigned char smq[];
+  unsigned char* ring = smq;                                                               // [kRbSlots][SLOT]
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smq + kRbSlots * T::SLOT);
+  unsigned long long* empty = full + kRbSlots;
+  double* dsum = reinterpret_cast<double*>(empty + kRbSlots);                             // [kRbCons][NPH]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kRbCons * T::NPH; i += blockDim.x) dsum[i] = 0.0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kRbSlots; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kRbCons);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const long long nchunk = ng / kRbChunk;
+  const long long nmine = nchunk > blockIdx.x ? (nchunk - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  if (warp == 0) {  // ---- producer
+    bool ok = true;
+    if (lane == 0) {
+      for (long long i = 0; i < nmine; ++i) {
+        const int s = static_cast<int>(i % kRbSlots);
+        if (i >= kRbSlots && !mbar_wait(&empty[s], static_cast<uint32_t>(((i / kRbSlots) - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const long long p0 = (blockIdx.x + i * gridDim.x) * static_cast<long long>(kRbChunk);
+        unsigned char* slot = ring + s * T::SLOT;
+        mbar_expect_tx(&full[s], T::SLOT);
+        bulk_copy(slot, delta + p0, kRbChunk * 4, &full[s]);
+#pragma unroll
+        for (int q = 0; q < T::G4; ++q)
+          bulk_copy(slot + kRbChunk * 4 + q * kRbChunk * 16, f4 + q * ng + p0, kRbChunk * 16, &full[s]);
+      }
+      if (!ok) atomicOr(status, 2);
+      // copies of the last slots may still be landing if the consumers stopped early
+      for (long long j = (nmine > kRbSlots ? nmine - kRbSlots : 0); j < nmine; ++j)
+        mbar_wait(&full[j % kRbSlots], static_cast<uint32_t>((j / kRbSlots) & 1));
+    }
+    __syncwarp();
+  } else {  // ---- consumers
+    const int cw = warp - 1;
+    const int part = cw % T::PARTS, sub = cw / T::PARTS, nsub = kRbCons / T::PARTS;
+    bool ok;
+    if (part == 0)
+      ok = rb_consume<NBP, 0>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH, lane);
+    else
+      ok = rb_consume<NBP, (T::PARTS > 1 ? 1 : 0)>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH, lane);
+    if (!ok && lane == 0) atomicOr(status, 2);
+  }
+  __syncthreads();
+  double* out = partials + static_cast<long long>(blockIdx.x) * nb * nb;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int r = e / nb, c = e % nb;
+    const int lo = r < c ? r : c, hi = r < c ? c : r;
+    const int k = lo * NBP - lo * (lo - 1) / 2 + (hi - lo);  // row-major pair index
+    const int pt = k / T::NPH, kk = k % T::NPH;
+    double sum = 0.0;
+    for (int w = pt; w < kRbCons; w += T::PARTS) sum += dsum[w * T::NPH + kk];
+    out[e] = sum;
+  }
+}
+
+template <int NBP>
+constexpr size_t smem_node_rb() {
+  return static_cast<size_t>(kRbSlots) * Tri<NBP>::SLOT + 2 * kRbSlots * sizeof(unsigned long long) +
+         static_cast<size_t>(kRbCons) * Tri<NBP>::NPH * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -331,7 +554,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_mass(const unsigned long long
 // One warp per output entry: lane j sums the partials j, j + 32, ... in order, then a fixed
 // butterfly combines the lanes, so the result does not depend on scheduling.
 __global__ void k_reduce(const double* __restrict__ part, int nparts, int nb, double scale,
-                         const double* __restrict__ wdiv, double* __restrict__ out) {
+                         const double* __restrict__ wdiv, double* __restrict__ out, int store) {
   const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (e >= nb * nb) return;  // whole warps leave together
@@ -344,8 +567,30 @@ __global__ void k_reduce(const double* __restrict__ part, int nparts, int nb, do
   if (lane == 0) {
     double sc = scale;
     if (wdiv) sc /= *wdiv;
-    out[e] += sc * sum;
+    // the product is rounded before the add (no fused multiply-add), so a contribution stored
+    // in a slot and added later (zeta_reduce_lm) rounds exactly as one added here
+    const double c = __dmul_rn(sc, sum);
+    out[e] = store ? c : __dadd_rn(out[e], c);
   }
+}
+
+// zeta_l of every form from per-(l, m) contribution slots, in the order the full measurement
+// adds them: 0, then the uniform term of l (particle form), then m = -l .. l.  One thread per
+// output entry.  slots: [form][(lmax+1)^2 + lmax+1][nb][nb], (l, m) at l^2 + l + m, the
+// uniform term of l at (lmax+1)^2 + l.
+__global__ void k_reduce_lm(const double* __restrict__ slots, int nforms, int part_form, int lmax, int nb,
+                            double* __restrict__ zeta) {
+  const int nb2 = nb * nb;
+  const int total = nforms * (lmax + 1) * nb2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int e = i % nb2, l = (i / nb2) % (lmax + 1), f = i / (nb2 * (lmax + 1));
+  const int nslot = (lmax + 1) * (lmax + 1) + lmax + 1;
+  const double* sf = slots + static_cast<long long>(f) * nslot * nb2;
+  double acc = 0.0;
+  if (f == part_form) acc = __dadd_rn(acc, sf[static_cast<long long>((lmax + 1) * (lmax + 1) + l) * nb2 + e]);
+  for (int m = -l; m <= l; ++m) acc = __dadd_rn(acc, sf[static_cast<long long>(l * l + l + m) * nb2 + e]);
+  zeta[i] = acc;
 }
 
 template <int NBP>
@@ -368,6 +613,13 @@ size_t smem_gamma() {
 template <int NBP>
 int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
   StageScope prof(c, ST_GRAM_NODE, 1, s);
+  if constexpr (NBP <= 20) {
+    const size_t smr = smem_node_rb<NBP>();
+    if (prep(k_gram_node_rb<NBP>, smr)) return ZETA_ECUDA;
+    k_gram_node_rb<NBP><<<gram_ctas(c, GK_NODE), kRbThreads, smr, s>>>(
+        delta, reinterpret_cast<const float4*>(alm), c->ng, c->p.nbins, partials, c->d_status);
+    return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+  }
   const size_t sm = smem_node<NBP>();
   if (prep(k_gram_node<NBP>, sm)) return ZETA_ECUDA;
   k_gram_node<NBP><<<gram_ctas(c, GK_NODE), kThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
@@ -440,10 +692,17 @@ int launch_mass(const zeta_ctx* c, const unsigned long long* hist, int l, double
 }
 
 int launch_reduce(const zeta_ctx* c, const double* partials, int nparts, double scale, const double* wdiv,
-                  double* out, cudaStream_t s) {
+                  double* out, cudaStream_t s, bool store) {
   StageScope prof(c, ST_REDUCE, 1, s);
   const int nb = c->p.nbins;
-  k_reduce<<<(nb * nb + 7) / 8, 256, 0, s>>>(partials, nparts, nb, scale, wdiv, out);
+  k_reduce<<<(nb * nb + 7) / 8, 256, 0, s>>>(partials, nparts, nb, scale, wdiv, out, store ? 1 : 0);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
+int launch_reduce_lm(const zeta_ctx* c, const double* slots, int nforms, int part_form, double* zeta, cudaStream_t s) {
+  StageScope prof(c, ST_REDUCE, 1, s);
+  const int total = nforms * (c->p.lmax + 1) * c->p.nbins * c->p.nbins;
+  k_reduce_lm<<<(total + 255) / 256, 256, 0, s>>>(slots, nforms, part_form, c->p.lmax, c->p.nbins, zeta);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 

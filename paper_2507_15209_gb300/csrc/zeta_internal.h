@@ -130,9 +130,27 @@ int launch_assign(const zeta_ctx* c, const float4* parts, int64_t np, float* del
                   unsigned long long* acc, double* scratch2, cudaStream_t s);
 int launch_wsum(const zeta_ctx* c, const float4* parts, int64_t np, double* wsum, double* scratch, cudaStream_t s);
 constexpr int kAssignScratchDoubles = 2 * 1024 + 4;
-// sorted_idx (optional): original index of each sorted particle
+// Per-particle data computed once per catalogue with the float64 cell arithmetic, so the kernels
+// that run per (l, m) need none: the cell (linear index z n^2 + y n + x) and (t_x, t_y, t_z, w),
+// the in-cell offsets and the weight (0 for a non-finite particle).  o_*: original order
+// (scratch, with the tile of each particle), s_*: sorted order.
+struct PartPrep {
+  int* o_tile = nullptr;
+  int* o_cell = nullptr;
+  float4* o_tq = nullptr;
+  int* s_cell = nullptr;
+  float4* s_tq = nullptr;
+};
+// sorted_idx (optional): original index of each sorted particle; prep (optional): also write the
+// prepared data of the sorted particles
 int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sorted, int64_t* tile_start,
-                int* counts, int* orig, cudaStream_t s, int* sorted_idx = nullptr);
+                int* counts, int* orig, cudaStream_t s, int* sorted_idx = nullptr, const PartPrep* prep = nullptr);
+// prepared data of an already sorted catalogue
+int launch_prep_sorted(const zeta_ctx* c, const float4* sorted, int64_t np, int* s_cell, float4* s_tq, cudaStream_t s);
+// assignment from the sorted, prepared catalogue (weight sums, then one CTA per tile writes delta)
+int launch_assign_tiles(const zeta_ctx* c, const float4* parts, int64_t np, const int64_t* tile_start,
+                        const int* s_cell, const float4* s_tq, float* delta, double* wsum, double* scratch,
+                        cudaStream_t s);
 
 // ---- adjoint (adjoint.cu) ----
 // S: symmetrised loss weights of one l, device float [nb][nb]
@@ -152,8 +170,8 @@ int gram_ctas(const zeta_ctx* c, int kind);
 int launch_gram_node(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
 int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, double* partials,
                       cudaStream_t s);
-int launch_gram_particles(const zeta_ctx* c, const float4* sorted, const int64_t* tile_start, int64_t np,
-                          const float* alm, float* pvals, double* partials, cudaStream_t s);
+int launch_gram_particles(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int64_t* tile_start,
+                          int64_t np, const float* alm, float* pvals, double* partials, cudaStream_t s);
 // Bytes of the interpolated particle rows [np][bins padded to 4] that launch_gram_particles uses.
 size_t particle_rows_bytes(const zeta_ctx* c, int64_t np);
 // tensor-core node Gram (gram_tc.cu), arithmetic chosen by c->p.gram
@@ -168,6 +186,8 @@ int launch_mass(const zeta_ctx* c, const unsigned long long* hist, int l, double
 int gram_particle_parts(const zeta_ctx* c);
 // out[b1][b2] += scale * (1/ *wdiv if wdiv) * sum_cta partials[cta][b1][b2], symmetrised.
 int launch_reduce(const zeta_ctx* c, const double* partials, int nparts, double scale, const double* wdiv,
-                  double* out, cudaStream_t s);
+                  double* out, cudaStream_t s, bool store = false);
+// zeta[f][l] = per-(l, m) slots summed in the full measurement's order (see zeta_reduce_lm).
+int launch_reduce_lm(const zeta_ctx* c, const double* slots, int nforms, int part_form, double* zeta, cudaStream_t s);
 
 }  // namespace zk

@@ -53,6 +53,9 @@ _SIGS = {
     "zeta_sum_particles": ([_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP], _INT),
     "zeta_mass_term": ([_VP, _VP, _INT, _DBL, _VP, _VP], _INT),
     "zeta_zeta_ell": ([_VP, _VP, _I64, _VP, _INT, _VP, _VP], _INT),
+    "zeta_zeta_lm": ([_VP, _VP, _I64, _VP, _INT, _INT, _INT, _VP, _VP], _INT),
+    "zeta_reduce_lm": ([_VP, _VP, _INT, _VP, _VP], _INT),
+    "zeta_lm_slots": ([_VP, _INT], _SZ),
     "zeta_get_status": ([_VP, _VP], _INT),
     "zeta_selftest_wait": ([_VP, _I64, _VP], _INT),
     "zeta_batch": ([_VP, _VP, _VP, _INT, _INT, _VP, _VP], _INT),
@@ -151,6 +154,17 @@ def assign_noalloc(n: int, box: float, dsup: int, particles, delta=None, wsum=No
                                                             particles.shape[0], _f32(delta, "delta", n ** 3),
                                                             _f64(wsum, "wsum", 1), _stream()))
     return delta, wsum
+
+
+def lm_pairs(lm_rank: int, lm_size: int, lmax: int) -> list:
+    """The (l, m) pairs rank lm_rank of lm_size runs in zeta_zeta_lm: index l^2 + l + m, round robin."""
+    return [(l, m) for l in range(lmax + 1) for m in range(-l, l + 1) if (l * l + l + m) % lm_size == lm_rank]
+
+
+def lm_slot(l: int, m: int) -> int:
+    """Slot of (l, m) in a zeta_zeta_lm slot array (per form); the uniform term of l is at
+    (lmax+1)^2 + l."""
+    return l * l + l + m
 
 
 def interleave(a):
@@ -350,6 +364,37 @@ class Context:
         _check("zeta_zeta_ell", lib().zeta_zeta_ell(self._h, _f32(particles, "particles", cols=4), np_,
                                                     _f32(delta, "delta", self.ng), bits,
                                                     _f64(out, "out", len(order) * per), _stream()))
+        return {f: out[i] for i, f in enumerate(order)}
+
+    def lm_slots(self, forms=("particle",)) -> int:
+        """Number of float64 values in a per-(l, m) slot array (zeta_lm_slots)."""
+        return int(lib().zeta_lm_slots(self._h, self.form_bits(forms) & 7))
+
+    def zeta_lm(self, lm_rank: int, lm_size: int, particles=None, delta=None, forms=("particle",), out=None):
+        """zeta_zeta_lm: this rank's (l, m) contributions, one slot each (see lm_pairs); returns
+        the flat float64 slot array."""
+        import torch
+        bits = self.form_bits(forms) & 7
+        k = self.lm_slots(forms)
+        if out is None:
+            out = torch.empty(k, dtype=torch.float64, device="cuda")
+        np_ = 0 if particles is None else particles.shape[0]
+        _check("zeta_zeta_lm", lib().zeta_zeta_lm(self._h, _f32(particles, "particles", cols=4), np_,
+                                                  _f32(delta, "delta", self.ng), bits, int(lm_rank), int(lm_size),
+                                                  _f64(out, "out", k), _stream()))
+        return out
+
+    def reduce_lm(self, slots, forms=("particle",), out=None):
+        """zeta_reduce_lm: {form: (lmax+1, nb, nb)} from summed slots, bit-identical to zeta_ell."""
+        import torch
+        bits = self.form_bits(forms) & 7
+        order = [f for f in ("node", "gamma", "particle") if bits & FORM_BITS[f]]
+        if out is None:
+            out = torch.empty((len(order), self.lmax + 1, self.nbins, self.nbins), dtype=torch.float64,
+                              device="cuda")
+        per = (self.lmax + 1) * self.nbins ** 2
+        _check("zeta_reduce_lm", lib().zeta_reduce_lm(self._h, _f64(slots, "slots", self.lm_slots(forms)), bits,
+                                                      _f64(out, "out", len(order) * per), _stream()))
         return {f: out[i] for i, f in enumerate(order)}
 
     def profile_enable(self, on: bool = True):

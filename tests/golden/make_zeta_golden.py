@@ -143,7 +143,14 @@ def main():
     args = ap.parse_args()
     forms = tuple(args.forms.split(","))
     cache = args.cache or tempfile.mkdtemp(prefix="zeta_golden_")
-    res = {"command": "python tests/golden/make_zeta_golden.py " + " ".join(sys.argv[1:]),
+    argv = []
+    skip = False
+    for a in sys.argv[1:]:  # the checkpoint directory is not part of the result's recipe
+        if skip or a == "--cache" or a.startswith("--cache="):
+            skip = a == "--cache"
+            continue
+        argv.append(a)
+    res = {"command": "python tests/golden/make_zeta_golden.py " + " ".join(argv),
            "oracle": "oracle/zeta_oracle.py (FP64)", "data": run(args.workload, forms, False, args.procs,
                                                                   os.path.join(cache, "data"))}
     if args.null:

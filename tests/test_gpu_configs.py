@@ -100,3 +100,8 @@ def test_plain_method_64_all_forms(Z):
 
 def test_plain_method_64_uniform_null(Z):
     _run(Z, "box500_n64_np20k", "null", ("node", "gamma", "particle"))
+
+
+@pytest.mark.slow
+def test_fp32_path_256_full_multipoles(Z):
+    _run(Z, "box1000_n256_np2m", "data", ("particle", "node"))
