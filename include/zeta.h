@@ -16,6 +16,8 @@
  *   zeta_sum_particles   step (6)  particle summation                         (Eq. DDD-sum-privertex)
  *   zeta_mass_term       step (6)  the uniform ("-1") term of the particle form, per l
  *   zeta_zeta_ell        steps (2)-(7)  the whole measurement of zeta_l(r1, r2), l <= lmax
+ *   zeta_xi              the 2PCF from the l = 0 machinery           (Eq. pair-counting)
+ *   zeta_host_legendre_sum, zeta_host_reduced_q  zeta(theta) and Q   (Eqs. triplet-counting, Q-factor)
  *
  * Conventions shared by every call
  *   - Grids are float32, indexed [z][y][x] with x fastest, side n, N_g = n^3, cell H = box/n.
@@ -74,8 +76,9 @@ enum {
   ZETA_EDATA = -7       /* device found invalid input data (non-finite particle)    */
 };
 
-/* Summation forms (bit mask).  ZETA_WS_BACKWARD only sizes the workspace for the gradient calls. */
-enum { ZETA_SUM_NODE = 1, ZETA_SUM_GAMMA = 2, ZETA_SUM_PARTICLE = 4, ZETA_WS_BACKWARD = 8 };
+/* Summation forms (bit mask).  ZETA_WS_BACKWARD and ZETA_WS_SS only size the workspace for the
+ * gradient calls and for zeta_zeta_ell_ss. */
+enum { ZETA_SUM_NODE = 1, ZETA_SUM_GAMMA = 2, ZETA_SUM_PARTICLE = 4, ZETA_WS_BACKWARD = 8, ZETA_WS_SS = 16 };
 
 /* Arithmetic of the node-form Gram contraction (Sec. 2.2 grid sum). */
 enum {
@@ -85,6 +88,13 @@ enum {
   ZETA_GRAM_BF16X3 = 3  /* tensor cores, split bf16 (hi*hi + hi*lo + lo*hi)          */
 };
 
+/* Radial part of the secondary-vertex windows (Sec. 3 binning, Eq. 3PCF-multipole-window). */
+enum {
+  ZETA_RADIAL_SHELL = 0, /* r^2-weighted average of j_l(k r) over the bin [edges[b], edges[b+1]) */
+  ZETA_RADIAL_POINT = 1  /* the spherical shell of radius radii[b] itself: j_l(k r_b), the     */
+                         /* paper's triangle sides R_A, R_B (one "bin" per radius)              */
+};
+
 typedef struct {
   int n;                /* grid side: power of two, 16 <= n <= 512                   */
   double box;           /* periodic box side, same unit as positions and edges       */
@@ -92,8 +102,21 @@ typedef struct {
   int lmax;             /* highest multipole l, 0 <= lmax <= 14                      */
   int nbins;            /* number of radial bins, 1 <= nbins <= 32                   */
   const double* edges;  /* host, nbins+1 strictly increasing, edges[0] > 0,          */
-                        /* edges[nbins] < box/2; copied by zeta_create               */
+                        /* edges[nbins] < box/2; copied by zeta_create (SHELL only;  */
+                        /* may be NULL with ZETA_RADIAL_POINT)                       */
   int gram;             /* ZETA_GRAM_*                                               */
+  /* Vertex windows (Fig. 1 steps (3)-(4), Sec. 3); all zero keeps the defaults above.  Each
+   * secondary vertex's kernel sqrt(4 pi) i^l W_l,b(|k|) R_lm(k-hat) may be multiplied by a
+   * spherical tophat and by the basis power spectrum; the grid forms' primary vertex may be
+   * smoothed by its own tophat.  W_TH(x) = 3 (sin x - x cos x) / x^3.                    */
+  int radial;           /* ZETA_RADIAL_SHELL (0) or ZETA_RADIAL_POINT                 */
+  const double* radii;  /* host, nbins radii in (0, box/2) for ZETA_RADIAL_POINT      */
+  double tophat;        /* R >= 0: secondary vertices times W_TH(|k| R) (0: none)     */
+  double tophat_primary;/* R >= 0: the node and Gamma forms' primary vertex delta is  */
+                        /* replaced by IDFT[DFT(delta) W_TH(|k| R)] (0: none); the     */
+                        /* particle form's primary vertex is the catalogue itself     */
+  int phi_hat;          /* 1: secondary vertices times Phi-hat(n) = prod_d            */
+                        /* sinc^{2D}(pi n_d / n), |beta-hat|^2 of the basis (no aliasing) */
 } zeta_params;
 
 /* Library version (major*10000 + minor*100 + patch). Host only. */
@@ -183,6 +206,38 @@ int zeta_mass_term(zeta_ctx* ctx, const float* delta_hat, int l, double sign, do
 int zeta_zeta_ell(zeta_ctx* ctx, const float* particles, int64_t np, const float* delta, int forms,
                   double* zeta, zeta_stream stream);
 
+/* The Szapudi-Szalay estimator with a random catalogue, Eq. (SSestimator), in multipoles: with
+ * delta_D and delta_R the contrasts of the data and of the randoms (each assigned like zeta_assign,
+ * so D and R are normalised to unit mean density), the numerator is the measurement of
+ * Delta = delta_D - delta_R (the SFC difference of Sec. 3) and the denominator that of
+ * R~ = 1 + delta_R, each exactly as zeta_zeta_ell on a given delta (grid forms: ZETA_SUM_NODE
+ * and/or ZETA_SUM_GAMMA).  The estimator is zeta(theta) = sum_l num_l P_l / sum_l den_l P_l
+ * (zeta_host_legendre_sum).  data, randoms: device float4[nd], float4[nr]; num, den: device
+ * double[nforms * (lmax+1) * nbins * nbins].  The workspace must be sized with ZETA_WS_SS. */
+int zeta_zeta_ell_ss(zeta_ctx* ctx, const float* data, int64_t nd, const float* randoms, int64_t nr, int forms,
+                     double* num, double* den, zeta_stream stream);
+
+/* The 2PCF from the same machinery (Sec. 2.1, Eq. pair-counting with the translated field of
+ * Eq. trans-field-FT; the isotropic shell filter of Eq. DD-windowfunction is the l = 0 window):
+ *   node form      xi_b = (1/N_g) sum_l delta_p(l) a_00,b(l), evaluated in Fourier space as
+ *                  (1/N_g^2) sum_n |delta_hat|^2 Phi-hat W_0,b W_p (Parseval; non-Nyquist modes)
+ *                  from per-|n|^2 fixed-point sums of |delta_hat|^2 Phi-hat;
+ *   particle form  xi_b = (1/W) sum_p w_p f_b(x_p), f_b the B-spline expansion of a_00,b at the
+ *                  particles (the uniform term vanishes: the fields have zero mean).
+ * particles / delta as for zeta_zeta_ell; forms: ZETA_SUM_NODE and/or ZETA_SUM_PARTICLE (the
+ * Gamma form is not offered here); xi: device double[nforms * nbins] (forms in that order).
+ * The context's vertex windows apply (radial, tophat, phi_hat; tophat_primary for the node form). */
+int zeta_xi(zeta_ctx* ctx, const float* particles, int64_t np, const float* delta, int forms, double* xi,
+            zeta_stream stream);
+
+/* The node-form 2PCF at arbitrary radii (point shells j_0(k r), times the context's secondary
+ * tophat, Phi-hat and primary tophat), from delta_hat (device, as zeta_fft_r2c writes it):
+ * xi[i] = (1/N_g^2) sum_n |delta_hat|^2 Phi-hat j_0(|k| radii[i]) W_TH(|k| R) W_p(|k|); radii: host
+ * double[nr] (0 < nr <= 4096, radii >= 0); xi: device double[nr].  This is the xi(r_3) the reduced
+ * 3PCF needs at the third side of each triangle.  Synchronises the stream. */
+int zeta_xi_radii(zeta_ctx* ctx, const float* delta_hat, int nr, const double* radii, double* xi,
+                  zeta_stream stream);
+
 /* The measurement split over (l, m) pairs, for running one catalogue on several GPUs.  The pairs
  * are independent (Eq. 3PCF-multipole-sum sums them; the paper's own code runs them in parallel,
  * Sec. 3.4), so P processes can each take the pairs of index i = l^2 + l + m with
@@ -213,7 +268,9 @@ size_t zeta_lm_slots(const zeta_ctx* ctx, int forms);
  *                            same particles (device float[np * 3] out, original order; the
  *                            weights w_p are held fixed).
  * The workspace must be sized with ZETA_WS_BACKWARD.  The particle scatter uses float atomics,
- * so that gradient is reproducible to float32 rounding only. */
+ * so that gradient is reproducible to float32 rounding only.  The secondary-vertex windows
+ * (radial, tophat, phi_hat) enter the transposed kernels; a context with tophat_primary > 0
+ * returns ZETA_ENOTSUP here. */
 int zeta_backward_node(zeta_ctx* ctx, const float* delta, const double* weights, float* grad, zeta_stream stream);
 int zeta_backward_particles(zeta_ctx* ctx, const float* particles, int64_t np, const double* weights, float* grad,
                             zeta_stream stream);
@@ -315,6 +372,26 @@ double zeta_host_ylm(int l, int m, double vx, double vy, double vz);
  * memory of (lmax + 1) N2 nbp floats.  n a power of two in [4, 512], box > 0, lmax <= 14,
  * 1 <= nbins <= 32, edges (nbins + 1 values) positive and increasing, else ZETA_EINVAL. */
 int zeta_host_jbar_table(int n, double box, int lmax, int nbins, const double* edges, float* out);
+
+/* The window table a context with these parameters uploads (the same layout as
+ * zeta_host_jbar_table): out[(l * N2 + n2) * nbp + b] = sqrt(4 pi) W_l,b(2 pi sqrt(n2) / box) / n^3,
+ * W_l,b the radial window of p->radial (bin average or point radius) times W_TH(k p->tophat) when
+ * p->tophat > 0.  Host only; ZETA_EINVAL on invalid parameters. */
+int zeta_host_window_table(const zeta_params* p, float* out);
+
+/* Phi-hat per axis: out[i] = sinc^{2 dsup}(pi f / n) for DFT index i < n, f its signed frequency
+ * (Fig. 1 step (3), the basis power spectrum without aliasing).  Host only. */
+int zeta_host_phi_hat(int n, int dsup, double* out);
+
+/* The 3PCF in angle from its multipoles, Eq. (triplet-counting): out[i][b1][b2] =
+ * sum_{l <= lmax} zeta_l[l][b1][b2] P_l(mu[i]), P_l by the three-term recurrence, float64 host
+ * arrays (zeta_l: (lmax+1) nb nb; mu: nmu values in [-1, 1]; out: nmu nb nb). */
+int zeta_host_legendre_sum(int lmax, int nb, const double* zeta_l, int nmu, const double* mu, double* out);
+
+/* The reduced 3PCF, Eq. (Q-factor): q[i] = zeta[i] / (xi1 xi2 + xi2 xi3 + xi3 xi1)[i], with xi1 =
+ * xi(r_1), xi2 = xi(r_2), xi3 = xi(r_3) of each triangle.  Host arrays of count doubles. */
+int zeta_host_reduced_q(int count, const double* zeta, const double* xi1, const double* xi2, const double* xi3,
+                        double* q);
 
 /* Mhat(k) = M(0) + 2 sum_{0<a<dsup} M(a) cos(2 pi k a / n) for 0 <= k < n, in float64: the 1-D
  * factor of the B-spline mass matrix's DFT in the uniform term of the particle form (Sec. 2.2,

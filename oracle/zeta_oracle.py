@@ -45,9 +45,10 @@ from scipy import special
 
 __all__ = [
     "bspline", "stencil_base", "assign", "contrast", "fft_integers", "nyquist_mask",
-    "jbar", "real_ylm", "window_kernel", "multipole_fields", "sum_node",
+    "jbar", "real_ylm", "tophat_window", "phi_hat", "radial_window", "primary_filter", "window_kernel", "multipole_fields", "sum_node",
     "gamma_1d", "mass_1d", "sum_gamma", "interpolate", "sum_particles",
-    "mass_term", "mass_term_fourier", "zeta_multipoles", "zeta_from_delta", "brute_force_raw",
+    "mass_term", "mass_term_fourier", "zeta_multipoles", "xi_node", "xi_particle", "legendre_sum", "reduced_q",
+    "zeta_szapudi_szalay", "zeta_from_delta", "brute_force_raw",
     "bspline_deriv", "interpolate_grad", "loss", "grad_node_delta", "grad_particle_positions",
 ]
 
@@ -179,35 +180,89 @@ def _grid_integers(n: int):
     return nx, ny, nz
 
 
-def window_kernel(ell: int, m: int, n: int, box: float, edges, bins=None):
-    """K_lm,b(n) = sqrt(4 pi) i^l jbar_l(|k_n|; b) R_lm(k_n-hat), Nyquist planes zero.
+def tophat_window(x):
+    """W_TH(x) = 3 (sin x - x cos x) / x^3, x = k R: the Fourier transform of the uniform ball of
+    radius R (unit volume integral), the vertex binning window of Sec. 3 (spherical tophat)."""
+    x = np.asarray(x, np.float64)
+    small = np.abs(x) < 1e-2
+    xs = np.where(small, 1.0, x)
+    w = 3.0 * (np.sin(xs) - xs * np.cos(xs)) / xs ** 3
+    x2 = x * x
+    return np.where(small, 1.0 - x2 / 10.0 + x2 * x2 / 280.0, w)
 
-    Eq. (3PCF-multipole-window) with the bin average of reading R4.
-    Returns complex array (len(bins), n, n, n) over the full DFT grid [z, y, x];
-    bins defaults to every bin.
+
+def phi_hat(n: int, dsup: int):
+    """Phi-hat(n) = prod_d sinc^{2 dsup}(pi n_d / n), the power spectrum |beta-hat|^2 of the
+    B-spline basis at the lattice wavevectors, without the aliasing sum (Fig. 1 step (3) and
+    Eq. SFC-3PCF-vertex; reading: the aliasing images are dropped as the paper's delta_{m,n}
+    does).  Full DFT grid [z, y, x]."""
+    s1 = np.sinc(fft_integers(n) / n) ** (2 * dsup)
+    return s1[:, None, None] * s1[None, :, None] * s1[None, None, :]
+
+
+def radial_window(ell: int, k, b: int, edges, vertex=None):
+    """The radial factor of the vertex window of bin b at wavenumbers k.
+
+    vertex["radial"] == "shell" (default): jbar_l(k; [edges[b], edges[b+1])) (reading R4);
+    "point": j_l(k r_b) with r_b = vertex["radii"][b], the spherical shell of Eq.
+    (3PCF-multipole-window) itself (the paper's triangle sides R_A, R_B).  A vertex["tophat"]
+    radius R > 0 multiplies by the spherical tophat W_TH(k R) (Sec. 3 binning)."""
+    vertex = vertex or {}
+    k = np.asarray(k, np.float64)
+    if vertex.get("radial", "shell") == "point":
+        out = special.spherical_jn(ell, k * float(vertex["radii"][b]))
+    else:
+        out = jbar(ell, k, edges[b], edges[b + 1])
+    if vertex.get("tophat", 0.0) > 0.0:
+        out = out * tophat_window(k * float(vertex["tophat"]))
+    return out
+
+
+def window_kernel(ell: int, m: int, n: int, box: float, edges, bins=None, vertex=None):
+    """K_lm,b(n) = sqrt(4 pi) i^l W_l,b(|k_n|) R_lm(k_n-hat) [Phi-hat(n)], Nyquist planes zero.
+
+    Eq. (3PCF-multipole-window) with the radial factor of radial_window (the bin average of
+    reading R4 by default) and, when vertex["phi_dsup"] = D > 0, the basis power spectrum
+    Phi-hat of Eq. (SFC-3PCF-vertex).  Returns complex array (len(bins), n, n, n) over the full
+    DFT grid [z, y, x]; bins defaults to every bin.
     """
+    vertex = vertex or {}
     nx, ny, nz = _grid_integers(n)
     n2 = nx * nx + ny * ny + nz * nz
     uniq, inv = np.unique(n2, return_inverse=True)
     kmag = 2.0 * math.pi / box * np.sqrt(uniq.astype(np.float64))
     ang = real_ylm(ell, m, nx, ny, nz)
+    if vertex.get("phi_dsup", 0):
+        ang = ang * phi_hat(n, vertex["phi_dsup"])
     ny_mask = nyquist_mask(n)
-    bins = list(range(len(edges) - 1)) if bins is None else list(bins)
+    nbins = len(vertex["radii"]) if vertex.get("radial") == "point" else len(edges) - 1
+    bins = list(range(nbins)) if bins is None else list(bins)
     out = np.empty((len(bins), n, n, n), np.complex128)
     for i, b in enumerate(bins):
-        jb = jbar(ell, kmag, edges[b], edges[b + 1])[inv].reshape(n2.shape)
+        jb = radial_window(ell, kmag, b, edges, vertex)[inv].reshape(n2.shape)
         kern = math.sqrt(FOUR_PI) * (1j ** ell) * jb * ang
         kern[ny_mask] = 0.0
         out[i] = kern
     return out
 
 
-def multipole_fields(delta_hat, ell: int, m: int, n: int, box: float, edges, bins=None):
+def primary_filter(delta, n: int, box: float, radius: float):
+    """The primary vertex smoothed by the spherical tophat of the given radius:
+    IDFT[DFT(delta) W_TH(|k| R)] (the binning function W_p of Fig. 1 step (3)), with the
+    Nyquist planes zero like every kernel of the method (reading R5)."""
+    nx, ny, nz = _grid_integers(n)
+    kmag = 2.0 * math.pi / box * np.sqrt((nx * nx + ny * ny + nz * nz).astype(np.float64))
+    kern = tophat_window(kmag * radius)
+    kern[nyquist_mask(n)] = 0.0
+    return np.fft.ifftn(np.fft.fftn(delta) * kern).real
+
+
+def multipole_fields(delta_hat, ell: int, m: int, n: int, box: float, edges, bins=None, vertex=None):
     """a_lm,b(l) = IDFT[delta_hat * K_lm,b], Eq. (SFC-3PCF-vertex), Fig. 1 step (5).
 
     The fields are real (readings R1, R5); returns float64 (len(bins), n, n, n).
     """
-    kern = window_kernel(ell, m, n, box, edges, bins)
+    kern = window_kernel(ell, m, n, box, edges, bins, vertex)
     out = np.empty(kern.shape, np.float64)
     for b in range(kern.shape[0]):
         a = np.fft.ifftn(delta_hat * kern[b])
@@ -341,7 +396,7 @@ def mass_term(a, dsup: int):
     return out / ng
 
 
-def mass_term_fourier(delta_hat, ell: int, n: int, box: float, edges, dsup: int, bins=None):
+def mass_term_fourier(delta_hat, ell: int, n: int, box: float, edges, dsup: int, bins=None, vertex=None):
     """U summed over m for one l, in Fourier space (reading R7 with the addition theorem).
 
     The real-space form above is (1/N_g) a_b1^T M3 a_b2 with a_b = IDFT(delta_hat K_b); by
@@ -357,13 +412,18 @@ def mass_term_fourier(delta_hat, ell: int, n: int, box: float, edges, dsup: int,
     nx, ny, nz = _grid_integers(n)
     n2 = nx * nx + ny * ny + nz * nz
     keep = ~nyquist_mask(n)
-    p = (np.abs(delta_hat) ** 2 * (mhat1[:, None, None] * mhat1[None, :, None] * mhat1[None, None, :]))[keep]
+    vertex = vertex or {}
+    p = np.abs(delta_hat) ** 2 * (mhat1[:, None, None] * mhat1[None, :, None] * mhat1[None, None, :])
+    if vertex.get("phi_dsup", 0):
+        p = p * phi_hat(n, vertex["phi_dsup"]) ** 2
+    p = p[keep]
     n2k = n2[keep]
     uniq, inv = np.unique(n2k, return_inverse=True)
     psum = np.bincount(inv.ravel(), weights=p, minlength=len(uniq))  # |delta_hat|^2 Mhat per |n|^2
     kmag = 2.0 * math.pi / box * np.sqrt(uniq.astype(np.float64))
-    bins = list(range(len(edges) - 1)) if bins is None else list(bins)
-    jb = np.stack([jbar(ell, kmag, edges[b], edges[b + 1]) for b in bins])
+    nbins = len(vertex["radii"]) if vertex.get("radial") == "point" else len(edges) - 1
+    bins = list(range(nbins)) if bins is None else list(bins)
+    jb = np.stack([radial_window(ell, kmag, b, edges, vertex) for b in bins])
     return (2 * ell + 1) * (jb * psum[None, :]) @ jb.T / float(n) ** 6
 
 
@@ -375,17 +435,22 @@ def _symmetrise(x):
 
 
 def zeta_from_delta(delta, n: int, box: float, edges, lmax: int, dsup: int,
-                    forms=("node",), particles=None, raw_particle=False):
+                    forms=("node",), particles=None, raw_particle=False, vertex=None, primary_tophat=0.0):
     """zeta_l(b1, b2) for l <= lmax from a contrast grid (and particles for that form).
 
     forms: any of "node", "gamma", "particle".  Returns (zeta, cond) dicts of
     float64 arrays (lmax+1, nb, nb); cond holds the sum of absolute values of
     the summed terms (the condition sum used to judge FP32 attainable error).
     raw_particle drops the U term (the raw-DDD reading used against brute force).
+    vertex sets the secondary-vertex windows (see window_kernel); primary_tophat > 0 smooths
+    the primary vertex of the grid forms with the spherical tophat of that radius (the
+    particle form's primary vertex is the particles themselves, unfiltered).
     """
-    nb = len(edges) - 1
+    vertex = vertex or {}
+    nb = len(vertex["radii"]) if vertex.get("radial") == "point" else len(edges) - 1
     delta = np.asarray(delta, np.float64)
     delta_hat = np.fft.fftn(delta)
+    prim = primary_filter(delta, n, box, primary_tophat) if primary_tophat > 0.0 else delta
     zeta = {f: np.zeros((lmax + 1, nb, nb)) for f in forms}
     cond = {f: np.zeros((lmax + 1, nb, nb)) for f in forms}
     if "particle" in forms:
@@ -393,12 +458,12 @@ def zeta_from_delta(delta, n: int, box: float, edges, lmax: int, dsup: int,
         w = np.asarray(particles[:, 3], np.float64)
     for ell in range(lmax + 1):
         for m in range(-ell, ell + 1):
-            a = multipole_fields(delta_hat, ell, m, n, box, edges)
+            a = multipole_fields(delta_hat, ell, m, n, box, edges, vertex=vertex)
             if "node" in forms:
-                zeta["node"][ell] += sum_node(delta, a)
-                cond["node"][ell] += sum_node(np.abs(delta), np.abs(a))
+                zeta["node"][ell] += sum_node(prim, a)
+                cond["node"][ell] += sum_node(np.abs(prim), np.abs(a))
             if "gamma" in forms:
-                zeta["gamma"][ell] += sum_gamma(delta, a, dsup)
+                zeta["gamma"][ell] += sum_gamma(prim, a, dsup)
             if "particle" in forms:
                 f = interpolate(a, pos, n, box, dsup)
                 wsum = float(w.sum())
@@ -413,7 +478,7 @@ def zeta_from_delta(delta, n: int, box: float, edges, lmax: int, dsup: int,
 
 
 def zeta_multipoles(particles, n: int, box: float, edges, lmax: int, dsup: int,
-                    forms=("node",), raw=False):
+                    forms=("node",), raw=False, vertex=None, primary_tophat=0.0):
     """Full pipeline from a catalogue: assign -> contrast -> DFT -> fields -> sums.
 
     raw=True keeps the primary and the fields on n/n_bar (no -1) and drops U,
@@ -423,7 +488,70 @@ def zeta_multipoles(particles, n: int, box: float, edges, lmax: int, dsup: int,
     eps, wsum = assign(particles[:, :3], particles[:, 3], n, box, dsup)
     delta = eps / (wsum / eps.size) if raw else contrast(eps, wsum)
     return zeta_from_delta(delta, n, box, edges, lmax, dsup, forms=forms,
-                           particles=particles, raw_particle=raw)
+                           particles=particles, raw_particle=raw, vertex=vertex, primary_tophat=primary_tophat)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1 and Sec. 3: the 2PCF from the same machinery, the 3PCF in angle, and the
+# reduced 3PCF.
+# ---------------------------------------------------------------------------
+def xi_node(delta, n: int, box: float, edges, vertex=None, primary_tophat=0.0):
+    """2PCF of the grid (Eq. pair-counting with the translated field of Eq. trans-field-FT):
+    xi_b = (1/N_g) sum_l delta_p(l) a_00,b(l), a_00,b the l = 0 field of bin b (whose window is
+    sqrt(4 pi) Y_00 W_0,b = W_0,b, the isotropic shell filter of Eq. DD-windowfunction) and
+    delta_p the primary vertex (smoothed when primary_tophat > 0).  Returns (nbins,)."""
+    delta = np.asarray(delta, np.float64)
+    prim = primary_filter(delta, n, box, primary_tophat) if primary_tophat > 0.0 else delta
+    a = multipole_fields(np.fft.fftn(delta), 0, 0, n, box, edges, vertex=vertex)
+    return (a.reshape(a.shape[0], -1) @ prim.ravel()) / delta.size
+
+
+def xi_particle(particles, n: int, box: float, edges, dsup: int, vertex=None):
+    """2PCF in the particle form: xi_b = (1/W) sum_p w_p f_b(x_p), f_b the B-spline expansion of
+    the l = 0 field of bin b from the particles' own contrast (the primary vertex is the
+    catalogue; the uniform term vanishes because the fields have zero mean).  Returns (nbins,)."""
+    p = np.asarray(particles, np.float64)
+    eps, wsum = assign(p[:, :3], p[:, 3], n, box, dsup)
+    delta = contrast(eps, wsum)
+    a = multipole_fields(np.fft.fftn(delta), 0, 0, n, box, edges, vertex=vertex)
+    f = interpolate(a, p[:, :3], n, box, dsup)
+    return f @ p[:, 3] / wsum
+
+
+def legendre_sum(zeta_l, mu):
+    """zeta(b1, b2, mu) = sum_l zeta_l(b1, b2) P_l(mu), Eq. (triplet-counting); zeta_l of shape
+    (lmax+1, nb, nb), mu a 1-D array -> (len(mu), nb, nb).  P_l by the three-term recurrence."""
+    zeta_l = np.asarray(zeta_l, np.float64)
+    mu = np.asarray(mu, np.float64)
+    out = np.zeros((len(mu),) + zeta_l.shape[1:])
+    p0, p1 = np.ones_like(mu), mu.copy()
+    for ell in range(zeta_l.shape[0]):
+        pl = p0 if ell == 0 else p1
+        out += pl[:, None, None] * zeta_l[ell][None]
+        if ell >= 1:
+            p0, p1 = p1, ((2 * ell + 1) * mu * p1 - ell * p0) / (ell + 1)
+    return out
+
+
+def reduced_q(zeta, xi1, xi2, xi3):
+    """Q = zeta / (xi(r1) xi(r2) + xi(r2) xi(r3) + xi(r3) xi(r1)), Eq. (Q-factor)."""
+    return zeta / (xi1 * xi2 + xi2 * xi3 + xi3 * xi1)
+
+
+def zeta_szapudi_szalay(data, randoms, n: int, box: float, edges, lmax: int, dsup: int, forms=("node",),
+                        vertex=None):
+    """Eq. (SSestimator) in multipoles: the numerator <(D - R)^3> and the denominator <R^3> with D and
+    R each normalised to unit mean density, Delta = delta_D - delta_R and R~ = 1 + delta_R (the SFC
+    difference of Sec. 3), each measured like zeta_from_delta (grid forms).  The estimator is
+    zeta(theta) = sum_l num_l P_l(cos theta) / sum_l den_l P_l(cos theta).  Returns (num, den) dicts."""
+    d = np.asarray(data, np.float64)
+    r = np.asarray(randoms, np.float64)
+    eps_d, w_d = assign(d[:, :3], d[:, 3], n, box, dsup)
+    eps_r, w_r = assign(r[:, :3], r[:, 3], n, box, dsup)
+    dd, dr = contrast(eps_d, w_d), contrast(eps_r, w_r)
+    num, _ = zeta_from_delta(dd - dr, n, box, edges, lmax, dsup, forms=forms, vertex=vertex)
+    den, _ = zeta_from_delta(1.0 + dr, n, box, edges, lmax, dsup, forms=forms, vertex=vertex)
+    return num, den
 
 
 # ---------------------------------------------------------------------------
@@ -514,7 +642,7 @@ def loss(zeta_l, weights):
     return float(np.sum(np.asarray(weights) * np.asarray(zeta_l)))
 
 
-def grad_node_delta(delta, weights, n: int, box: float, edges, lmax: int):
+def grad_node_delta(delta, weights, n: int, box: float, edges, lmax: int, vertex=None):
     """dL/d delta for the node form: (1/N_g) [sum_lm sum S a a + IDFT(sum_lm (-1)^l sum_b K_b DFT(h_b))],
     h_b = 2 delta sum_b' S[b, b'] a_b'."""
     delta = np.asarray(delta, np.float64)
@@ -525,7 +653,7 @@ def grad_node_delta(delta, weights, n: int, box: float, edges, lmax: int):
     for ell in range(lmax + 1):
         s = 0.5 * (weights[ell] + weights[ell].T)
         for m in range(-ell, ell + 1):
-            kern = window_kernel(ell, m, n, box, edges)
+            kern = window_kernel(ell, m, n, box, edges, vertex=vertex)
             a = np.stack([np.fft.ifftn(dh * kern[b]).real for b in range(kern.shape[0])])
             q += np.einsum("ij,ixyz,jxyz->xyz", s, a, a)
             hb = 2.0 * delta[None] * np.einsum("ij,jxyz->ixyz", s, a)
@@ -533,7 +661,7 @@ def grad_node_delta(delta, weights, n: int, box: float, edges, lmax: int):
     return (q + np.fft.ifftn(gk).real) / ng
 
 
-def grad_particle_positions(particles, weights, n: int, box: float, edges, lmax: int, dsup: int):
+def grad_particle_positions(particles, weights, n: int, box: float, edges, lmax: int, dsup: int, vertex=None):
     """dL/dx_p (N_p, 3) for the particle form, with the fields built from the particles' own
     assignment: the direct term through f_b(x_p), plus the term through delta (assignment),
     where dL/d delta = IDFT(sum_lm (-1)^l sum_b K_b DFT(h_b - u_b)), h_b the assignment of
@@ -551,7 +679,7 @@ def grad_particle_positions(particles, weights, n: int, box: float, edges, lmax:
     for ell in range(lmax + 1):
         s = 0.5 * (weights[ell] + weights[ell].T)
         for m in range(-ell, ell + 1):
-            kern = window_kernel(ell, m, n, box, edges)
+            kern = window_kernel(ell, m, n, box, edges, vertex=vertex)
             nb = kern.shape[0]
             a = np.stack([np.fft.ifftn(dh * kern[b]).real for b in range(nb)])
             f = interpolate(a, pos, n, box, dsup)

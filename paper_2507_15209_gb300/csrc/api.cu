@@ -15,7 +15,8 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t delta = 0, dhat = 0, spectra = 0, fields = 0, partials = 0, small = 0, mhist = 0, sorted = 0, tstart = 0,
-         counts = 0, orig = 0, pvals = 0, o_tile = 0, o_cell = 0, o_tq = 0, s_cell = 0, s_tq = 0;
+         counts = 0, orig = 0, pvals = 0, o_tile = 0, o_cell = 0, o_tq = 0, s_cell = 0, s_tq = 0, dprim = 0,
+         xi_radii = 0, dss = 0;
   // backward (gradient) regions
   size_t gk = 0, q = 0, wts = 0, hfield = 0, direct = 0, sidx = 0;
   size_t total = 0;
@@ -23,7 +24,7 @@ struct Layout {
 
 // Workspace regions of the full measurement for np particles (np may be 0); with backward,
 // also the regions of the gradient calls (placed after the forward ones).
-Layout layout(const zeta_ctx* c, int64_t np, bool backward = false) {
+Layout layout(const zeta_ctx* c, int64_t np, bool backward = false, bool ss = false) {
   Layout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -37,6 +38,8 @@ Layout layout(const zeta_ctx* c, int64_t np, bool backward = false) {
   L.spectra = take(g * c->p.nbins);                    // plain half spectra of the C2R passes
   L.fields = take(g * 4 * ((c->p.nbins + 3) / 4));     // bin-interleaved fields; also the assign accumulator
   L.partials = take(sizeof(double) * kMaxCtas * c->p.nbins * c->p.nbins);
+  if (c->p.tophat_primary > 0) L.dprim = take(g);  // the grid forms' smoothed primary vertex
+  L.xi_radii = take(sizeof(double) * 4096);          // radii of zeta_xi_radii
   L.small = take(sizeof(double) * (kAssignScratchDoubles + 8));
   L.mhist = take(sizeof(unsigned long long) * static_cast<size_t>(c->nn2 + 1));  // uniform-term sums per |n|^2
   L.sorted = take(sizeof(float4) * static_cast<size_t>(np));
@@ -58,6 +61,7 @@ Layout layout(const zeta_ctx* c, int64_t np, bool backward = false) {
     L.direct = take(sizeof(float) * 3 * static_cast<size_t>(np));
     L.sidx = take(sizeof(int) * static_cast<size_t>(np));
   }
+  if (ss) L.dss = take(g);  // the random catalogue's grid of the Szapudi-Szalay estimator
   L.total = off;
   return L;
 }
@@ -66,9 +70,9 @@ bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int check_ctx(const zeta_ctx* c) { return c ? ZETA_OK : ZETA_EINVAL; }
 
-int need_ws(const zeta_ctx* c, int64_t np, bool backward = false) {
+int need_ws(const zeta_ctx* c, int64_t np, bool backward = false, bool ss = false) {
   if (!c->ws) return ZETA_EWORKSPACE;
-  if (layout(c, np, backward).total > c->ws_bytes) return ZETA_EWORKSPACE;
+  if (layout(c, np, backward, ss).total > c->ws_bytes) return ZETA_EWORKSPACE;
   return ZETA_OK;
 }
 
@@ -126,18 +130,31 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
   if (!(p->box > 0) || !std::isfinite(p->box)) return ZETA_EINVAL;
   if (p->dsup != 2 && p->dsup != 4) return ZETA_EINVAL;
   if (p->lmax < 0 || p->lmax > kMaxL) return ZETA_EINVAL;
-  if (p->nbins < 1 || p->nbins > kMaxBins || !p->edges) return ZETA_EINVAL;
+  if (p->nbins < 1 || p->nbins > kMaxBins) return ZETA_EINVAL;
   if (p->gram < ZETA_GRAM_FP32 || p->gram > ZETA_GRAM_BF16X3) return ZETA_EINVAL;
-  if (!(p->edges[0] > 0)) return ZETA_EINVAL;
-  for (int b = 0; b < p->nbins; ++b)
-    if (!(p->edges[b + 1] > p->edges[b]) || !std::isfinite(p->edges[b + 1])) return ZETA_EINVAL;
-  if (!(p->edges[p->nbins] < 0.5 * p->box)) return ZETA_EINVAL;
+  if (!(p->tophat >= 0) || !std::isfinite(p->tophat) || !(p->tophat_primary >= 0) ||
+      !std::isfinite(p->tophat_primary) || (p->phi_hat != 0 && p->phi_hat != 1))
+    return ZETA_EINVAL;
+  if (p->radial == ZETA_RADIAL_SHELL) {
+    if (!p->edges || !(p->edges[0] > 0)) return ZETA_EINVAL;
+    for (int b = 0; b < p->nbins; ++b)
+      if (!(p->edges[b + 1] > p->edges[b]) || !std::isfinite(p->edges[b + 1])) return ZETA_EINVAL;
+    if (!(p->edges[p->nbins] < 0.5 * p->box)) return ZETA_EINVAL;
+  } else if (p->radial == ZETA_RADIAL_POINT) {
+    if (!p->radii) return ZETA_EINVAL;
+    for (int b = 0; b < p->nbins; ++b)
+      if (!(p->radii[b] > 0) || !(p->radii[b] < 0.5 * p->box)) return ZETA_EINVAL;
+  } else {
+    return ZETA_EINVAL;
+  }
 
   zeta_ctx* c = new (std::nothrow) zeta_ctx();
   if (!c) return ZETA_ENOMEM;
   c->p = *p;
-  c->edges.assign(p->edges, p->edges + p->nbins + 1);
-  c->p.edges = c->edges.data();
+  if (p->radial == ZETA_RADIAL_SHELL) c->edges.assign(p->edges, p->edges + p->nbins + 1);
+  else c->radii.assign(p->radii, p->radii + p->nbins);
+  c->p.edges = c->edges.empty() ? nullptr : c->edges.data();
+  c->p.radii = c->radii.empty() ? nullptr : c->radii.data();
   c->n = p->n;
   c->nc = p->n / 2;
   c->ng = static_cast<int64_t>(p->n) * p->n * p->n;
@@ -154,11 +171,23 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
     return fail(ZETA_ECUDA);
 
   std::vector<float> jtab;
-  host_jbar_table(p->n, p->box, p->lmax, p->nbins, c->edges.data(), jtab);
+  VertexSpec vs;
+  vs.radial = p->radial;
+  vs.edges = c->p.edges;
+  vs.radii = c->p.radii;
+  vs.tophat = p->tophat;
+  host_window_table(p->n, p->box, p->lmax, p->nbins, vs, jtab);
   std::vector<float2> tw;
   host_twiddles(p->n, tw);
   std::vector<float> mhat;
-  host_mass_hat(p->n, p->dsup, mhat);
+  host_mass_hat(p->n, p->dsup, mhat, p->phi_hat != 0);
+  std::vector<double> ph64;
+  host_phi_hat_1d(p->n, p->dsup, ph64);
+  std::vector<float> phi(p->n, 1.0f);
+  if (p->phi_hat)
+    for (int i = 0; i < p->n; ++i) phi[i] = static_cast<float>(ph64[i]);
+  std::vector<float> wprim;
+  if (p->tophat_primary > 0) host_tophat_table(p->n, p->box, p->tophat_primary, wprim);
   std::vector<double> qt, qw, qb;
   host_cell_quadrature(c->gamma_q, p->dsup, qt, qw, qb);
   std::vector<float> gq;
@@ -170,6 +199,14 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
   if (cudaMalloc(&c->d_mhat, mhat.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
   if (cudaMalloc(&c->d_gq, gq.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
   if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) return fail(ZETA_ENOMEM);
+  if (cudaMalloc(&c->d_phi, phi.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
+  if (cudaMemcpy(c->d_phi, phi.data(), phi.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(ZETA_ECUDA);
+  if (!wprim.empty()) {
+    if (cudaMalloc(&c->d_wprim, wprim.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
+    if (cudaMemcpy(c->d_wprim, wprim.data(), wprim.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(ZETA_ECUDA);
+  }
   if (cudaMemcpy(c->d_jtab, jtab.data(), jtab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_mhat, mhat.data(), mhat.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -191,13 +228,15 @@ int zeta_destroy(zeta_ctx* c) {
   cudaFree(c->d_mhat);
   cudaFree(c->d_gq);
   cudaFree(c->d_status);
+  cudaFree(c->d_phi);
+  cudaFree(c->d_wprim);
   delete c;
   return ZETA_OK;
 }
 
 size_t zeta_workspace_bytes(const zeta_ctx* c, int64_t np_max, int forms) {
-  if (!c || np_max < 0 || np_max > 0x7fffffffLL || forms < 0 || forms > 15) return 0;
-  return layout(c, np_max, (forms & ZETA_WS_BACKWARD) != 0).total;
+  if (!c || np_max < 0 || np_max > 0x7fffffffLL || forms < 0 || forms > 31) return 0;
+  return layout(c, np_max, (forms & ZETA_WS_BACKWARD) != 0, (forms & ZETA_WS_SS) != 0).total;
 }
 
 int zeta_set_workspace(zeta_ctx* c, void* dptr, size_t bytes) {
@@ -342,6 +381,12 @@ int measure(zeta_ctx* c, const float* particles, int64_t np, const float* delta,
   ZK_TRY(launch_r2c(c, dl, dhat, stream));
   unsigned long long* hist = at<unsigned long long>(c, L.mhist);
   if (want_p) ZK_TRY(launch_mass_hist(c, dhat, hist, stream));
+  // the grid forms' primary vertex (smoothed by its tophat, if the context has one)
+  const float* prim = dl;
+  if (c->p.tophat_primary > 0 && (forms & (ZETA_SUM_NODE | ZETA_SUM_GAMMA))) {
+    ZK_TRY(launch_primary(c, dhat, at<float>(c, L.dprim), stream));
+    prim = at<float>(c, L.dprim);
+  }
 
   int nforms = 0, idx_node = -1, idx_gamma = -1, idx_part = -1;
   if (forms & ZETA_SUM_NODE) idx_node = nforms++;
@@ -368,13 +413,13 @@ int measure(zeta_ctx* c, const float* particles, int64_t np, const float* delta,
       if ((l * l + l + m) % lm_size != lm_rank) continue;
       ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, at<float2>(c, L.spectra), fields, stream));
       if (idx_node >= 0) {
-        ZK_TRY(c->p.gram == ZETA_GRAM_FP32 ? launch_gram_node(c, dl, fields, part, stream)
-                                           : launch_gram_node_tc(c, dl, fields, part, stream));
+        ZK_TRY(c->p.gram == ZETA_GRAM_FP32 ? launch_gram_node(c, prim, fields, part, stream)
+                                           : launch_gram_node_tc(c, prim, fields, part, stream));
         ZK_TRY(launch_reduce(c, part, gram_ctas(c, c->p.gram == ZETA_GRAM_FP32 ? GK_NODE : GK_TC), inv_ng, nullptr,
                              out(idx_node, l, m), stream, slots));
       }
       if (idx_gamma >= 0) {
-        ZK_TRY(launch_gram_gamma(c, dl, fields, part, stream));
+        ZK_TRY(launch_gram_gamma(c, prim, fields, part, stream));
         ZK_TRY(launch_reduce(c, part, gram_ctas(c, GK_GAMMA), inv_ng, nullptr, out(idx_gamma, l, m), stream, slots));
       }
       if (idx_part >= 0) {
@@ -395,6 +440,89 @@ extern "C" {
 int zeta_zeta_ell(zeta_ctx* c, const float* particles, int64_t np, const float* delta, int forms, double* zeta,
                   zeta_stream stream) {
   return measure(c, particles, np, delta, forms, 0, 1, false, zeta, stream);
+}
+
+int zeta_xi(zeta_ctx* c, const float* particles, int64_t np, const float* delta, int forms, double* xi,
+            zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!xi || forms < 1 || (forms & ~(ZETA_SUM_NODE | ZETA_SUM_PARTICLE))) return ZETA_EINVAL;
+  const bool want_p = forms & ZETA_SUM_PARTICLE;
+  if ((want_p || !delta) && (!particles || np < 1 || np > 0x7fffffffLL)) return ZETA_EINVAL;
+  const int64_t npl = want_p ? np : 0;
+  ZK_TRY(need_ws(c, npl));
+  const Layout L = layout(c, npl);
+  const int nb = c->p.nbins;
+  const float4* parts = reinterpret_cast<const float4*>(particles);
+  double* small = at<double>(c, L.small);
+  double* wsum = small + kAssignScratchDoubles + 4;
+  float* dl = delta ? const_cast<float*>(delta) : at<float>(c, L.delta);
+  float2* dhat = at<float2>(c, L.dhat);
+  float* fields = at<float>(c, L.fields);
+  double* part = at<double>(c, L.partials);
+  int64_t* tstart = at<int64_t>(c, L.tstart);
+  const PartPrep q = prep_of(c, L);
+  if (want_p) {
+    ZK_TRY(launch_sort(c, parts, np, at<float4>(c, L.sorted), tstart, at<int>(c, L.counts), at<int>(c, L.orig),
+                       stream, nullptr, &q));
+    if (!delta)
+      ZK_TRY(launch_assign_tiles(c, parts, np, tstart, q.s_cell, q.s_tq, dl, wsum, small, stream));
+    else
+      ZK_TRY(launch_wsum(c, parts, np, wsum, small, stream));
+  } else if (!delta) {
+    ZK_TRY(launch_assign(c, parts, np, dl, wsum, reinterpret_cast<unsigned long long*>(fields), small, stream));
+  }
+  ZK_TRY(launch_r2c(c, dl, dhat, stream));
+  int f = 0;
+  if (forms & ZETA_SUM_NODE) {
+    unsigned long long* hist = at<unsigned long long>(c, L.mhist);
+    ZK_TRY(launch_mass_hist(c, dhat, hist, stream, c->d_phi));
+    ZK_TRY(launch_xi_hist(c, hist, nb, nullptr, xi + f * nb, stream));
+    ++f;
+  }
+  if (want_p) {
+    ZK_TRY(launch_alm(c, dhat, 0, 0, 0, nb, at<float2>(c, L.spectra), fields, stream));
+    ZK_TRY(launch_particle_xi(c, q.s_cell, q.s_tq, tstart, np, fields, at<float>(c, L.pvals), part, stream));
+    ZK_TRY(launch_reduce_vec(c, part, gram_particle_parts(c), wsum, xi + f * nb, stream));
+  }
+  return ZETA_OK;
+}
+
+int zeta_zeta_ell_ss(zeta_ctx* c, const float* data, int64_t nd, const float* randoms, int64_t nr, int forms,
+                     double* num, double* den, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!data || !randoms || nd < 1 || nr < 1 || nd > 0x7fffffffLL || nr > 0x7fffffffLL || !num || !den ||
+      forms < 1 || (forms & ~(ZETA_SUM_NODE | ZETA_SUM_GAMMA)))
+    return ZETA_EINVAL;
+  ZK_TRY(need_ws(c, 0, false, true));
+  const Layout L = layout(c, 0, false, true);
+  double* small = at<double>(c, L.small);
+  float* dd = at<float>(c, L.delta);
+  float* dr = at<float>(c, L.dss);
+  unsigned long long* acc = at<unsigned long long>(c, L.fields);
+  double* w = small + kAssignScratchDoubles + 4;
+  ZK_TRY(launch_assign(c, reinterpret_cast<const float4*>(data), nd, dd, w, acc, small, stream));
+  ZK_TRY(launch_assign(c, reinterpret_cast<const float4*>(randoms), nr, dr, w, acc, small, stream));
+  ZK_TRY(launch_ss_fields(c, dd, dr, stream));
+  ZK_TRY(measure(c, nullptr, 0, dd, forms, 0, 1, false, num, stream));
+  return measure(c, nullptr, 0, dr, forms, 0, 1, false, den, stream);
+}
+
+int zeta_xi_radii(zeta_ctx* c, const float* delta_hat, int nr, const double* radii, double* xi, zeta_stream stream) {
+  ZK_TRY(check_ctx(c));
+  if (!delta_hat || !radii || !xi || nr < 1 || nr > 4096) return ZETA_EINVAL;
+  for (int i = 0; i < nr; ++i)
+    if (!(radii[i] >= 0) || !std::isfinite(radii[i])) return ZETA_EINVAL;
+  ZK_TRY(need_ws(c, 0));
+  const Layout L = layout(c, 0);
+  // the radii go to the device through the workspace's small scratch (after the weight sums)
+  double* dr = at<double>(c, L.xi_radii);
+  if (cudaMemcpyAsync(dr, radii, sizeof(double) * nr, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    return ZETA_ECUDA;
+  unsigned long long* hist = at<unsigned long long>(c, L.mhist);
+  ZK_TRY(launch_mass_hist(c, reinterpret_cast<const float2*>(delta_hat), hist, stream, c->d_phi));
+  ZK_TRY(launch_xi_hist(c, hist, nr, dr, xi, stream));
+  // the host array must stay valid until the copy has been read
+  return cudaStreamSynchronize(stream) == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
 int zeta_zeta_lm(zeta_ctx* c, const float* particles, int64_t np, const float* delta, int forms, int lm_rank,
@@ -617,6 +745,7 @@ extern "C" {
 int zeta_backward_node(zeta_ctx* c, const float* delta, const double* weights, float* grad, zeta_stream stream) {
   ZK_TRY(check_ctx(c));
   if (!delta || !weights || !grad) return ZETA_EINVAL;
+  if (c->p.tophat_primary > 0) return ZETA_ENOTSUP;
   ZK_TRY(need_ws(c, 0, true));
   const Layout L = layout(c, 0, true);
   const int nb = c->p.nbins;
@@ -647,6 +776,7 @@ int zeta_backward_particles(zeta_ctx* c, const float* particles, int64_t np, con
                             zeta_stream stream) {
   ZK_TRY(check_ctx(c));
   if (!particles || np < 1 || np > 0x7fffffffLL || !weights || !grad) return ZETA_EINVAL;
+  if (c->p.tophat_primary > 0) return ZETA_ENOTSUP;
   ZK_TRY(need_ws(c, np, true));
   const Layout L = layout(c, np, true);
   const int nb = c->p.nbins;

@@ -267,7 +267,8 @@ struct AlmZ {
 template <int N, int T>
 __global__ void __launch_bounds__(AlmZ<N, T>::NT, AlmZ<N, T>::MINB)
     k_alm_z(const float2* __restrict__ dhat, float2* __restrict__ out, long long fstride, int nf,
-            const float4* __restrict__ jt4, int nbp4, int l, int m, const float2* __restrict__ twg) {
+            const float4* __restrict__ jt4, int nbp4, int l, int m, const float2* __restrict__ twg,
+            const float* __restrict__ phi) {
   constexpr int NC = N / 2;
   constexpr int NT = AlmZ<N, T>::NT;
   constexpr int PPT = AlmZ<N, T>::PPT;
@@ -302,7 +303,9 @@ __global__ void __launch_bounds__(AlmZ<N, T>::NT, AlmZ<N, T>::MINB)
     const bool nyq = (z == N / 2);
     const int row = nyq ? 0 : (nx * nx + ny * ny + nz * nz) * nbp4;
     pn[s * NT + threadIdx.x] = row;
-    const float a = nyq ? 0.f : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz));
+    const float a = nyq ? 0.f
+                        : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz)) *
+                              (__ldg(phi + nx) * __ldg(phi + iy) * __ldg(phi + z));
     pd[s * NT + threadIdx.x] = cscale(dhat[colbase + z * zstride + c], a);
     jn[s] = __ldg(jt4 + row);
   }
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
 template <int N, int T>
 __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
     k_adj_z(const float2* __restrict__ spec, long long fstride, int nf, const float4* __restrict__ jt4, int nbp4,
-            int l, int m, float2* __restrict__ gk, const float2* __restrict__ twg) {
+            int l, int m, float2* __restrict__ gk, const float2* __restrict__ twg, const float* __restrict__ phi) {
   constexpr int NC = N / 2;
   constexpr int NT = RegThreads<N, T, 512>::NT;
   extern __shared__ float2 sm[];
@@ -407,7 +410,9 @@ __global__ void __launch_bounds__(RegThreads<N, T, 512>::NT)
     const int nz = signed_freq(z, N), nx = x0 + c;
     const bool nyq = (z == N / 2);
     n2[idx] = nyq ? 0 : nx * nx + ny * ny + nz * nz;
-    ang[idx] = nyq ? 0.f : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz));
+    ang[idx] = nyq ? 0.f
+                   : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz)) *
+                         (__ldg(phi + nx) * __ldg(phi + iy) * __ldg(phi + z));
     acc[idx] = make_float2(0.f, 0.f);
   }
   __syncthreads();
@@ -504,7 +509,8 @@ int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf
     if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
     const int nbp4 = (c->p.nbins + 3) / 4;
     const float4* jt4 = reinterpret_cast<const float4*>(c->d_jtab) + static_cast<long long>(l) * c->nn2 * nbp4 + b0 / 4;
-    k_alm_z<N, T><<<dim3(NC / T, N), AlmZ<N, T>::NT, smz, s>>>(dhat, spec, fstride, nf, jt4, nbp4, l, m, c->d_tw);
+    k_alm_z<N, T><<<dim3(NC / T, N), AlmZ<N, T>::NT, smz, s>>>(dhat, spec, fstride, nf, jt4, nbp4, l, m, c->d_tw,
+                                                                c->d_phi);
     if (check_launch()) return ZETA_ECUDA;
   }
   {
@@ -585,7 +591,7 @@ int adj_impl(const zeta_ctx* c, const float* fields, int nf, float2* spec, int l
   const int nbp4 = (c->p.nbins + 3) / 4;
   const float4* jt4 = reinterpret_cast<const float4*>(c->d_jtab) + static_cast<long long>(l) * c->nn2 * nbp4;
   k_adj_z<N, TZ><<<dim3(NC / TZ, N), RegThreads<N, TZ, 512>::NT, smz, s>>>(spec, fstride, nf, jt4, nbp4, l, m, gk,
-                                                                          c->d_tw);
+                                                                          c->d_tw, c->d_phi);
   return check_launch();
 }
 
@@ -600,6 +606,35 @@ int launch_c2r_inplace(const zeta_ctx* c, float2* data, int nf, cudaStream_t s) 
 #define ZK_CALL(NN) c2r_full<NN>(c, data, nf, s)
   ZK_DISPATCH_N(c->n, ZK_CALL)
 #undef ZK_CALL
+}
+
+// out = dhat * W(|n|^2) on the stored half spectrum, zero on the Nyquist planes (the table holds
+// the primary-vertex tophat with the 1/N_g of the inverse transform)
+__global__ void k_primary_mul(const float2* __restrict__ dhat, const float* __restrict__ w, int n,
+                              float2* __restrict__ out) {
+  const int nc = n / 2;
+  const long long total = static_cast<long long>(n) * n * nc;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(blockDim.x) * gridDim.x) {
+    const int ix = static_cast<int>(i % nc), iy = static_cast<int>((i / nc) % n),
+              iz = static_cast<int>(i / (static_cast<long long>(nc) * n));
+    float2 v = make_float2(0.f, 0.f);
+    if (iy != n / 2 && iz != n / 2) {
+      const int fy = signed_freq(iy, n), fz = signed_freq(iz, n);
+      v = cscale(dhat[i], __ldg(w + (ix * ix + fy * fy + fz * fz)));
+    }
+    out[i] = v;
+  }
+}
+
+int launch_primary(const zeta_ctx* c, const float2* dhat, float* out, cudaStream_t s) {
+  if (!c->d_wprim) return ZETA_EINVAL;
+  {
+    StageScope prof(c, ST_R2C, 1, s);
+    k_primary_mul<<<c->num_sms * 8, 256, 0, s>>>(dhat, c->d_wprim, c->n, reinterpret_cast<float2*>(out));
+    if (check_launch()) return ZETA_ECUDA;
+  }
+  return launch_c2r_inplace(c, reinterpret_cast<float2*>(out), 1, s);
 }
 
 }  // namespace zk

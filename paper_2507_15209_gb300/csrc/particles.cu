@@ -140,15 +140,17 @@ __device__ __forceinline__ float sum8_scatter(float4 a, int l8) {
   return k;
 }
 
-// The producer's walk over staged (tile, batch, group) items, identical to the consumers'.
+// The producer's walk over staged (tile, batch, group) items, identical to the consumers'; the
+// next tile's particle range is loaded one tile ahead.
 struct ItemWalk {
   TileWalk walk;
   int ngrp, staged_min;
-  long long pk = 0, s0 = 0, s1 = 0, bs = 0;
-  int tx = 0, ty = 0, tz = 0, q = -1;
-  bool valid = false;
+  long long pk = 0, s0 = 0, s1 = 0, bs = 0, n0 = 0, n1 = 0;
+  int tx = 0, ty = 0, tz = 0, q = -1, nx = 0, ny = 0, nz = 0;
+  bool valid = false, have_next = false;
   __device__ __forceinline__ void start() {
     valid = walk.tile(0, s0, s1, tx, ty, tz);
+    have_next = walk.tile(1, n0, n1, nx, ny, nz);
     bs = s0;
   }
   __device__ __forceinline__ void next() {
@@ -160,7 +162,14 @@ struct ItemWalk {
         bs += kPBP;  // batch done (or not staged)
         q = 0;
       } else {
-        valid = walk.tile(++pk, s0, s1, tx, ty, tz);
+        ++pk;
+        valid = have_next;
+        s0 = n0;
+        s1 = n1;
+        tx = nx;
+        ty = ny;
+        tz = nz;
+        have_next = walk.tile(pk + 1, n0, n1, nx, ny, nz);
         bs = s0;
         q = 0;
       }
@@ -262,14 +271,41 @@ __global__ void __launch_bounds__(kIThreads, 3)
   const int lg = __ffs(n) - 1;
   long long ci = 0;
   bool ok = true;
-  long long s0, s1;
-  int tx, ty, tz;
-  for (long long k = 0; walk.tile(k, s0, s1, tx, ty, tz); ++k) {
+  long long s0 = 0, s1 = 0;
+  int tx = 0, ty = 0, tz = 0;
+  // the next tile's particle range and this thread's particle of the next batch are loaded one
+  // step ahead, so their global-memory latency is not on the consumers' critical path
+  long long n0 = 0, n1 = 0;
+  int nx = 0, ny = 0, nz = 0;
+  bool have_next = walk.tile(0, n0, n1, nx, ny, nz);
+  long long pf_bs = -1;
+  int pf_cell = 0;
+  float4 pf_tq = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long k = 0; have_next; ++k) {
+    s0 = n0;
+    s1 = n1;
+    tx = nx;
+    ty = ny;
+    tz = nz;
+    have_next = walk.tile(k + 1, n0, n1, nx, ny, nz);
     for (long long bs = s0; bs < s1; bs += kPBP) {
       const int cnt = static_cast<int>((s1 - bs) < kPBP ? (s1 - bs) : kPBP);
       if (cnt < staged_min) continue;  // k_interp_part_l1 takes this batch
-      if (ct < cnt)
-        particle_setup<D, PW>(s_cell[bs + ct], s_tq[bs + ct], n, lg, tx, ty, tz, true, org[ct], bw + ct * PW);
+      if (ct < cnt) {
+        const bool pre = pf_bs == bs;
+        particle_setup<D, PW>(pre ? pf_cell : s_cell[bs + ct], pre ? pf_tq : s_tq[bs + ct], n, lg, tx, ty, tz,
+                              true, org[ct], bw + ct * PW);
+      }
+      {  // prefetch the next batch (this tile's next one, or the first of the next tile)
+        const bool same = bs + kPBP < s1;
+        const long long nb0 = same ? bs + kPBP : (have_next ? n0 : -1);
+        const long long nend = same ? s1 : n1;
+        pf_bs = nb0;
+        if (nb0 >= 0 && nb0 + ct < nend && ct < kPBP) {
+          pf_cell = s_cell[nb0 + ct];
+          pf_tq = s_tq[nb0 + ct];
+        }
+      }
       consumer_sync();  // setup visible; the previous batch's value rows are written out
       for (int q = 0; q < ngrp; ++q, ++ci) {
         const int s = static_cast<int>(ci % kKS);
@@ -567,9 +603,94 @@ int part_impl(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const in
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
+// Per-CTA sums of w_p f_b(x_p) over the interpolated rows (the particle form of the 2PCF): each
+// thread sums a fixed stride of particles in float32 runs of at most kFlush particles, flushed to
+// float64; the CTA adds its threads in a fixed order.  partials[cta][nb].
+template <int NBP>
+__global__ void __launch_bounds__(kThreads) k_row_sums(const float* __restrict__ pvals, const float4* __restrict__ s_tq,
+                                                       long long np, int nb, double* __restrict__ partials) {
+  __shared__ double red[kThreads];
+  double dacc[NBP];
+  float acc[NBP];
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) {
+    dacc[b] = 0.0;
+    acc[b] = 0.f;
+  }
+  int pending = 0;
+  for (long long p = blockIdx.x * static_cast<long long>(kThreads) + threadIdx.x; p < np;
+       p += static_cast<long long>(kThreads) * gridDim.x) {
+    const float w = __ldg(s_tq + p).w;
+    const float4* row = reinterpret_cast<const float4*>(pvals + p * NBP);
+#pragma unroll
+    for (int j = 0; j < NBP / 4; ++j) {
+      const float4 v = __ldg(row + j);
+      acc[4 * j] = fmaf(w, v.x, acc[4 * j]);
+      acc[4 * j + 1] = fmaf(w, v.y, acc[4 * j + 1]);
+      acc[4 * j + 2] = fmaf(w, v.z, acc[4 * j + 2]);
+      acc[4 * j + 3] = fmaf(w, v.w, acc[4 * j + 3]);
+    }
+    if (++pending == kFlush) {
+#pragma unroll
+      for (int b = 0; b < NBP; ++b) {
+        dacc[b] += acc[b];
+        acc[b] = 0.f;
+      }
+      pending = 0;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) {
+    if (b >= nb) break;  // uniform across the CTA
+    red[threadIdx.x] = dacc[b] + static_cast<double>(acc[b]);
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[static_cast<long long>(blockIdx.x) * nb + b] = red[0];
+    __syncthreads();
+  }
+}
+
+template <int NBP, int D>
+int xi_impl(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int64_t* tile_start, int64_t np,
+            const float* alm, float* pvals, double* partials, cudaStream_t s) {
+  StageScope prof(c, ST_GRAM_PART, part_staged_on(c) + part_l1_on(c) + 1, s);
+  const long long* ts = reinterpret_cast<const long long*>(tile_start);
+  const float4* f4 = reinterpret_cast<const float4*>(alm);
+  if (part_staged_on(c)) {
+    const size_t sm = InterpSmem<NBP, D>::BYTES;
+    if (prep(k_interp_part<NBP, D>, sm)) return ZETA_ECUDA;
+    k_interp_part<NBP, D><<<gram_ctas(c, GK_PART), kIThreads, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n,
+                                                                       c->p.nbins, c->staged_min, pvals, c->d_status);
+  }
+  if (part_l1_on(c)) {
+    const size_t sm = InterpL1Smem<NBP, D>::BYTES;
+    if (prep(k_interp_part_l1<NBP, D>, sm)) return ZETA_ECUDA;
+    k_interp_part_l1<NBP, D><<<c->num_sms, kThreadsL1, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n, c->p.nbins,
+                                                                c->staged_min, pvals);
+  }
+  k_row_sums<NBP><<<c->num_sms * kRowsCtasPerSm, kThreads, 0, s>>>(pvals, s_tq, np, c->p.nbins, partials);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
 }  // namespace
 
 int gram_particle_parts(const zeta_ctx* c) { return c->num_sms * kRowsCtasPerSm; }
+
+int launch_particle_xi(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int64_t* tile_start,
+                       int64_t np, const float* alm, float* pvals, double* partials, cudaStream_t s) {
+  if (c->p.dsup == 2) {
+#define ZK_CALL(P) xi_impl<P, 2>(c, s_cell, s_tq, tile_start, np, alm, pvals, partials, s)
+    ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
+#undef ZK_CALL
+  } else {
+#define ZK_CALL(P) xi_impl<P, 4>(c, s_cell, s_tq, tile_start, np, alm, pvals, partials, s)
+    ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
+#undef ZK_CALL
+  }
+}
 
 size_t particle_rows_bytes(const zeta_ctx* c, int64_t np) {
   return sizeof(float) * static_cast<size_t>(np) * nbp_of(c->p.nbins);

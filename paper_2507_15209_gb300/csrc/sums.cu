@@ -593,6 +593,52 @@ __global__ void k_reduce_lm(const double* __restrict__ slots, int nforms, int pa
   zeta[i] = acc;
 }
 
+// ---------------------------------------------------------------------------------------
+// 2PCF (Eq. pair-counting with Eq. trans-field-FT; Sec. 3 for the windows).  By Parseval the node
+// form (1/N_g) sum_l delta_p(l) a_00,b(l) equals (1/N_g^2) sum_n |delta_hat|^2 Phi-hat(n) W_0,b(k)
+// W_p(k) over the non-Nyquist modes, which depends on the mode only through |n|^2 apart from
+// Phi-hat: so the per-|n|^2 sums H of (1 or 2) |delta_hat|^2 Phi-hat (the fixed-point histogram of
+// the uniform term, with Phi-hat as its per-axis table) give every bin, and any radius, as one
+// sum over the 3 (n/2 - 1)^2 + 1 values of |n|^2.  One CTA per output value; each thread sums
+// a fixed stride of |n|^2 in float64 and the CTA reduces in a fixed order.
+// mode 0: out[b] for the bins, radial factor from the window table (l = 0 row);
+// mode 1: out[i] for radii[i], radial factor j_0(k r_i) W_TH(k rsec).
+__global__ void __launch_bounds__(256) k_xi_hist(const unsigned long long* __restrict__ hist,
+                                                 const unsigned long long* __restrict__ wmax_bits, long long nn2,
+                                                 const float* __restrict__ jt0, int nbp, const float* __restrict__ wprim,
+                                                 double ng, double kunit, const double* __restrict__ radii,
+                                                 double rsec, int mode, double* __restrict__ out) {
+  __shared__ double red[256];
+  const double unit = __longlong_as_double(static_cast<long long>(*wmax_bits)) / kMassUnit;
+  const int o = blockIdx.x;
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < nn2; i += blockDim.x) {
+    const unsigned long long h = hist[i];
+    if (!h) continue;
+    double f;
+    if (mode == 0) {
+      f = static_cast<double>(__ldg(jt0 + i * nbp + o)) * ng * 0.28209479177387814;  // / sqrt(4 pi)
+    } else {
+      const double k = kunit * sqrt(static_cast<double>(i));
+      const double x = k * radii[o];
+      f = x > 0.0 ? sin(x) / x : 1.0;
+      if (rsec > 0.0) {
+        const double y = k * rsec;
+        f *= y > 1e-2 ? 3.0 * (sin(y) - y * cos(y)) / (y * y * y) : 1.0 - y * y / 10.0;
+      }
+    }
+    if (wprim) f *= static_cast<double>(__ldg(wprim + i)) * ng;
+    acc += static_cast<double>(h) * f;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[o] = red[0] * unit / (ng * ng);
+}
+
 template <int NBP>
 size_t smem_node() {
   return NodeRing<NBP>::BYTES;
@@ -675,13 +721,42 @@ int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, d
   }
 }
 
-int launch_mass_hist(const zeta_ctx* c, const float2* dhat, unsigned long long* hist, cudaStream_t s) {
+int launch_mass_hist(const zeta_ctx* c, const float2* dhat, unsigned long long* hist, cudaStream_t s,
+                     const float* table1d) {
   StageScope prof(c, ST_MASS, 2, s);
   // hist[0 .. nn2) the fixed-point sums, hist[nn2] the bits of max w
   if (cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (c->nn2 + 1), s) != cudaSuccess) return ZETA_ECUDA;
   const int grid = c->num_sms * 8;
-  k_mass_max<<<grid, kThreads, 0, s>>>(dhat, c->d_mhat, c->n, hist + c->nn2);
-  k_mass_hist<<<grid, kThreads, 0, s>>>(dhat, c->d_mhat, c->n, hist + c->nn2, hist);
+  const float* t = table1d ? table1d : c->d_mhat;
+  k_mass_max<<<grid, kThreads, 0, s>>>(dhat, t, c->n, hist + c->nn2);
+  k_mass_hist<<<grid, kThreads, 0, s>>>(dhat, t, c->n, hist + c->nn2, hist);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
+// out[b] = (1 / *wdiv) sum_cta partials[cta][b], the CTAs in order (one thread per b).
+__global__ void k_reduce_vec(const double* __restrict__ part, int nparts, int nb, const double* __restrict__ wdiv,
+                             double* __restrict__ out) {
+  const int b = threadIdx.x;
+  if (b >= nb) return;
+  double sum = 0.0;
+  for (int k = 0; k < nparts; ++k) sum += part[static_cast<long long>(k) * nb + b];
+  out[b] = sum / *wdiv;
+}
+
+int launch_reduce_vec(const zeta_ctx* c, const double* partials, int nparts, const double* wdiv, double* out,
+                      cudaStream_t s) {
+  StageScope prof(c, ST_REDUCE, 1, s);
+  k_reduce_vec<<<1, 32, 0, s>>>(partials, nparts, c->p.nbins, wdiv, out);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
+int launch_xi_hist(const zeta_ctx* c, const unsigned long long* hist, int nout, const double* radii, double* out,
+                   cudaStream_t s) {
+  StageScope prof(c, ST_MASS, 1, s);
+  const int nbp = 4 * ((c->p.nbins + 3) / 4);
+  const double kunit = 2.0 * 3.14159265358979323846 / c->p.box;
+  k_xi_hist<<<nout, 256, 0, s>>>(hist, hist + c->nn2, c->nn2, c->d_jtab, nbp, c->d_wprim, static_cast<double>(c->ng),
+                                 kunit, radii, c->p.tophat, radii ? 1 : 0, out);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 

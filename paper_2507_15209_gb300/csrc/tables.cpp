@@ -12,6 +12,10 @@
 //  * B-spline mass (Gram) values M(a) = beta_{2D}(a) and the per-cell Gauss-Legendre
 //    quadrature used by the connection-coefficient sum (Eq. con-coeff), from the explicit
 //    truncated-power form of the centred cardinal B-spline.
+//  * The vertex windows of Sec. 3: the spherical tophat W_TH(kR) = 3 (sin x - x cos x) / x^3
+//    that may multiply every secondary vertex (and smooth the primary one), the point-radius
+//    shell j_l(k r) of Eq. 3PCF-multipole-window, and the basis power spectrum Phi-hat (Fig. 1
+//    step (3)) as a per-axis factor sinc^{2D}(pi n_d / n).
 //  * DFT twiddles.
 #include <cmath>
 #include <thread>
@@ -154,7 +158,21 @@ void host_jbar_values(int l, double box, double r_lo, double r_hi, const int64_t
   }
 }
 
+double tophat_window(double x) {
+  if (std::fabs(x) < 1e-2) {
+    const double x2 = x * x;
+    return 1.0 - x2 / 10.0 + x2 * x2 / 280.0;
+  }
+  return 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x * x);
+}
+
 void host_jbar_table(int n, double box, int lmax, int nbins, const double* edges, std::vector<float>& out) {
+  VertexSpec v;
+  v.edges = edges;
+  host_window_table(n, box, lmax, nbins, v, out);
+}
+
+void host_window_table(int n, double box, int lmax, int nbins, const VertexSpec& v, std::vector<float>& out) {
   const int64_t nn2 = table_n2_count(n);
   const double ng = static_cast<double>(n) * n * n;
   const double pref = std::sqrt(4.0 * kPi) / ng;
@@ -169,12 +187,18 @@ void host_jbar_table(int n, double box, int lmax, int nbins, const double* edges
     double num[kMaxL + 2];
     for (int64_t i = t; i < nn2; i += nth) {
       const double k = 2.0 * kPi / box * std::sqrt(static_cast<double>(i));
+      const double wth = v.tophat > 0.0 ? tophat_window(k * v.tophat) : 1.0;
       for (int b = 0; b < nbins; ++b) {
-        const double r_lo = edges[b], r_hi = edges[b + 1];
-        const double den = (r_hi * r_hi * r_hi - r_lo * r_lo * r_lo) / 3.0;
-        shell_moments(lmax, k, r_lo, r_hi, gx, gw, num);
+        double den = 1.0;
+        if (v.radial == ZETA_RADIAL_POINT) {
+          sph_bessel_all(lmax, k * v.radii[b], num);
+        } else {
+          const double r_lo = v.edges[b], r_hi = v.edges[b + 1];
+          den = (r_hi * r_hi * r_hi - r_lo * r_lo * r_lo) / 3.0;
+          shell_moments(lmax, k, r_lo, r_hi, gx, gw, num);
+        }
         for (int l = 0; l <= lmax; ++l)
-          out[(static_cast<size_t>(l) * nn2 + i) * nbp + b] = static_cast<float>(pref * num[l] / den);
+          out[(static_cast<size_t>(l) * nn2 + i) * nbp + b] = static_cast<float>(pref * wth * num[l] / den);
       }
     }
   };
@@ -226,11 +250,30 @@ static void mass_hat_f64(int n, int dsup, double* out) {
   }
 }
 
-void host_mass_hat(int n, int dsup, std::vector<float>& out) {
-  std::vector<double> v(n);
+void host_mass_hat(int n, int dsup, std::vector<float>& out, bool with_phi) {
+  std::vector<double> v(n), ph;
   mass_hat_f64(n, dsup, v.data());
+  if (with_phi) host_phi_hat_1d(n, dsup, ph);
   out.resize(n);
-  for (int k = 0; k < n; ++k) out[k] = static_cast<float>(v[k]);
+  for (int k = 0; k < n; ++k) out[k] = static_cast<float>(with_phi ? v[k] * ph[k] * ph[k] : v[k]);
+}
+
+void host_phi_hat_1d(int n, int dsup, std::vector<double>& out) {
+  out.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const int f = i < n / 2 ? i : i - n;
+    const double x = kPi * f / n;
+    const double sinc = f == 0 ? 1.0 : std::sin(x) / x;
+    out[i] = std::pow(sinc, 2 * dsup);
+  }
+}
+
+void host_tophat_table(int n, double box, double radius, std::vector<float>& out) {
+  const int64_t nn2 = table_n2_count(n);
+  out.resize(nn2);
+  const double ng = static_cast<double>(n) * n * n;
+  for (int64_t i = 0; i < nn2; ++i)
+    out[i] = static_cast<float>(tophat_window(2.0 * kPi / box * std::sqrt(static_cast<double>(i)) * radius) / ng);
 }
 
 void host_cell_quadrature(int q, int dsup, std::vector<double>& t, std::vector<double>& wq,
@@ -269,6 +312,40 @@ extern "C" int zeta_host_jbar_table(int n, double box, int lmax, int nbins, cons
   std::vector<float> t;
   zk::host_jbar_table(n, box, lmax, nbins, edges, t);
   for (size_t i = 0; i < t.size(); ++i) out[i] = t[i];
+  return ZETA_OK;
+}
+
+extern "C" int zeta_host_window_table(const zeta_params* p, float* out) {
+  if (!p || !out || p->n < 4 || p->n > 512 || (p->n & (p->n - 1)) || !(p->box > 0) || p->lmax < 0 ||
+      p->lmax > zk::kMaxL || p->nbins < 1 || p->nbins > zk::kMaxBins || p->tophat < 0 || !std::isfinite(p->tophat))
+    return ZETA_EINVAL;
+  zk::VertexSpec v;
+  v.radial = p->radial;
+  v.edges = p->edges;
+  v.radii = p->radii;
+  v.tophat = p->tophat;
+  if (p->radial == ZETA_RADIAL_POINT) {
+    if (!p->radii) return ZETA_EINVAL;
+    for (int b = 0; b < p->nbins; ++b)
+      if (!(p->radii[b] > 0) || !std::isfinite(p->radii[b])) return ZETA_EINVAL;
+  } else if (p->radial == ZETA_RADIAL_SHELL) {
+    if (!p->edges || !(p->edges[0] > 0)) return ZETA_EINVAL;
+    for (int b = 0; b < p->nbins; ++b)
+      if (!(p->edges[b + 1] > p->edges[b])) return ZETA_EINVAL;
+  } else {
+    return ZETA_EINVAL;
+  }
+  std::vector<float> t;
+  zk::host_window_table(p->n, p->box, p->lmax, p->nbins, v, t);
+  for (size_t i = 0; i < t.size(); ++i) out[i] = t[i];
+  return ZETA_OK;
+}
+
+extern "C" int zeta_host_phi_hat(int n, int dsup, double* out) {
+  if (n < 2 || n > (1 << 20) || (dsup != 2 && dsup != 4) || !out) return ZETA_EINVAL;
+  std::vector<double> v;
+  zk::host_phi_hat_1d(n, dsup, v);
+  for (int i = 0; i < n; ++i) out[i] = v[i];
   return ZETA_OK;
 }
 
@@ -320,4 +397,33 @@ extern "C" double zeta_host_ylm(int l, int m, double vx, double vy, double vz) {
   }
   const double ang = (m == 0) ? 1.0 : std::sqrt(2.0) * (m > 0 ? cr : ci);
   return qc * ang;
+}
+
+extern "C" int zeta_host_legendre_sum(int lmax, int nb, const double* zeta_l, int nmu, const double* mu, double* out) {
+  if (lmax < 0 || nb < 1 || nmu < 1 || !zeta_l || !mu || !out) return ZETA_EINVAL;
+  const size_t nb2 = static_cast<size_t>(nb) * nb;
+  for (int i = 0; i < nmu; ++i) {
+    if (!(mu[i] >= -1.0 && mu[i] <= 1.0)) return ZETA_EINVAL;
+    double* o = out + i * nb2;
+    for (size_t e = 0; e < nb2; ++e) o[e] = 0.0;
+    double p0 = 1.0, p1 = mu[i];
+    for (int l = 0; l <= lmax; ++l) {
+      const double pl = l == 0 ? p0 : p1;
+      for (size_t e = 0; e < nb2; ++e) o[e] += pl * zeta_l[l * nb2 + e];
+      if (l >= 1) {
+        const double p2 = ((2.0 * l + 1.0) * mu[i] * p1 - l * p0) / (l + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+    }
+  }
+  return ZETA_OK;
+}
+
+extern "C" int zeta_host_reduced_q(int count, const double* zeta, const double* xi1, const double* xi2,
+                                   const double* xi3, double* q) {
+  if (count < 0 || (count && (!zeta || !xi1 || !xi2 || !xi3 || !q))) return ZETA_EINVAL;
+  for (int i = 0; i < count; ++i)
+    q[i] = zeta[i] / (xi1[i] * xi2[i] + xi2[i] * xi3[i] + xi3[i] * xi1[i]);
+  return ZETA_OK;
 }

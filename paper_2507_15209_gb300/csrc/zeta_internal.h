@@ -20,9 +20,23 @@ inline int64_t table_n2_count(int n) {
   const int64_t h = n / 2 - 1;
   return 3 * h * h + 1;
 }
-// sqrt(4 pi) jbar_l(k; b) / N_g for l <= lmax, all n2 < table_n2_count(n), all bins, laid out
-// [l][n2][b] with the bins padded to a multiple of 4 (one float4 gathers four bins).
+// The radial part of the secondary-vertex window: the r^2-weighted shell average over
+// [edges[b], edges[b+1]) or the shell of radius radii[b] itself, times W_TH(k tophat) if tophat > 0.
+struct VertexSpec {
+  int radial = ZETA_RADIAL_SHELL;
+  const double* edges = nullptr;
+  const double* radii = nullptr;
+  double tophat = 0.0;
+};
+// sqrt(4 pi) W_l,b(k) / N_g for l <= lmax, all n2 < table_n2_count(n), all bins, laid out
+// [l][n2][b] with the bins padded to a multiple of 4 (one float4 gathers four bins); W_l,b the
+// radial window of the spec (host_jbar_table: the plain shell average jbar_l(k; b)).
 void host_jbar_table(int n, double box, int lmax, int nbins, const double* edges, std::vector<float>& out);
+void host_window_table(int n, double box, int lmax, int nbins, const VertexSpec& v, std::vector<float>& out);
+// Phi-hat per axis: sinc^{2 dsup}(pi f / n) at DFT index i (signed frequency f), float64.
+void host_phi_hat_1d(int n, int dsup, std::vector<double>& out);
+// W_TH(|k| radius) / N_g by integer |n|^2 < table_n2_count(n) (the primary-vertex tophat).
+void host_tophat_table(int n, double box, double radius, std::vector<float>& out);
 void host_jbar_values(int l, double box, double r_lo, double r_hi, const int64_t* n2, int64_t count,
                       double* out);
 // W_n^e = exp(-2 pi i e / n), e < n, as (cos, sin) pairs rounded to float32.
@@ -31,8 +45,9 @@ void host_twiddles(int n, std::vector<float2>& out);
 void host_ylm_constants(double* mm, double* a, double* b);
 // B-spline Gram values M(a) for |a| < dsup, index a + dsup - 1.
 void host_mass_1d(int dsup, double* out);
-// 1-D DFT of the mass sequence: Mhat(k) = sum_a M(a) cos(2 pi k a / n), k-index < n.
-void host_mass_hat(int n, int dsup, std::vector<float>& out);
+// 1-D DFT of the mass sequence: Mhat(k) = sum_a M(a) cos(2 pi k a / n), k-index < n; with_phi
+// multiplies by the square of the per-axis Phi-hat (the uniform term of Phi-hat-windowed fields).
+void host_mass_hat(int n, int dsup, std::vector<float>& out, bool with_phi = false);
 // Gauss-Legendre nodes/weights on [0, 1] (q points) and the stencil weights
 // beta(t_q + dsup/2 - 1 - o) for o < dsup: wq[q], beta[q * dsup + o].
 void host_cell_quadrature(int q, int dsup, std::vector<double>& t, std::vector<double>& wq,
@@ -73,6 +88,9 @@ struct zeta_ctx {
   float2* d_tw = nullptr;     // W_n^e, e < n
   float* d_mhat = nullptr;    // Mhat(k) for k-index < n
   float* d_gq = nullptr;      // cell quadrature: weights[q] then beta[q*dsup+o]
+  float* d_phi = nullptr;     // Phi-hat per axis by DFT index (all ones without phi_hat)
+  float* d_wprim = nullptr;   // primary-vertex tophat W_TH / N_g by |n|^2 (tophat_primary > 0)
+  std::vector<double> radii;
   int* d_status = nullptr;    // latched device status
   // workspace
   char* ws = nullptr;
@@ -124,6 +142,9 @@ int launch_adj_spectral(const zeta_ctx* c, const float* fields, int nf, float2* 
                         cudaStream_t s);
 // Inverse-only helpers reused by other stages: C2R of nf half spectra in place.
 int launch_c2r_inplace(const zeta_ctx* c, float2* data, int nf, cudaStream_t s);
+// The grid forms' primary vertex smoothed by the tophat: out (float[n^3]) = IDFT[dhat W_TH]
+// (the workspace buffer out holds the intermediate half spectrum).
+int launch_primary(const zeta_ctx* c, const float2* dhat, float* out, cudaStream_t s);
 
 // ---- launchers (assign.cu) ----
 int launch_assign(const zeta_ctx* c, const float4* parts, int64_t np, float* delta, double* wsum,
@@ -145,6 +166,8 @@ struct PartPrep {
 // prepared data of the sorted particles
 int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sorted, int64_t* tile_start,
                 int* counts, int* orig, cudaStream_t s, int* sorted_idx = nullptr, const PartPrep* prep = nullptr);
+// Szapudi-Szalay fields: data_delta <- delta_D - delta_R, rand_delta <- 1 + delta_R
+int launch_ss_fields(const zeta_ctx* c, float* data_delta, float* rand_delta, cudaStream_t s);
 // prepared data of an already sorted catalogue
 int launch_prep_sorted(const zeta_ctx* c, const float4* sorted, int64_t np, int* s_cell, float4* s_tq, cudaStream_t s);
 // assignment from the sorted, prepared catalogue (weight sums, then one CTA per tile writes delta)
@@ -180,7 +203,18 @@ int launch_wait_selftest(const zeta_ctx* c, long long spins, cudaStream_t s);
 // Uniform term of the particle form: launch_mass_hist sums the mode weights of dhat per integer
 // |n|^2 into hist (nn2 + 1 words: the sums, then the scale), once per catalogue; launch_mass
 // writes the per-CTA partial Grams of one l from it.
-int launch_mass_hist(const zeta_ctx* c, const float2* dhat, unsigned long long* hist, cudaStream_t s);
+int launch_mass_hist(const zeta_ctx* c, const float2* dhat, unsigned long long* hist, cudaStream_t s,
+                     const float* table1d = nullptr);
+// 2PCF from a histogram of (1 or 2) |delta_hat|^2 Phi-hat per |n|^2 (launch_mass_hist with c->d_phi):
+// radii == nullptr: out[b] for the bins (nout = nbins); else out[i] at the point radii (device).
+int launch_xi_hist(const zeta_ctx* c, const unsigned long long* hist, int nout, const double* radii, double* out,
+                   cudaStream_t s);
+// out[b] = sum_cta partials[cta][b] / *wdiv (fixed order)
+int launch_reduce_vec(const zeta_ctx* c, const double* partials, int nparts, const double* wdiv, double* out,
+                      cudaStream_t s);
+// Particle form of the 2PCF: interpolated rows of the l = 0 fields, then per-CTA sums of w f_b.
+int launch_particle_xi(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int64_t* tile_start,
+                       int64_t np, const float* alm, float* pvals, double* partials, cudaStream_t s);
 int launch_mass(const zeta_ctx* c, const unsigned long long* hist, int l, double* partials, cudaStream_t s);
 // Number of per-CTA partial Grams launch_gram_particles writes.
 int gram_particle_parts(const zeta_ctx* c);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libzeta.so")
 
 SUM_NODE, SUM_GAMMA, SUM_PARTICLE = 1, 2, 4
 GRAM = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
-FORM_BITS = {"node": SUM_NODE, "gamma": SUM_GAMMA, "particle": SUM_PARTICLE, "backward": 8}
+FORM_BITS = {"node": SUM_NODE, "gamma": SUM_GAMMA, "particle": SUM_PARTICLE, "backward": 8, "ss": 16}
 _ERR = {0: "ok", -1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ETIMEOUT", -5: "ENOTSUP", -6: "EWORKSPACE",
         -7: "EDATA"}
 
@@ -30,7 +30,30 @@ class ZetaError(RuntimeError):
 
 class _Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("box", ctypes.c_double), ("dsup", ctypes.c_int), ("lmax", ctypes.c_int),
-                ("nbins", ctypes.c_int), ("edges", ctypes.POINTER(ctypes.c_double)), ("gram", ctypes.c_int)]
+                ("nbins", ctypes.c_int), ("edges", ctypes.POINTER(ctypes.c_double)), ("gram", ctypes.c_int),
+                ("radial", ctypes.c_int), ("radii", ctypes.POINTER(ctypes.c_double)), ("tophat", ctypes.c_double),
+                ("tophat_primary", ctypes.c_double), ("phi_hat", ctypes.c_int)]
+
+
+RADIAL = {"shell": 0, "point": 1}
+
+
+def make_params(n, box, dsup, lmax, edges=None, gram="fp32", radial="shell", radii=None, tophat=0.0,
+                tophat_primary=0.0, phi_hat=False):
+    """zeta_params from Python values; returns (struct, arrays that must outlive it)."""
+    keep = []
+
+    def arr(x):
+        if x is None:
+            return None
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    nbins = len(radii) if radial == "point" else len(edges) - 1
+    p = _Params(int(n), float(box), int(dsup), int(lmax), int(nbins), arr(edges), GRAM[gram], RADIAL[radial],
+                arr(radii), float(tophat), float(tophat_primary), 1 if phi_hat else 0)
+    return p, keep
 
 
 _lib = None
@@ -75,6 +98,13 @@ _SIGS = {
     "zeta_host_jbar_table": ([_INT, _DBL, _INT, _INT, _VP, _VP], _INT),
     "zeta_host_mass_hat": ([_INT, _INT, _VP], _INT),
     "zeta_host_cell_quadrature": ([_INT, _INT, _VP, _VP, _VP], _INT),
+    "zeta_host_window_table": ([ctypes.POINTER(_Params), _VP], _INT),
+    "zeta_xi": ([_VP, _VP, _I64, _VP, _INT, _VP, _VP], _INT),
+    "zeta_zeta_ell_ss": ([_VP, _VP, _I64, _VP, _I64, _INT, _VP, _VP, _VP], _INT),
+    "zeta_xi_radii": ([_VP, _VP, _INT, _VP, _VP, _VP], _INT),
+    "zeta_host_legendre_sum": ([_INT, _INT, _VP, _INT, _VP, _VP], _INT),
+    "zeta_host_reduced_q": ([_INT, _VP, _VP, _VP, _VP, _VP], _INT),
+    "zeta_host_phi_hat": ([_INT, _INT, _VP], _INT),
 }
 
 
@@ -154,6 +184,28 @@ def assign_noalloc(n: int, box: float, dsup: int, particles, delta=None, wsum=No
                                                             particles.shape[0], _f32(delta, "delta", n ** 3),
                                                             _f64(wsum, "wsum", 1), _stream()))
     return delta, wsum
+
+
+def legendre_sum(zeta_l, mu):
+    """zeta_host_legendre_sum: zeta(b1, b2, mu) = sum_l zeta_l P_l(mu); numpy in, numpy (nmu, nb, nb) out."""
+    z = np.ascontiguousarray(zeta_l, dtype=np.float64)
+    m = np.ascontiguousarray(mu, dtype=np.float64)
+    nb = z.shape[-1]
+    out = np.empty((len(m), nb, nb))
+    _check("zeta_host_legendre_sum", lib().zeta_host_legendre_sum(z.shape[0] - 1, nb, z.ctypes.data_as(ctypes.c_void_p),
+                                                                  len(m), m.ctypes.data_as(ctypes.c_void_p),
+                                                                  out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def reduced_q(zeta, xi1, xi2, xi3):
+    """zeta_host_reduced_q: Q = zeta / (xi1 xi2 + xi2 xi3 + xi3 xi1), element-wise (numpy)."""
+    arrs = [np.ascontiguousarray(np.broadcast_to(a, np.shape(zeta)), dtype=np.float64).ravel()
+            for a in (zeta, xi1, xi2, xi3)]
+    q = np.empty(arrs[0].size)
+    _check("zeta_host_reduced_q", lib().zeta_host_reduced_q(q.size, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
+                                                            q.ctypes.data_as(ctypes.c_void_p)))
+    return q.reshape(np.shape(zeta))
 
 
 def lm_pairs(lm_rank: int, lm_size: int, lmax: int) -> list:
@@ -236,13 +288,16 @@ class Context:
     """A libzeta context with a torch-allocated workspace."""
 
     def __init__(self, n: int, box: float, dsup: int, lmax: int, edges, gram: str = "fp32", np_max: int = 0,
-                 forms=("node",)):
+                 forms=("node",), radial: str = "shell", radii=None, tophat: float = 0.0,
+                 tophat_primary: float = 0.0, phi_hat: bool = False):
+        """edges: bin edges (radial "shell"); radial "point" with radii instead (edges may be None);
+        tophat / tophat_primary / phi_hat: the vertex windows of zeta_params."""
         import torch
         self.n, self.box, self.dsup, self.lmax = int(n), float(box), int(dsup), int(lmax)
-        self.edges = np.ascontiguousarray(edges, dtype=np.float64)
-        self.nbins = len(self.edges) - 1
-        self._edges_c = self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        p = _Params(self.n, self.box, self.dsup, self.lmax, self.nbins, self._edges_c, GRAM[gram])
+        self.edges = None if edges is None else np.ascontiguousarray(edges, dtype=np.float64)
+        p, self._keep = make_params(n, box, dsup, lmax, self.edges, gram, radial, radii, tophat, tophat_primary,
+                                    phi_hat)
+        self.nbins = int(p.nbins)
         h = ctypes.c_void_p()
         _check("zeta_create", lib().zeta_create(ctypes.byref(p), ctypes.byref(h)))
         self._h = h
@@ -365,6 +420,45 @@ class Context:
                                                     _f32(delta, "delta", self.ng), bits,
                                                     _f64(out, "out", len(order) * per), _stream()))
         return {f: out[i] for i, f in enumerate(order)}
+
+    def zeta_ell_ss(self, data, randoms, forms=("node",)):
+        """zeta_zeta_ell_ss: the Szapudi-Szalay numerator and denominator multipoles,
+        ({form: (lmax+1, nb, nb)}, {form: (lmax+1, nb, nb)})."""
+        import torch
+        bits = self.form_bits(forms) & (SUM_NODE | SUM_GAMMA)
+        order = [f for f in ("node", "gamma") if bits & FORM_BITS[f]]
+        shape = (len(order), self.lmax + 1, self.nbins, self.nbins)
+        num = torch.empty(shape, dtype=torch.float64, device="cuda")
+        den = torch.empty(shape, dtype=torch.float64, device="cuda")
+        k = len(order) * (self.lmax + 1) * self.nbins ** 2
+        _check("zeta_zeta_ell_ss", lib().zeta_zeta_ell_ss(self._h, _f32(data, "data", cols=4), data.shape[0],
+                                                          _f32(randoms, "randoms", cols=4), randoms.shape[0], bits,
+                                                          _f64(num, "num", k), _f64(den, "den", k), _stream()))
+        return {f: num[i] for i, f in enumerate(order)}, {f: den[i] for i, f in enumerate(order)}
+
+    def xi(self, particles=None, delta=None, forms=("node",), out=None):
+        """zeta_xi: the 2PCF per bin, {form: tensor (nb,) float64} for the node and particle forms."""
+        import torch
+        bits = self.form_bits(forms) & (SUM_NODE | SUM_PARTICLE)
+        order = [f for f in ("node", "particle") if bits & FORM_BITS[f]]
+        if out is None:
+            out = torch.empty((len(order), self.nbins), dtype=torch.float64, device="cuda")
+        np_ = 0 if particles is None else particles.shape[0]
+        _check("zeta_xi", lib().zeta_xi(self._h, _f32(particles, "particles", cols=4), np_,
+                                        _f32(delta, "delta", self.ng), bits, _f64(out, "out", len(order) * self.nbins),
+                                        _stream()))
+        return {f: out[i] for i, f in enumerate(order)}
+
+    def xi_radii(self, delta_hat, radii, out=None):
+        """zeta_xi_radii: the node-form 2PCF at the given radii (device float64 tensor)."""
+        import torch
+        r = np.ascontiguousarray(radii, dtype=np.float64)
+        if out is None:
+            out = torch.empty(len(r), dtype=torch.float64, device="cuda")
+        _check("zeta_xi_radii", lib().zeta_xi_radii(self._h, _f32(delta_hat, "delta_hat", self.ng), len(r),
+                                                    r.ctypes.data_as(ctypes.c_void_p), _f64(out, "out", len(r)),
+                                                    _stream()))
+        return out
 
     def lm_slots(self, forms=("particle",)) -> int:
         """Number of float64 values in a per-(l, m) slot array (zeta_lm_slots)."""

@@ -146,3 +146,66 @@ def test_host_window_table_matches_oracle(zmod, n, box, lmax, edges):
         for b in range(nb):
             want = pref * O.jbar(ell, k, edges[b], edges[b + 1])
             np.testing.assert_allclose(tab[ell, :, b], want, rtol=1e-6, atol=1e-9 * pref)
+
+
+@pytest.mark.parametrize("vertex", [
+    {"radial": "shell", "tophat": 12.0},
+    {"radial": "point", "radii": [7.5, 19.0, 41.0]},
+    {"radial": "point", "radii": [7.5, 19.0, 41.0], "tophat": 5.0},
+])
+def test_window_table_with_vertex_windows_matches_oracle(zmod, vertex):
+    """The table a context uploads with the vertex windows of Sec. 3 on, every entry against the
+    oracle's radial window: sqrt(4 pi) W_l,b(k) / N_g."""
+    n, box, lmax = 32, 200.0, 6
+    edges = np.array([6.0, 13.0, 22.0, 35.0])
+    p, keep = zmod.make_params(n, box, 4, lmax, edges if vertex["radial"] == "shell" else None,
+                               radial=vertex["radial"], radii=vertex.get("radii"), tophat=vertex.get("tophat", 0.0))
+    nb = p.nbins
+    nbp = 4 * ((nb + 3) // 4)
+    n2max = 3 * (n // 2 - 1) ** 2 + 1
+    out = np.zeros((lmax + 1) * n2max * nbp, np.float32)
+    assert zmod.lib().zeta_host_window_table(ctypes.byref(p), out.ctypes.data_as(ctypes.c_void_p)) == 0
+    out = out.reshape(lmax + 1, n2max, nbp)
+    k = 2 * math.pi / box * np.sqrt(np.arange(n2max, dtype=np.float64))
+    for ell in range(lmax + 1):
+        for b in range(nb):
+            want = math.sqrt(4 * math.pi) * O.radial_window(ell, k, b, edges, vertex) / n ** 3
+            np.testing.assert_allclose(out[ell, :, b], want, rtol=2e-6, atol=1e-7 * np.abs(want).max())
+        np.testing.assert_array_equal(out[ell, :, nb:], 0.0)
+    bad, keep2 = zmod.make_params(n, box, 4, lmax, None, radial="point", radii=[7.5, -1.0])
+    assert zmod.lib().zeta_host_window_table(ctypes.byref(bad), out.ctypes.data_as(ctypes.c_void_p)) == -1
+
+
+@pytest.mark.parametrize("dsup", [2, 4])
+def test_phi_hat_per_axis_matches_oracle(zmod, dsup):
+    n = 24
+    out = np.zeros(n)
+    assert zmod.lib().zeta_host_phi_hat(n, dsup, out.ctypes.data_as(ctypes.c_void_p)) == 0
+    full = O.phi_hat(n, dsup)
+    np.testing.assert_allclose(out, full[0, 0, :], rtol=1e-14)
+    np.testing.assert_allclose(np.multiply.outer(np.multiply.outer(out, out), out), full, rtol=1e-13)
+
+
+def test_create_rejects_bad_vertex_windows(zmod):
+    lib = zmod.lib()
+    edges = np.array([5.0, 10.0, 20.0])
+    for kw in (dict(radial="point", radii=[5.0, 60.0]), dict(radial="point", radii=[0.0, 10.0]),
+               dict(tophat=-1.0), dict(tophat_primary=float("nan"))):
+        p, keep = zmod.make_params(32, 100.0, 4, 2, None if kw.get("radial") == "point" else edges, **kw)
+        h = ctypes.c_void_p()
+        assert lib.zeta_create(ctypes.byref(p), ctypes.byref(h)) == -1, kw
+
+
+def test_legendre_sum_and_reduced_q_match_oracle(zmod):
+    rng = np.random.default_rng(17)
+    zl = rng.standard_normal((9, 3, 3))
+    mu = np.linspace(-1.0, 1.0, 13)
+    np.testing.assert_allclose(zmod.legendre_sum(zl, mu), O.legendre_sum(zl, mu), rtol=1e-13, atol=1e-13)
+    z, x1, x2, x3 = (rng.uniform(0.2, 2.0, 7) for _ in range(4))
+    np.testing.assert_allclose(zmod.reduced_q(z, x1, x2, x3), O.reduced_q(z, x1, x2, x3), rtol=1e-15)
+    # the generating function of the Legendre polynomials, through the library
+    t = 0.45
+    gl = zmod.legendre_sum((t ** np.arange(61))[:, None, None] * np.ones((1, 1, 1)), mu)
+    np.testing.assert_allclose(gl[:, 0, 0], (1 - 2 * mu * t + t * t) ** -0.5, rtol=1e-14)
+    with pytest.raises(zmod.ZetaError):
+        zmod.legendre_sum(zl, [1.5])

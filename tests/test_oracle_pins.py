@@ -253,6 +253,157 @@ def test_triad_closed_form_node_sum():
         np.testing.assert_allclose(zeta["node"][ell], want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
 
 
+# --- vertex windows: tophat, point radius, basis power spectrum, primary tophat ---------------
+def test_tophat_window_is_the_average_over_a_ball():
+    """W_TH(kR) is the mean of exp(i k.x) over the uniform ball of radius R (Monte Carlo)."""
+    rng = np.random.default_rng(31)
+    npts = 400_000
+    v = rng.standard_normal((npts, 3))
+    v *= (rng.random(npts) ** (1.0 / 3.0) / np.linalg.norm(v, axis=1))[:, None]  # uniform in the unit ball
+    for kr in (0.3, 2.0, 4.4934, 7.0):
+        kvec = np.array([0.3, -0.5, 0.8])
+        kvec *= kr / np.linalg.norm(kvec)
+        samples = np.cos(v @ kvec)
+        sem = samples.std() / math.sqrt(npts)
+        assert abs(samples.mean() - float(O.tophat_window(kr))) < 5 * sem + 1e-12, kr
+    assert float(O.tophat_window(0.0)) == 1.0
+    np.testing.assert_allclose(O.tophat_window(np.array([1e-3, 5e-3])),
+                               3 * (np.sin([1e-3, 5e-3]) - np.array([1e-3, 5e-3]) * np.cos([1e-3, 5e-3]))
+                               / np.array([1e-3, 5e-3]) ** 3, rtol=1e-6)
+
+
+def test_point_radius_is_the_thin_shell_limit():
+    """The point-radius window j_l(k r) is the limit of the shell average over [r - e, r + e):
+    the difference falls as e^2."""
+    k = np.array([0.05, 0.31, 0.9])
+    r = 23.0
+    for ell in (0, 1, 4):
+        want = O.radial_window(ell, k, 0, None, {"radial": "point", "radii": [r]})
+        np.testing.assert_allclose(want, special.spherical_jn(ell, k * r), rtol=1e-14)
+        errs = [np.abs(O.jbar(ell, k, r - e, r + e) - want).max() for e in (1.0, 0.5, 0.25)]
+        assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, (ell, errs)
+
+
+@pytest.mark.parametrize("dsup", [2, 4])
+def test_phi_hat_is_the_bspline_power_spectrum(dsup):
+    """Phi-hat(n) = prod_d |beta-hat(2 pi n_d / n)|^2 with beta-hat the continuous Fourier transform of
+    the B-spline (exact Gauss-Legendre quadrature per unit interval)."""
+    n = 16
+    half = dsup // 2
+
+    def bhat(q):
+        return O._unit_interval_quadrature(lambda u: O.bspline(u, dsup) * np.cos(q * u), -half, half, nq=16)
+
+    iv = O.fft_integers(n)
+    one = np.array([bhat(2 * math.pi * f / n) ** 2 for f in iv])
+    want = one[:, None, None] * one[None, :, None] * one[None, None, :]
+    np.testing.assert_allclose(O.phi_hat(n, dsup), want, rtol=1e-12, atol=1e-15)
+
+
+def test_triad_closed_form_with_vertex_windows():
+    """The Fourier-triad closed form with every vertex window on: point radii, a secondary-vertex
+    tophat, Phi-hat and a primary-vertex tophat, node and Gamma forms' primary."""
+    n, box, lmax, dsup = 16, 100.0, 3, 2
+    radii = [13.0, 29.0]
+    rt, rp = 9.0, 6.0
+    vertex = {"radial": "point", "radii": radii, "tophat": rt, "phi_dsup": dsup}
+    modes = [(1, 2, 0), (-3, 1, 2)]
+    modes.append(tuple(-(a + b) for a, b in zip(*modes)))
+    amps, phases = (0.7, 1.1, 0.9), (0.3, -1.2, 2.0)
+    delta = _triad_delta(n, modes, amps, phases)
+    zeta, _ = O.zeta_from_delta(delta, n, box, None, lmax, dsup, forms=("node",), vertex=vertex,
+                                primary_tophat=rp)
+    kv = [2 * math.pi / box * np.array(m, float) for m in modes]
+    s1 = {f: np.sinc(f / n) ** (2 * dsup) for f in range(-n, n)}
+    phi = [s1[m[0]] * s1[m[1]] * s1[m[2]] for m in modes]
+    pref = 2 * np.prod(amps) * math.cos(sum(phases))
+    for ell in range(lmax + 1):
+        want = np.zeros((2, 2))
+        for b1 in range(2):
+            for b2 in range(2):
+                tot = 0.0
+                for a1 in range(3):
+                    for a2 in range(3):
+                        if a1 == a2:
+                            continue
+                        a3 = 3 - a1 - a2
+                        k1, k2, k3 = (np.linalg.norm(kv[a]) for a in (a1, a2, a3))
+                        v1 = special.spherical_jn(ell, k1 * radii[b1]) * O.tophat_window(k1 * rt) * phi[a1]
+                        v2 = special.spherical_jn(ell, k2 * radii[b2]) * O.tophat_window(k2 * rt) * phi[a2]
+                        mu = kv[a1] @ kv[a2] / (k1 * k2)
+                        tot += v1 * v2 * float(O.tophat_window(k3 * rp)) * special.eval_legendre(ell, mu)
+                want[b1, b2] = pref * (-1) ** ell * (2 * ell + 1) * tot
+        np.testing.assert_allclose(zeta["node"][ell], want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
+
+
+# --- 2PCF, angular 3PCF and reduced 3PCF -------------------------------------------------
+def test_xi_of_a_single_mode_is_the_shell_average_of_its_cosine():
+    """For delta = 2A cos(k.x + phi) on the lattice, the node-form 2PCF of bin b is
+    2A^2 jbar_0(|k|; b) (shell average of cos(k.r)); with a point radius 2A^2 j_0(|k| r); a primary
+    and a secondary tophat each multiply by W_TH(|k| R)."""
+    n, box = 16, 80.0
+    edges = np.array([5.0, 11.0, 19.0])
+    mode, amp, ph = (2, -1, 3), 0.8, 0.4
+    lz, ly, lx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    delta = 2 * amp * np.cos(2 * math.pi * (mode[0] * lx + mode[1] * ly + mode[2] * lz) / n + ph)
+    k = 2 * math.pi / box * np.linalg.norm(mode)
+    want = 2 * amp ** 2 * np.array([O.jbar(0, np.array([k]), edges[b], edges[b + 1])[0] for b in range(2)])
+    np.testing.assert_allclose(O.xi_node(delta, n, box, edges), want, rtol=1e-12)
+    v = {"radial": "point", "radii": [7.0, 15.0], "tophat": 4.0}
+    want = 2 * amp ** 2 * special.spherical_jn(0, k * np.array([7.0, 15.0])) * O.tophat_window(k * 4.0) \
+        * O.tophat_window(k * 3.0)
+    np.testing.assert_allclose(O.xi_node(delta, n, box, None, vertex=v, primary_tophat=3.0), want, rtol=1e-12)
+
+
+def test_xi_particle_form_on_nodes_reduces_to_the_node_form():
+    """Hat basis with a particle of weight 1 + delta_l on every node: the particle-form 2PCF is the
+    node-form one plus the mean of the field, which is zero."""
+    n, box = 8, 64.0
+    edges = np.array([9.0, 17.0, 27.0])
+    rng = np.random.default_rng(12)
+    d0 = rng.uniform(-0.7, 0.7, (n, n, n))
+    d0 -= d0.mean()
+    h = box / n
+    lz, ly, lx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    parts = np.stack([lx.ravel() * h, ly.ravel() * h, lz.ravel() * h, (1 + d0).ravel()], 1)
+    np.testing.assert_allclose(O.xi_particle(parts, n, box, edges, 2), O.xi_node(d0, n, box, edges),
+                               rtol=1e-11, atol=1e-14)
+
+
+def test_legendre_sum_generating_function():
+    """sum_l t^l P_l(mu) = (1 - 2 mu t + t^2)^(-1/2): with zeta_l = t^l the resummation is closed."""
+    t, lmax = 0.45, 60
+    mu = np.linspace(-1, 1, 41)
+    zl = (t ** np.arange(lmax + 1))[:, None, None] * np.ones((1, 2, 2))
+    got = O.legendre_sum(zl, mu)
+    want = (1 - 2 * mu * t + t * t) ** -0.5
+    np.testing.assert_allclose(got[:, 0, 1], want, rtol=1e-14)
+
+
+def test_reduced_q_of_a_hierarchical_3pcf():
+    xi1, xi2, xi3 = np.array([0.8]), np.array([0.3]), np.array([1.7])
+    zeta = 1.3 * (xi1 * xi2 + xi2 * xi3 + xi3 * xi1)
+    np.testing.assert_allclose(O.reduced_q(zeta, xi1, xi2, xi3), 1.3, rtol=1e-15)
+
+
+def test_szapudi_szalay_with_lattice_randoms_reduces_to_the_plain_estimator():
+    """Randoms on every node of the lattice (hat basis) have delta_R = 0 exactly, so the numerator
+    is the plain measurement of delta_D and the denominator that of the constant 1 (1 for l = 0, 0
+    above)."""
+    n, box, lmax = 8, 64.0, 2
+    edges = np.array([9.0, 17.0, 27.0])
+    h = box / n
+    lz, ly, lx = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    lattice = np.stack([lx.ravel() * h, ly.ravel() * h, lz.ravel() * h, np.full(n ** 3, 2.5)], 1)
+    data = _small_catalogue(21, n_p=900, box=box)
+    num, den = O.zeta_szapudi_szalay(data, lattice, n, box, edges, lmax, 2, forms=("node", "gamma"))
+    plain, _ = O.zeta_multipoles(data, n, box, edges, lmax, 2, forms=("node", "gamma"))
+    for f in ("node", "gamma"):
+        np.testing.assert_allclose(num[f], plain[f], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(den[f][0], 1.0, rtol=1e-13)
+        np.testing.assert_allclose(den[f][1:], 0.0, atol=1e-13)
+
+
 def test_constant_field_gives_c_cubed():
     n, box = 8, 50.0
     edges = np.array([6.0, 12.0, 20.0])
