@@ -312,28 +312,63 @@ def _events_ms(fn, reps, stream):
 
 
 def _gram_variants(ctx, dev, w, stream):
-    """Node-form Gram per arithmetic on the fields of one (l, m) of this catalogue: ms per
-    launch, speedup over float32, relative Frobenius error against the float32 result."""
+    """Node-form Gram per arithmetic.  On this workload: ms per launch on the fields of one (l, m)
+    and speedup over float32 (tensor-core variants), and the node-form measurement alone in
+    float32 against bfloat16 field storage (seconds per catalogue, relative Frobenius difference).
+    On the 256^3 / 2M-particle workload: each variant's per-l relative error against the FP64
+    oracle's cached result (tests/golden/zeta_box1000_n256_np2m.json)."""
     import torch
+    from paper_2507_15209_gb300.zeta import Context
     nb = ctx.nbins
     delta, _ = ctx.assign(dev)
     dhat = ctx.fft_r2c(delta)
     alm = ctx.reconstruct_alm(dhat, 2, 1)
     out = {}
-    ref = None
     for g in ("fp32", "tf32", "bf16", "bf16x3"):
         ctx.set_gram(g)
         gram = torch.zeros((nb, nb), dtype=torch.float64, device="cuda")
         ms = _events_ms(lambda: ctx.sum_grid(delta, alm, "node", gram=gram), 5, stream)
-        val = ctx.sum_grid(delta, alm, "node").cpu().numpy()
-        if ref is None:
-            ref = val
-        err = float(np.linalg.norm(val - ref) / np.linalg.norm(ref))
-        out[g] = {"ms_per_launch": round(ms, 4), "rel_err_vs_fp32": err}
-    ctx.set_gram("fp32")
+        out[g] = {"ms_per_launch": round(ms, 4)}
+    del alm
     for g in out:
         out[g]["speedup_vs_fp32"] = round(out["fp32"]["ms_per_launch"] / out[g]["ms_per_launch"], 3)
-    del alm
+    node = {}
+    res = {}
+    stage_ms = {}
+    for g in ("fp32", "bf16_fields"):
+        ctx.set_gram(g)
+        node[g] = _events_ms(lambda: ctx.zeta_ell(particles=dev, forms=("node",)), 1, stream) / 1e3
+        ctx.profile_enable(True)
+        res[g] = ctx.zeta_ell(particles=dev, forms=("node",))["node"].cpu().numpy()
+        prof = ctx.profile_read()
+        ctx.profile_enable(False)
+        stage_ms[g] = {k: round(v[0] / max(v[2], 1), 4) for k, v in prof.items()
+                       if k in ("alm_x", "gram_node") and v[1]}
+    ctx.set_gram("fp32")
+    out["node_form_s_per_catalog"] = {g: round(v, 4) for g, v in node.items()}
+    out["node_form_ms_per_call"] = stage_ms
+    out["node_gram_bf16_fields_speedup"] = round(stage_ms["fp32"]["gram_node"] / stage_ms["bf16_fields"]["gram_node"],
+                                                 3)
+    out["node_form_bf16_fields_speedup"] = round(node["fp32"] / node["bf16_fields"], 3)
+    out["node_form_bf16_fields_rel_diff"] = float(np.linalg.norm(res["bf16_fields"] - res["fp32"])
+                                                  / np.linalg.norm(res["fp32"]))
+    gpath = os.path.join(ROOT, "tests", "golden", "zeta_box1000_n256_np2m.json")
+    if os.path.exists(gpath):
+        with open(gpath) as fh:
+            gold = json.load(fh)["data"]
+        w2 = WORKLOADS["box1000_n256_np2m"]
+        parts = mocks.lognormal_catalogue(w2["n"], w2["n_p"], w2["box"], w2["field_seed"], w2["sample_seed"])
+        want = np.array(gold["zeta"]["node"])
+        c2 = Context(w2["n"], w2["box"], w2["dsup"], w2["lmax"], wl_edges(w2), np_max=len(parts), forms=("node",))
+        p2 = torch.from_numpy(parts).cuda()
+        errs = {}
+        for g in ("fp32", "tf32", "bf16", "bf16x3", "bf16_fields"):
+            c2.set_gram(g)
+            got = c2.zeta_ell(particles=p2, forms=("node",))["node"].cpu().numpy()
+            errs[g] = [float(f"{np.linalg.norm(got[l] - want[l]) / np.linalg.norm(want[l]):.2e}")
+                       for l in range(want.shape[0])]
+        c2.close()
+        out["per_l_rel_err_vs_fp64_oracle_box1000_n256"] = errs
     return out
 
 

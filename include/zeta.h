@@ -85,7 +85,13 @@ enum {
   ZETA_GRAM_FP32 = 0,   /* plain float32 FMA, the reference path                    */
   ZETA_GRAM_TF32 = 1,   /* tensor cores, tf32 inputs, fp32 accumulation             */
   ZETA_GRAM_BF16 = 2,   /* tensor cores, bf16 inputs, fp32 accumulation             */
-  ZETA_GRAM_BF16X3 = 3  /* tensor cores, split bf16 (hi*hi + hi*lo + lo*hi)          */
+  ZETA_GRAM_BF16X3 = 3, /* tensor cores, split bf16 (hi*hi + hi*lo + lo*hi)          */
+  ZETA_GRAM_BF16_FIELDS = 4 /* zeta_zeta_ell of the node form alone (nbins <= 20): the last
+                         inverse pass stores the fields as bfloat16 (round to nearest even)
+                         and the float32 Gram reads them, half the field bytes of the
+                         contraction; other forms, or more bins, are refused by zeta_zeta_ell
+                         (ZETA_EINVAL / ZETA_ENOTSUP); zeta_sum_grid on a caller's float32
+                         fields runs the float32 Gram                                   */
 };
 
 /* Radial part of the secondary-vertex windows (Sec. 3 binning, Eq. 3PCF-multipole-window). */

@@ -68,6 +68,9 @@ Layout layout(const zeta_ctx* c, int64_t np, bool backward = false, bool ss = fa
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// the node-form Gram runs on the tensor cores
+bool tc_gram(const zeta_ctx* c) { return c->p.gram >= ZETA_GRAM_TF32 && c->p.gram <= ZETA_GRAM_BF16X3; }
+
 int check_ctx(const zeta_ctx* c) { return c ? ZETA_OK : ZETA_EINVAL; }
 
 int need_ws(const zeta_ctx* c, int64_t np, bool backward = false, bool ss = false) {
@@ -131,7 +134,7 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
   if (p->dsup != 2 && p->dsup != 4) return ZETA_EINVAL;
   if (p->lmax < 0 || p->lmax > kMaxL) return ZETA_EINVAL;
   if (p->nbins < 1 || p->nbins > kMaxBins) return ZETA_EINVAL;
-  if (p->gram < ZETA_GRAM_FP32 || p->gram > ZETA_GRAM_BF16X3) return ZETA_EINVAL;
+  if (p->gram < ZETA_GRAM_FP32 || p->gram > ZETA_GRAM_BF16_FIELDS) return ZETA_EINVAL;
   if (!(p->tophat >= 0) || !std::isfinite(p->tophat) || !(p->tophat_primary >= 0) ||
       !std::isfinite(p->tophat_primary) || (p->phi_hat != 0 && p->phi_hat != 1))
     return ZETA_EINVAL;
@@ -252,7 +255,7 @@ int64_t zeta_tile_count(const zeta_ctx* c) { return c ? c->ntiles : 0; }
 
 int zeta_set_gram(zeta_ctx* c, int gram) {
   ZK_TRY(check_ctx(c));
-  if (gram < ZETA_GRAM_FP32 || gram > ZETA_GRAM_BF16X3) return ZETA_EINVAL;
+  if (gram < ZETA_GRAM_FP32 || gram > ZETA_GRAM_BF16_FIELDS) return ZETA_EINVAL;
   c->p.gram = gram;
   drop_batch_graph(c);
   return ZETA_OK;
@@ -294,11 +297,11 @@ int zeta_sum_grid(zeta_ctx* c, const float* delta, const float* alm, int form, d
   const Layout L = layout(c, 0);
   double* part = at<double>(c, L.partials);
   if (form == ZETA_SUM_NODE)
-    ZK_TRY(c->p.gram == ZETA_GRAM_FP32 ? launch_gram_node(c, delta, alm, part, stream)
-                                       : launch_gram_node_tc(c, delta, alm, part, stream));
+    ZK_TRY(!tc_gram(c) ? launch_gram_node(c, delta, alm, part, stream)
+                       : launch_gram_node_tc(c, delta, alm, part, stream));
   else
     ZK_TRY(launch_gram_gamma(c, delta, alm, part, stream));
-  return launch_reduce(c, part, gram_ctas(c, form == ZETA_SUM_NODE ? (c->p.gram == ZETA_GRAM_FP32 ? GK_NODE : GK_TC) : GK_GAMMA),
+  return launch_reduce(c, part, gram_ctas(c, form == ZETA_SUM_NODE ? (tc_gram(c) ? GK_TC : GK_NODE) : GK_GAMMA),
                        1.0 / static_cast<double>(c->ng), nullptr, gram, stream);
 }
 
@@ -352,6 +355,10 @@ int measure(zeta_ctx* c, const float* particles, int64_t np, const float* delta,
             bool slots, double* zeta, cudaStream_t stream) {
   ZK_TRY(check_ctx(c));
   if (!zeta || forms < 1 || forms > 7 || lm_size < 1 || lm_rank < 0 || lm_rank >= lm_size) return ZETA_EINVAL;
+  // bfloat16 fields serve the node form alone (the other forms interpolate or integrate them)
+  const bool bf16f = c->p.gram == ZETA_GRAM_BF16_FIELDS;
+  if (bf16f && forms != ZETA_SUM_NODE) return ZETA_EINVAL;
+  if (bf16f && c->p.nbins > 20) return ZETA_ENOTSUP;
   const bool want_p = forms & ZETA_SUM_PARTICLE;
   if ((want_p || !delta) && (!particles || np < 1 || np > 0x7fffffffLL)) return ZETA_EINVAL;
   const int64_t npl = want_p ? np : 0;
@@ -411,11 +418,11 @@ int measure(zeta_ctx* c, const float* particles, int64_t np, const float* delta,
     }
     for (int m = -l; m <= l; ++m) {
       if ((l * l + l + m) % lm_size != lm_rank) continue;
-      ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, at<float2>(c, L.spectra), fields, stream));
+      ZK_TRY(launch_alm(c, dhat, l, m, 0, nb, at<float2>(c, L.spectra), fields, stream, bf16f));
       if (idx_node >= 0) {
-        ZK_TRY(c->p.gram == ZETA_GRAM_FP32 ? launch_gram_node(c, prim, fields, part, stream)
-                                           : launch_gram_node_tc(c, prim, fields, part, stream));
-        ZK_TRY(launch_reduce(c, part, gram_ctas(c, c->p.gram == ZETA_GRAM_FP32 ? GK_NODE : GK_TC), inv_ng, nullptr,
+        ZK_TRY(!tc_gram(c) ? launch_gram_node(c, prim, fields, part, stream, bf16f)
+                           : launch_gram_node_tc(c, prim, fields, part, stream));
+        ZK_TRY(launch_reduce(c, part, gram_ctas(c, tc_gram(c) ? GK_TC : GK_NODE), inv_ng, nullptr,
                              out(idx_node, l, m), stream, slots));
       }
       if (idx_gamma >= 0) {
@@ -629,7 +636,7 @@ int zeta_autotune(zeta_ctx* c, const float* particles, int64_t np, int forms, ze
     }
   };
   std::vector<int> kinds;
-  if (forms & ZETA_SUM_NODE) kinds.push_back(c->p.gram == ZETA_GRAM_FP32 ? GK_NODE : GK_TC);
+  if (forms & ZETA_SUM_NODE) kinds.push_back(tc_gram(c) ? GK_TC : GK_NODE);
   if (forms & ZETA_SUM_GAMMA) kinds.push_back(GK_GAMMA);
   if (want_p) {
     kinds.push_back(GK_PART);

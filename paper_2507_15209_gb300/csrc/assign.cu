@@ -295,9 +295,32 @@ __global__ void k_prep_sorted(const float4* __restrict__ sorted, long long np, i
 // fixed-point contribution round(w beta 2^k) by a shared-memory atomic; then the tile writes
 // delta = eps / eps_bar - 1 of its 512 nodes.  No global atomics, and integer sums, so the
 // result does not depend on the order of the particles.  w beta is formed exactly as a pair of
-// float32 (hi + lo, by an FMA) and each part rounded to the fixed point separately, so no float64
-// arithmetic is needed per contribution.
+// float32 (hi + lo, by an FMA) and each part rounded to the fixed point separately with integer
+// instructions (fix64), so no float64 arithmetic is needed per contribution.
 constexpr int kAccPitch = kTile + 1;  // 64-bit words per node row of the tile accumulator
+
+// round(x 2^k) as a 64-bit integer (|x| 2^k < 2^62), ties to even, with integer instructions only
+// (a float -> int64 conversion runs on the float64 pipe, which is narrow on this part): x is
+// m 2^(e - 23) with a 24-bit integer m, so the result is m shifted by e - 23 + k.
+__device__ __forceinline__ long long fix64(float x, int k) {
+  const unsigned int b = __float_as_uint(x);
+  const int ex = static_cast<int>((b >> 23) & 0xffu);
+  if (ex == 0) return 0;  // zero (or a denormal, far below one fixed-point unit here)
+  const long long m = static_cast<long long>((b & 0x7fffffu) | 0x800000u);
+  const int sh = ex - 150 + k;  // x 2^k = m 2^sh
+  long long r;
+  if (sh >= 0) {
+    r = m << sh;
+  } else if (sh <= -25) {
+    r = 0;  // below half a unit
+  } else {
+    const int d = -sh;
+    const long long half = 1LL << (d - 1);
+    const long long q = m >> d, rem = m & ((1LL << d) - 1);
+    r = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+  }
+  return (b >> 31) ? -r : r;
+}
 
 template <int D>
 __global__ void __launch_bounds__(256) k_assign_tiles(const long long* __restrict__ tile_start,
@@ -339,11 +362,14 @@ __global__ void __launch_bounds__(256) k_assign_tiles(const long long* __restric
   }
   __syncthreads();
   const int k2 = ilogb(wstat[2]);  // fixed-point scale 2^k2
-  const int total = nb_pre[27];
+  // one item per (particle, z-layer of its stencil): the heavy particles of the tile itself are
+  // spread over all warps instead of the few that a one-particle-per-thread split would give them
+  const int total = nb_pre[27] * D;
   int k = 0;
   for (int j = threadIdx.x; j < total; j += blockDim.x) {
-    while (j >= nb_pre[k + 1]) ++k;
-    const long long i = nb_s0[k] + (j - nb_pre[k]);
+    const int jp = j / D, oz = j - jp * D;
+    while (jp >= nb_pre[k + 1]) ++k;
+    const long long i = nb_s0[k] + (jp - nb_pre[k]);
     const float4 q = s_tq[i];
     if (q.w == 0.f) continue;
     const int cell = s_cell[i];
@@ -358,30 +384,32 @@ __global__ void __launch_bounds__(256) k_assign_tiles(const long long* __restric
       if (r[d] > mask - (D - 1)) r[d] -= n;  // the stencil starts before the tile
       reach = reach && r[d] + D - 1 >= 0 && r[d] < kTile;
     }
-    if (!reach) continue;
-    float wv[3][D];
-    bspline_weights<D>(q.x, wv[0]);
-    bspline_weights<D>(q.y, wv[1]);
-    bspline_weights<D>(q.z, wv[2]);
-    // the part of the stencil inside the tile, per axis
-    int o0[3], o1[3];
+    const int lz = r[2] + oz;
+    if (!reach || lz < 0 || lz >= kTile) continue;
+    float wx[D], wy[D], wz[D];
+    bspline_weights<D>(q.x, wx);
+    bspline_weights<D>(q.y, wy);
+    bspline_weights<D>(q.z, wz);
+    float wzo = wz[0];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      o0[d] = r[d] < 0 ? -r[d] : 0;
-      o1[d] = kTile - r[d] < D ? kTile - r[d] : D;
-    }
-    for (int oz = o0[2]; oz < o1[2]; ++oz)
-      for (int oy = o0[1]; oy < o1[1]; ++oy) {
-        const float wyz = wv[2][oz] * wv[1][oy];
-        unsigned long long* row = acc + ((r[2] + oz) * kTile + r[1] + oy) * kAccPitch + r[0];
-        for (int ox = o0[0]; ox < o1[0]; ++ox) {
-          const float b = wyz * wv[0][ox];
-          const float hi = q.w * b;
-          const float lo = fmaf(q.w, b, -hi);
-          const long long v = __float2ll_rn(ldexpf(hi, k2)) + __float2ll_rn(ldexpf(lo, k2));
-          atomicAdd(row + ox, static_cast<unsigned long long>(v));
-        }
+    for (int o = 1; o < D; ++o) wzo = oz == o ? wz[o] : wzo;
+#pragma unroll
+    for (int oy = 0; oy < D; ++oy) {
+      const int ly = r[1] + oy;
+      if (ly < 0 || ly >= kTile) continue;
+      const float wyz = wzo * wy[oy];
+      unsigned long long* row = acc + (lz * kTile + ly) * kAccPitch + r[0];
+#pragma unroll
+      for (int ox = 0; ox < D; ++ox) {
+        const int lx = r[0] + ox;
+        if (lx < 0 || lx >= kTile) continue;
+        const float b = wyz * wx[ox];
+        const float hi = q.w * b;
+        const float lo = fmaf(q.w, b, -hi);
+        const long long v = fix64(hi, k2) + fix64(lo, k2);
+        atomicAdd(row + ox, static_cast<unsigned long long>(v));
       }
+    }
   }
   __syncthreads();
   const double w = wstat[0];
@@ -450,6 +478,23 @@ int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sort
   k_tile_order<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, s>>>(
       parts, st, c->ntiles, orig, sorted, sorted_idx, prep ? prep->o_cell : nullptr, prep ? prep->o_tq : nullptr,
       prep ? prep->s_cell : nullptr, prep ? prep->s_tq : nullptr);
+  return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+}
+
+// Szapudi-Szalay fields from the two contrasts: a = delta_D - delta_R (in place of delta_D) and
+// r = 1 + delta_R (in place of delta_R).
+__global__ void k_ss_fields(float* __restrict__ a, float* __restrict__ r, long long ng) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < ng;
+       i += static_cast<long long>(blockDim.x) * gridDim.x) {
+    const float dr = r[i];
+    a[i] = a[i] - dr;
+    r[i] = 1.0f + dr;
+  }
+}
+
+int launch_ss_fields(const zeta_ctx* c, float* data_delta, float* rand_delta, cudaStream_t s) {
+  StageScope prof(c, ST_ASSIGN, 1, s);
+  k_ss_fields<<<grid_for(c->ng, 256, c->num_sms), 256, 0, s>>>(data_delta, rand_delta, c->ng);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 

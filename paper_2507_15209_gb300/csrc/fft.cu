@@ -13,6 +13,8 @@
 // Every pass moves a tile of T contiguous complex columns (or RB rows) between HBM and
 // shared memory with coalesced accesses and transforms it with the radix-8 shared-memory
 // FFT of fft.cuh.
+#include <cuda_bf16.h>
+
 #include "fft.cuh"
 #include "fftreg.cuh"
 #include "zeta_internal.h"
@@ -63,6 +65,12 @@ __device__ __forceinline__ float ylm_dev(int l, int m, float nx, float ny, float
 }
 
 __device__ __forceinline__ int signed_freq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// two floats as a pair of bfloat16 (round to nearest even), the first in the low half
+__device__ __forceinline__ uint32_t bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
 
 // ---------------------------------------------------------------------------------------
 // Threads per CTA of a register-staged transform: eight points per thread, at most MAXT.
@@ -169,7 +177,7 @@ __global__ void __launch_bounds__(256) k_c2r_x(float2* __restrict__ data, long l
 // (X[k] - conj X[NC-k]) (X[NC] = 0) straight from global memory; its outputs z[j] =
 // (x[2j], x[2j+1]) are gathered in shared memory and leave as float4 bin groups.
 // grid (n*n/RB, ngroups); spec holds nf plain half spectra, fstride complex apart.
-template <int N, int RB>
+template <int N, int RB, bool BF16 = false>
 __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
     k_c2r_x4(const float2* __restrict__ spec, long long fstride, int nf, float4* __restrict__ out,
              const float2* __restrict__ twg) {
@@ -238,9 +246,19 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
     const int r = idx / NC, j = idx % NC;
     const float2* src = res + j * PS + r;
     const float2 z0 = src[0], z1 = src[RB], z2 = src[2 * RB], z3 = src[3 * RB];
-    float4* o = out + (static_cast<long long>(g) * N * N + r0 + r) * N + 2 * j;
-    o[0] = make_float4(z0.x, z1.x, z2.x, z3.x);
-    o[1] = make_float4(z0.y, z1.y, z2.y, z3.y);
+    const long long at = (static_cast<long long>(g) * N * N + r0 + r) * N + 2 * j;
+    if constexpr (BF16) {  // four bins of a point as bfloat16 (8 bytes), rounded to nearest even
+      uint4 v;
+      v.x = bf16x2(z0.x, z1.x);
+      v.y = bf16x2(z2.x, z3.x);
+      v.z = bf16x2(z0.y, z1.y);
+      v.w = bf16x2(z2.y, z3.y);
+      *reinterpret_cast<uint4*>(reinterpret_cast<uint2*>(out) + at) = v;
+    } else {
+      float4* o = out + at;
+      o[0] = make_float4(z0.x, z1.x, z2.x, z3.x);
+      o[1] = make_float4(z0.y, z1.y, z2.y, z3.y);
+    }
   }
 }
 
@@ -498,7 +516,7 @@ int c2r_impl(const zeta_ctx* c, float2* data, int nf, cudaStream_t s, bool do_y)
 
 template <int N>
 int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
-             cudaStream_t s) {
+             cudaStream_t s, bool bf16) {
   constexpr int NC = N / 2;
   constexpr int T = kTz < NC ? kTz : NC;
   constexpr int TY = kTy < NC ? kTy : NC;
@@ -523,10 +541,16 @@ int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf
   StageScope prof(c, ST_ALM_X, 1, s);
   constexpr int RB = kRB4;
   size_t smx = x4_smem<N, RB>();
-  if (set_smem(k_c2r_x4<N, RB>, smx)) return ZETA_ECUDA;
   const int ng4 = (nf + 3) / 4;
-  k_c2r_x4<N, RB><<<dim3(N * N / RB, ng4), RegThreads<N / 2, 4 * RB, 256>::NT, smx, s>>>(
-      spec, fstride, nf, reinterpret_cast<float4*>(out), c->d_tw);
+  if (bf16) {
+    if (set_smem(k_c2r_x4<N, RB, true>, smx)) return ZETA_ECUDA;
+    k_c2r_x4<N, RB, true><<<dim3(N * N / RB, ng4), RegThreads<N / 2, 4 * RB, 256>::NT, smx, s>>>(
+        spec, fstride, nf, reinterpret_cast<float4*>(out), c->d_tw);
+  } else {
+    if (set_smem(k_c2r_x4<N, RB>, smx)) return ZETA_ECUDA;
+    k_c2r_x4<N, RB><<<dim3(N * N / RB, ng4), RegThreads<N / 2, 4 * RB, 256>::NT, smx, s>>>(
+        spec, fstride, nf, reinterpret_cast<float4*>(out), c->d_tw);
+  }
   return check_launch();
 }
 
@@ -564,8 +588,8 @@ int launch_r2c(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t
 }
 
 int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
-               cudaStream_t s) {
-#define ZK_CALL(NN) alm_impl<NN>(c, dhat, l, m, b0, nf, spec, out, s)
+               cudaStream_t s, bool bf16) {
+#define ZK_CALL(NN) alm_impl<NN>(c, dhat, l, m, b0, nf, spec, out, s, bf16)
   ZK_DISPATCH_N(c->n, ZK_CALL)
 #undef ZK_CALL
 }

@@ -123,13 +123,14 @@ constexpr int kRbChunk = 256;                    // points per ring slot
 constexpr int kRbSlots = 8;
 constexpr int kRbFlush = 128;                    // points per lane between float64 flushes
 
-template <int NBP>
+template <int NBP, bool BF16 = false>
 struct Tri {
   static constexpr int NP = NBP * (NBP + 1) / 2;
   static constexpr int PARTS = NP > 120 ? 2 : 1;
   static constexpr int NPH = (NP + PARTS - 1) / PARTS;
   static constexpr int G4 = NBP / 4;
-  static constexpr int SLOT = kRbChunk * 4 * (1 + 4 * G4);  // bytes: delta, then G4 runs of float4
+  static constexpr int GB = BF16 ? 8 : 16;  // bytes of one point's bin group
+  static constexpr int SLOT = kRbChunk * (4 + GB * G4);  // bytes: delta, then G4 runs of bin groups
   // pair index k (row-major over b1 <= b2) -> b1, b2
   __host__ __device__ static constexpr int b1_of(int k) {
     int r = 0;
@@ -200,11 +201,11 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
-template <int NBP, int H>
+template <int NBP, int H, bool BF16>
 __device__ __forceinline__ bool rb_consume(const unsigned char* ring, unsigned long long* full,
                                            unsigned long long* empty, long long nmine, int sub, int nsub,
                                            double* drow, int lane) {
-  using T = Tri<NBP>;
+  using T = Tri<NBP, BF16>;
   constexpr int NR = (T::NPH + 31) / 32;
   float acc[T::NPH];
   double dacc[NR];
@@ -222,17 +223,24 @@ __device__ __forceinline__ bool rb_consume(const unsigned char* ring, unsigned l
     }
     const unsigned char* slot = ring + s * T::SLOT;
     const float* dl = reinterpret_cast<const float*>(slot);
-    const float4* g4 = reinterpret_cast<const float4*>(slot + kRbChunk * 4);
     for (int j = sub; j < kRbChunk / 32; j += nsub) {
       const int p = j * 32 + lane;
       float v[NBP];
 #pragma unroll
       for (int q = 0; q < T::G4; ++q) {
-        const float4 x = g4[q * kRbChunk + p];
-        v[4 * q] = x.x;
-        v[4 * q + 1] = x.y;
-        v[4 * q + 2] = x.z;
-        v[4 * q + 3] = x.w;
+        if constexpr (BF16) {  // bfloat16 -> float is a 16-bit shift
+          const uint2 x = reinterpret_cast<const uint2*>(slot + kRbChunk * 4)[q * kRbChunk + p];
+          v[4 * q] = __uint_as_float(x.x << 16);
+          v[4 * q + 1] = __uint_as_float(x.x & 0xffff0000u);
+          v[4 * q + 2] = __uint_as_float(x.y << 16);
+          v[4 * q + 3] = __uint_as_float(x.y & 0xffff0000u);
+        } else {
+          const float4 x = reinterpret_cast<const float4*>(slot + kRbChunk * 4)[q * kRbChunk + p];
+          v[4 * q] = x.x;
+          v[4 * q + 1] = x.y;
+          v[4 * q + 2] = x.z;
+          v[4 * q + 3] = x.w;
+        }
       }
       rb_accum_seq<NBP, H>(acc, v, dl[p], std::make_integer_sequence<int, T::NPH>{});
       if (++pending == kRbFlush) {
@@ -250,11 +258,11 @@ __device__ __forceinline__ bool rb_consume(const unsigned char* ring, unsigned l
   return ok;
 }
 
-template <int NBP>
+template <int NBP, bool BF16>
 __global__ void __launch_bounds__(kRbThreads, 1)
-    k_gram_node_rb(const float* __restrict__ delta, const float4* __restrict__ f4, long long ng, int nb,
+    k_gram_node_rb(const float* __restrict__ delta, const unsigned char* __restrict__ fields, long long ng, int nb,
                    double* __restrict__ partials, int* __restrict__ status) {
-  using T = Tri<NBP>;
+  using T = Tri<NBP, BF16>;
   extern __shared__ __align__(128) unsigned char smq[];
   unsigned char* ring = smq;                                                               // [kRbSlots][SLOT]
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smq + kRbSlots * T::SLOT);
@@ -287,7 +295,8 @@ __global__ void __launch_bounds__(kRbThreads, 1)
         bulk_copy(slot, delta + p0, kRbChunk * 4, &full[s]);
 #pragma unroll
         for (int q = 0; q < T::G4; ++q)
-          bulk_copy(slot + kRbChunk * 4 + q * kRbChunk * 16, f4 + q * ng + p0, kRbChunk * 16, &full[s]);
+          bulk_copy(slot + kRbChunk * 4 + q * kRbChunk * T::GB, fields + (q * ng + p0) * T::GB, kRbChunk * T::GB,
+                    &full[s]);
       }
       if (!ok) atomicOr(status, 2);
       // copies of the last slots may still be landing if the consumers stopped early
@@ -300,9 +309,10 @@ __global__ void __launch_bounds__(kRbThreads, 1)
     const int part = cw % T::PARTS, sub = cw / T::PARTS, nsub = kRbCons / T::PARTS;
     bool ok;
     if (part == 0)
-      ok = rb_consume<NBP, 0>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH, lane);
+      ok = rb_consume<NBP, 0, BF16>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH, lane);
     else
-      ok = rb_consume<NBP, (T::PARTS > 1 ? 1 : 0)>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH, lane);
+      ok = rb_consume<NBP, (T::PARTS > 1 ? 1 : 0), BF16>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH,
+                                                         lane);
     if (!ok && lane == 0) atomicOr(status, 2);
   }
   __syncthreads();
@@ -318,10 +328,10 @@ __global__ void __launch_bounds__(kRbThreads, 1)
   }
 }
 
-template <int NBP>
+template <int NBP, bool BF16>
 constexpr size_t smem_node_rb() {
-  return static_cast<size_t>(kRbSlots) * Tri<NBP>::SLOT + 2 * kRbSlots * sizeof(unsigned long long) +
-         static_cast<size_t>(kRbCons) * Tri<NBP>::NPH * sizeof(double);
+  return static_cast<size_t>(kRbSlots) * Tri<NBP, BF16>::SLOT + 2 * kRbSlots * sizeof(unsigned long long) +
+         static_cast<size_t>(kRbCons) * Tri<NBP, BF16>::NPH * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -657,15 +667,25 @@ size_t smem_gamma() {
 }
 
 template <int NBP>
-int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
+int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s,
+              bool bf16) {
   StageScope prof(c, ST_GRAM_NODE, 1, s);
   if constexpr (NBP <= 20) {
-    const size_t smr = smem_node_rb<NBP>();
-    if (prep(k_gram_node_rb<NBP>, smr)) return ZETA_ECUDA;
-    k_gram_node_rb<NBP><<<gram_ctas(c, GK_NODE), kRbThreads, smr, s>>>(
-        delta, reinterpret_cast<const float4*>(alm), c->ng, c->p.nbins, partials, c->d_status);
+    const unsigned char* f = reinterpret_cast<const unsigned char*>(alm);
+    if (bf16) {
+      const size_t smr = smem_node_rb<NBP, true>();
+      if (prep(k_gram_node_rb<NBP, true>, smr)) return ZETA_ECUDA;
+      k_gram_node_rb<NBP, true><<<gram_ctas(c, GK_NODE), kRbThreads, smr, s>>>(delta, f, c->ng, c->p.nbins, partials,
+                                                                              c->d_status);
+    } else {
+      const size_t smr = smem_node_rb<NBP, false>();
+      if (prep(k_gram_node_rb<NBP, false>, smr)) return ZETA_ECUDA;
+      k_gram_node_rb<NBP, false><<<gram_ctas(c, GK_NODE), kRbThreads, smr, s>>>(delta, f, c->ng, c->p.nbins, partials,
+                                                                               c->d_status);
+    }
     return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
   }
+  if (bf16) return ZETA_ENOTSUP;  // bfloat16 fields only with the register-blocked Gram
   const size_t sm = smem_node<NBP>();
   if (prep(k_gram_node<NBP>, sm)) return ZETA_ECUDA;
   k_gram_node<NBP><<<gram_ctas(c, GK_NODE), kThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
@@ -703,8 +723,9 @@ int gram_ctas(const zeta_ctx* c, int kind) {
   return g > kMaxCtas ? kMaxCtas : g;
 }
 
-int launch_gram_node(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
-#define ZK_CALL(P) node_impl<P>(c, delta, alm, partials, s)
+int launch_gram_node(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s,
+                     bool bf16) {
+#define ZK_CALL(P) node_impl<P>(c, delta, alm, partials, s, bf16)
   ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
 #undef ZK_CALL
 }

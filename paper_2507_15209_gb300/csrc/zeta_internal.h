@@ -134,8 +134,9 @@ int set_ylm_constants();
 int launch_r2c(const zeta_ctx* c, const float* delta, float2* dhat, cudaStream_t s);
 // nf fields of bins b0.. : plain half spectra in spec (nf * n^3/2 complex, scratch), result in out as
 // ceil(nf/4) bin-interleaved groups [g][z][y][x][4].
+// bf16: the groups are written as four bfloat16 per point ([g][z][y][x][4], 8 bytes) instead of float4
 int launch_alm(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
-               cudaStream_t s);
+               cudaStream_t s, bool bf16 = false);
 // Adjoint of the reconstruction for nf bin-interleaved real fields h_b (bins 0..nf-1):
 // gk += sum_b (-1)^l K_lm,b DFT(h_b); spec is scratch for nf half spectra.
 int launch_adj_spectral(const zeta_ctx* c, const float* fields, int nf, float2* spec, int l, int m, float2* gk,
@@ -190,7 +191,8 @@ int launch_adj_finish_particles(const zeta_ctx* c, const float4* parts, int64_t 
 // ---- launchers (sums.cu) ----
 enum GramKind { GK_NODE = 0, GK_PART = 1, GK_GAMMA = 2, GK_MASS = 3, GK_TC = 4 };
 int gram_ctas(const zeta_ctx* c, int kind);
-int launch_gram_node(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
+int launch_gram_node(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s,
+                     bool bf16 = false);
 int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, double* partials,
                       cudaStream_t s);
 int launch_gram_particles(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int64_t* tile_start,

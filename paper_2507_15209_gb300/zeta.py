@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libzeta.so")
 
 SUM_NODE, SUM_GAMMA, SUM_PARTICLE = 1, 2, 4
-GRAM = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
+GRAM = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "bf16_fields": 4}
 FORM_BITS = {"node": SUM_NODE, "gamma": SUM_GAMMA, "particle": SUM_PARTICLE, "backward": 8, "ss": 16}
 _ERR = {0: "ok", -1: "EINVAL", -2: "ECUDA", -3: "ENOMEM", -4: "ETIMEOUT", -5: "ENOTSUP", -6: "EWORKSPACE",
         -7: "EDATA"}
