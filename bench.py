@@ -387,21 +387,30 @@ def _batch_sample(ncat, stream):
     allp = torch.from_numpy(np.concatenate(cats)).cuda()
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     e = wl_edges(w)
-    ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=int(sizes.max()), forms=("particle",))
-    tune = ctx.autotune(allp[: int(sizes[0])], forms=("particle",))
     views = [allp[int(offs[i]):int(offs[i + 1])] for i in range(ncat)]
     out = torch.empty((ncat, 1, w["lmax"] + 1, len(e) - 1, len(e) - 1), dtype=torch.float64, device="cuda")
+    res = {"workload": "batch64_n256", "catalogues": ncat, "particles": int(sizes.sum())}
+    for copies in (1, 2, 3):
+        ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=int(sizes.max()), forms=("particle",),
+                      ws_copies=copies)
+        if copies == 1:
+            res["tuned_ctas_per_sm"] = ctx.autotune(allp[: int(sizes[0])], forms=("particle",))
+            tuned, staging = res["tuned_ctas_per_sm"], ctx.staging()
 
-    def one_by_one():
-        for i in range(ncat):
-            ctx.zeta_ell(particles=views[i], forms=("particle",), out=out[i])
+            def one_by_one():
+                for i in range(ncat):
+                    ctx.zeta_ell(particles=views[i], forms=("particle",), out=out[i])
 
-    ms_seq = _events_ms(one_by_one, 2, stream)
-    ms_batch = _events_ms(lambda: ctx.batch(allp, offs, forms=("particle",), out=out), 2, stream)
-    ctx.close()
-    return {"workload": "batch64_n256", "catalogues": ncat, "particles": int(sizes.sum()),
-            "s_per_catalog_batched": ms_batch / 1e3 / ncat, "s_per_catalog_one_by_one": ms_seq / 1e3 / ncat,
-            "speedup": round(ms_seq / ms_batch, 4), "tuned_ctas_per_sm": tune}
+            ms_seq = _events_ms(one_by_one, 2, stream)
+            res["s_per_catalog_one_by_one"] = ms_seq / 1e3 / ncat
+        else:
+            ctx.set_tuning(tuned)
+            ctx.set_staging(staging)
+        ms_batch = _events_ms(lambda: ctx.batch(allp, offs, forms=("particle",), out=out), 2, stream)
+        res[f"s_per_catalog_batched_{copies}_in_flight"] = ms_batch / 1e3 / ncat
+        res[f"speedup_{copies}_in_flight"] = round(ms_seq / ms_batch, 4)
+        ctx.close()
+    return res
 
 
 def _cufft_reference(w, nb, stages, stream):

@@ -288,7 +288,11 @@ int zeta_backward_particles(zeta_ctx* ctx, const float* particles, int64_t np, c
  * with a single cudaGraphLaunch on `stream`; a later call with the same pointers, forms and
  * offsets relaunches the cached graph.  zeta: device double[ncat * nforms * (lmax+1) * nb * nb]
  * (each catalogue's block as zeta_zeta_ell writes it).  The workspace must cover the largest
- * catalogue.  Changing the workspace or the tuning drops the cached graph. */
+ * catalogue; when it holds k >= 2 whole per-catalogue workspaces (k times
+ * zeta_workspace_bytes(ctx, largest np, forms), k <= 4), k catalogues run concurrently: the
+ * graph forks k streams, and catalogue i runs on stream i mod k in slice i mod k of the
+ * workspace (the catalogues share no data, so their kernels overlap where the GPU has room).
+ * Results do not depend on k.  Changing the workspace or the tuning drops the cached graph. */
 int zeta_batch(zeta_ctx* ctx, const float* particles, const int64_t* offsets, int ncat, int forms, double* zeta,
                zeta_stream stream);
 

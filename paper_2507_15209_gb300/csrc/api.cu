@@ -226,6 +226,11 @@ int zeta_destroy(zeta_ctx* c) {
   profile_release(c);
   if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (int j = 0; j < zeta_ctx::kMaxBatchStreams - 1; ++j) {
+    if (c->cap_aux[j]) cudaStreamDestroy(c->cap_aux[j]);
+    if (c->cap_join[j]) cudaEventDestroy(c->cap_join[j]);
+  }
+  if (c->cap_fork) cudaEventDestroy(c->cap_fork);
   cudaFree(c->d_jtab);
   cudaFree(c->d_tw);
   cudaFree(c->d_mhat);
@@ -560,14 +565,29 @@ int zeta_batch(zeta_ctx* c, const float* particles, const int64_t* offsets, int 
     if (np < 1 || np > 0x7fffffffLL) return ZETA_EINVAL;
     if (np > np_max) np_max = np;
   }
-  ZK_TRY(need_ws(c, (forms & ZETA_SUM_PARTICLE) ? np_max : 0));
+  const int64_t npl = (forms & ZETA_SUM_PARTICLE) ? np_max : 0;
+  ZK_TRY(need_ws(c, npl));
+  // catalogues in flight: as many whole per-catalogue workspaces as the caller's holds (<= 4)
+  const size_t per_ws = layout(c, npl).total;
+  int k = static_cast<int>(c->ws_bytes / per_ws);
+  if (k > zeta_ctx::kMaxBatchStreams) k = zeta_ctx::kMaxBatchStreams;
+  if (k > ncat) k = ncat;
+  if (k < 1) k = 1;
   std::vector<int64_t> key = {static_cast<int64_t>(reinterpret_cast<uintptr_t>(particles)),
-                              static_cast<int64_t>(reinterpret_cast<uintptr_t>(zeta)), forms, ncat};
+                              static_cast<int64_t>(reinterpret_cast<uintptr_t>(zeta)), forms, ncat, k};
   key.insert(key.end(), offsets, offsets + ncat + 1);
   if (!c->batch_exec || key != c->batch_key) {
     drop_batch_graph(c);
     if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
       return ZETA_ECUDA;
+    if (!c->cap_fork && cudaEventCreateWithFlags(&c->cap_fork, cudaEventDisableTiming) != cudaSuccess)
+      return ZETA_ECUDA;
+    for (int j = 0; j < k - 1; ++j) {
+      if (!c->cap_aux[j] && cudaStreamCreateWithFlags(&c->cap_aux[j], cudaStreamNonBlocking) != cudaSuccess)
+        return ZETA_ECUDA;
+      if (!c->cap_join[j] && cudaEventCreateWithFlags(&c->cap_join[j], cudaEventDisableTiming) != cudaSuccess)
+        return ZETA_ECUDA;
+    }
     int nforms = ((forms & 1) ? 1 : 0) + ((forms & 2) ? 1 : 0) + ((forms & 4) ? 1 : 0);
     const size_t per_cat = static_cast<size_t>(nforms) * (c->p.lmax + 1) * c->p.nbins * c->p.nbins;
     c->capturing = true;
@@ -576,12 +596,33 @@ int zeta_batch(zeta_ctx* c, const float* particles, const int64_t* offsets, int 
       return ZETA_ECUDA;
     }
     int rc = ZETA_OK;
-    for (int i = 0; i < ncat && rc == ZETA_OK; ++i)
+    // fork: the auxiliary streams join the capture behind an event of the capturing stream
+    if (k > 1 && cudaEventRecord(c->cap_fork, c->cap_stream) != cudaSuccess) rc = ZETA_ECUDA;
+    for (int j = 0; j < k - 1 && rc == ZETA_OK; ++j)
+      if (cudaStreamWaitEvent(c->cap_aux[j], c->cap_fork, 0) != cudaSuccess) rc = ZETA_ECUDA;
+    // catalogue i runs on stream i mod k in workspace slice i mod k (the launches record the
+    // slice's addresses, so the context's workspace is switched only while capturing)
+    char* const ws0 = c->ws;
+    const size_t ws_bytes0 = c->ws_bytes;
+    for (int i = 0; i < ncat && rc == ZETA_OK; ++i) {
+      const int j = i % k;
+      c->ws = ws0 + j * per_ws;
+      c->ws_bytes = per_ws;
       rc = zeta_zeta_ell(c, particles + 4 * offsets[i], offsets[i + 1] - offsets[i], nullptr, forms,
-                         zeta + i * per_cat, c->cap_stream);
+                         zeta + i * per_cat, j == 0 ? c->cap_stream : c->cap_aux[j - 1]);
+    }
+    c->ws = ws0;
+    c->ws_bytes = ws_bytes0;
+    // join every auxiliary stream back into the capturing stream
+    for (int j = 0; j < k - 1; ++j) {
+      if (cudaEventRecord(c->cap_join[j], c->cap_aux[j]) != cudaSuccess ||
+          cudaStreamWaitEvent(c->cap_stream, c->cap_join[j], 0) != cudaSuccess)
+        rc = rc ? rc : ZETA_ECUDA;
+    }
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &g);
     c->capturing = false;
+    c->batch_streams = k;
     if (rc != ZETA_OK || ec != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return rc != ZETA_OK ? rc : ZETA_ECUDA;

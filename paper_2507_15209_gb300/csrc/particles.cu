@@ -597,9 +597,12 @@ int part_impl(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const in
     k_interp_part_l1<NBP, D><<<c->num_sms, kThreadsL1, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n, c->p.nbins,
                                                                 c->staged_min, pvals);
   }
+  if constexpr (NBP <= 20) {  // register-blocked Gram of the rows (sums.cu), one CTA per SM
+    return launch_gram_rows_rb(c, pvals, s_tq, np, partials, gram_particle_parts(c), s);
+  }
   const size_t sm = smem_rows<NBP>();
   if (prep(k_gram_rows<NBP>, sm)) return ZETA_ECUDA;
-  k_gram_rows<NBP><<<c->num_sms * kRowsCtasPerSm, kThreads, sm, s>>>(pvals, s_tq, np, c->p.nbins, partials);
+  k_gram_rows<NBP><<<gram_particle_parts(c), kThreads, sm, s>>>(pvals, s_tq, np, c->p.nbins, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
@@ -671,13 +674,13 @@ int xi_impl(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int6
     k_interp_part_l1<NBP, D><<<c->num_sms, kThreadsL1, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n, c->p.nbins,
                                                                 c->staged_min, pvals);
   }
-  k_row_sums<NBP><<<c->num_sms * kRowsCtasPerSm, kThreads, 0, s>>>(pvals, s_tq, np, c->p.nbins, partials);
+  k_row_sums<NBP><<<gram_particle_parts(c), kThreads, 0, s>>>(pvals, s_tq, np, c->p.nbins, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
 }  // namespace
 
-int gram_particle_parts(const zeta_ctx* c) { return c->num_sms * kRowsCtasPerSm; }
+int gram_particle_parts(const zeta_ctx* c) { return c->p.nbins <= 20 ? c->num_sms : c->num_sms * kRowsCtasPerSm; }
 
 int launch_particle_xi(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int64_t* tile_start,
                        int64_t np, const float* alm, float* pvals, double* partials, cudaStream_t s) {

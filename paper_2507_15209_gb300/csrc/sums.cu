@@ -123,14 +123,12 @@ constexpr int kRbChunk = 256;                    // points per ring slot
 constexpr int kRbSlots = 8;
 constexpr int kRbFlush = 128;                    // points per lane between float64 flushes
 
-template <int NBP, bool BF16 = false>
+template <int NBP>
 struct Tri {
   static constexpr int NP = NBP * (NBP + 1) / 2;
   static constexpr int PARTS = NP > 120 ? 2 : 1;
   static constexpr int NPH = (NP + PARTS - 1) / PARTS;
   static constexpr int G4 = NBP / 4;
-  static constexpr int GB = BF16 ? 8 : 16;  // bytes of one point's bin group
-  static constexpr int SLOT = kRbChunk * (4 + GB * G4);  // bytes: delta, then G4 runs of bin groups
   // pair index k (row-major over b1 <= b2) -> b1, b2
   __host__ __device__ static constexpr int b1_of(int k) {
     int r = 0;
@@ -201,11 +199,21 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
-template <int NBP, int H, bool BF16>
+// Slot layouts of the register-blocked Gram: MODE 0 node form (delta, then the float4 bin
+// groups), 1 node form on bfloat16 fields (delta, then bfloat16 x 4 groups), 2 particle rows
+// (the float4 (t, w) records, then the rows [particle][NBP]); cnt points in the last chunk.
+template <int NBP, int MODE>
+struct RbLayout {
+  static constexpr int G4 = NBP / 4;
+  static constexpr int SLOT = MODE == 2 ? kRbChunk * (16 + 4 * NBP) : kRbChunk * (4 + (MODE == 1 ? 8 : 16) * G4);
+};
+
+template <int NBP, int H, int MODE>
 __device__ __forceinline__ bool rb_consume(const unsigned char* ring, unsigned long long* full,
                                            unsigned long long* empty, long long nmine, int sub, int nsub,
-                                           double* drow, int lane) {
-  using T = Tri<NBP, BF16>;
+                                           double* drow, int lane, long long ntot, long long c0, long long cstride) {
+  using T = Tri<NBP>;
+  using Lo = RbLayout<NBP, MODE>;
   constexpr int NR = (T::NPH + 31) / 32;
   float acc[T::NPH];
   double dacc[NR];
@@ -221,28 +229,46 @@ __device__ __forceinline__ bool rb_consume(const unsigned char* ring, unsigned l
       ok = false;
       break;
     }
-    const unsigned char* slot = ring + s * T::SLOT;
-    const float* dl = reinterpret_cast<const float*>(slot);
+    const unsigned char* slot = ring + s * Lo::SLOT;
+    const long long left = ntot - (c0 + i * cstride) * kRbChunk;
+    const int cnt = left < kRbChunk ? static_cast<int>(left) : kRbChunk;
     for (int j = sub; j < kRbChunk / 32; j += nsub) {
       const int p = j * 32 + lane;
+      if (j * 32 >= cnt) break;  // warp-uniform
       float v[NBP];
+      float w;
+      if constexpr (MODE == 2) {
+        w = reinterpret_cast<const float4*>(slot)[p].w;
+        const float4* row = reinterpret_cast<const float4*>(slot + kRbChunk * 16) + p * T::G4;
 #pragma unroll
-      for (int q = 0; q < T::G4; ++q) {
-        if constexpr (BF16) {  // bfloat16 -> float is a 16-bit shift
-          const uint2 x = reinterpret_cast<const uint2*>(slot + kRbChunk * 4)[q * kRbChunk + p];
-          v[4 * q] = __uint_as_float(x.x << 16);
-          v[4 * q + 1] = __uint_as_float(x.x & 0xffff0000u);
-          v[4 * q + 2] = __uint_as_float(x.y << 16);
-          v[4 * q + 3] = __uint_as_float(x.y & 0xffff0000u);
-        } else {
-          const float4 x = reinterpret_cast<const float4*>(slot + kRbChunk * 4)[q * kRbChunk + p];
+        for (int q = 0; q < T::G4; ++q) {
+          const float4 x = row[q];
           v[4 * q] = x.x;
           v[4 * q + 1] = x.y;
           v[4 * q + 2] = x.z;
           v[4 * q + 3] = x.w;
         }
+      } else {
+        w = reinterpret_cast<const float*>(slot)[p];
+#pragma unroll
+        for (int q = 0; q < T::G4; ++q) {
+          if constexpr (MODE == 1) {  // bfloat16 -> float is a 16-bit shift
+            const uint2 x = reinterpret_cast<const uint2*>(slot + kRbChunk * 4)[q * kRbChunk + p];
+            v[4 * q] = __uint_as_float(x.x << 16);
+            v[4 * q + 1] = __uint_as_float(x.x & 0xffff0000u);
+            v[4 * q + 2] = __uint_as_float(x.y << 16);
+            v[4 * q + 3] = __uint_as_float(x.y & 0xffff0000u);
+          } else {
+            const float4 x = reinterpret_cast<const float4*>(slot + kRbChunk * 4)[q * kRbChunk + p];
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+          }
+        }
       }
-      rb_accum_seq<NBP, H>(acc, v, dl[p], std::make_integer_sequence<int, T::NPH>{});
+      if (p >= cnt) w = 0.f;  // a ragged last chunk: the slot holds stale (finite) values there
+      rb_accum_seq<NBP, H>(acc, v, w, std::make_integer_sequence<int, T::NPH>{});
       if (++pending == kRbFlush) {
         rb_flush<NBP>(acc, dacc, lane);
         pending = 0;
@@ -258,14 +284,17 @@ __device__ __forceinline__ bool rb_consume(const unsigned char* ring, unsigned l
   return ok;
 }
 
-template <int NBP, bool BF16>
+// MODE 0/1: node form over ng grid points (delta, fields); MODE 2: weighted Gram of the particle
+// rows over ng = np particles (delta = the prepared float4 records as floats, fields = the rows).
+template <int NBP, int MODE>
 __global__ void __launch_bounds__(kRbThreads, 1)
     k_gram_node_rb(const float* __restrict__ delta, const unsigned char* __restrict__ fields, long long ng, int nb,
                    double* __restrict__ partials, int* __restrict__ status) {
-  using T = Tri<NBP, BF16>;
+  using T = Tri<NBP>;
+  using Lo = RbLayout<NBP, MODE>;
   extern __shared__ __align__(128) unsigned char smq[];
   unsigned char* ring = smq;                                                               // [kRbSlots][SLOT]
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(smq + kRbSlots * T::SLOT);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smq + kRbSlots * Lo::SLOT);
   unsigned long long* empty = full + kRbSlots;
   double* dsum = reinterpret_cast<double*>(empty + kRbSlots);                             // [kRbCons][NPH]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -278,7 +307,7 @@ __global__ void __launch_bounds__(kRbThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const long long nchunk = ng / kRbChunk;
+  const long long nchunk = (ng + kRbChunk - 1) / kRbChunk;
   const long long nmine = nchunk > blockIdx.x ? (nchunk - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   if (warp == 0) {  // ---- producer
     bool ok = true;
@@ -290,13 +319,21 @@ __global__ void __launch_bounds__(kRbThreads, 1)
           break;
         }
         const long long p0 = (blockIdx.x + i * gridDim.x) * static_cast<long long>(kRbChunk);
-        unsigned char* slot = ring + s * T::SLOT;
-        mbar_expect_tx(&full[s], T::SLOT);
-        bulk_copy(slot, delta + p0, kRbChunk * 4, &full[s]);
+        unsigned char* slot = ring + s * Lo::SLOT;
+        if constexpr (MODE == 2) {  // a ragged last chunk copies only its particles
+          const long long left = ng - p0;
+          const uint32_t cnt = static_cast<uint32_t>(left < kRbChunk ? left : kRbChunk);
+          mbar_expect_tx(&full[s], cnt * (16 + 4 * NBP));
+          bulk_copy(slot, delta + 4 * p0, cnt * 16, &full[s]);
+          bulk_copy(slot + kRbChunk * 16, fields + p0 * 4 * NBP, cnt * 4 * NBP, &full[s]);
+        } else {
+          constexpr int GB = MODE == 1 ? 8 : 16;
+          mbar_expect_tx(&full[s], Lo::SLOT);
+          bulk_copy(slot, delta + p0, kRbChunk * 4, &full[s]);
 #pragma unroll
-        for (int q = 0; q < T::G4; ++q)
-          bulk_copy(slot + kRbChunk * 4 + q * kRbChunk * T::GB, fields + (q * ng + p0) * T::GB, kRbChunk * T::GB,
-                    &full[s]);
+          for (int q = 0; q < T::G4; ++q)
+            bulk_copy(slot + kRbChunk * 4 + q * kRbChunk * GB, fields + (q * ng + p0) * GB, kRbChunk * GB, &full[s]);
+        }
       }
       if (!ok) atomicOr(status, 2);
       // copies of the last slots may still be landing if the consumers stopped early
@@ -309,10 +346,11 @@ __global__ void __launch_bounds__(kRbThreads, 1)
     const int part = cw % T::PARTS, sub = cw / T::PARTS, nsub = kRbCons / T::PARTS;
     bool ok;
     if (part == 0)
-      ok = rb_consume<NBP, 0, BF16>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH, lane);
+      ok = rb_consume<NBP, 0, MODE>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH, lane, ng, blockIdx.x,
+                                    gridDim.x);
     else
-      ok = rb_consume<NBP, (T::PARTS > 1 ? 1 : 0), BF16>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH,
-                                                         lane);
+      ok = rb_consume<NBP, (T::PARTS > 1 ? 1 : 0), MODE>(ring, full, empty, nmine, sub, nsub, dsum + cw * T::NPH,
+                                                         lane, ng, blockIdx.x, gridDim.x);
     if (!ok && lane == 0) atomicOr(status, 2);
   }
   __syncthreads();
@@ -328,10 +366,10 @@ __global__ void __launch_bounds__(kRbThreads, 1)
   }
 }
 
-template <int NBP, bool BF16>
+template <int NBP, int MODE>
 constexpr size_t smem_node_rb() {
-  return static_cast<size_t>(kRbSlots) * Tri<NBP, BF16>::SLOT + 2 * kRbSlots * sizeof(unsigned long long) +
-         static_cast<size_t>(kRbCons) * Tri<NBP, BF16>::NPH * sizeof(double);
+  return static_cast<size_t>(kRbSlots) * RbLayout<NBP, MODE>::SLOT + 2 * kRbSlots * sizeof(unsigned long long) +
+         static_cast<size_t>(kRbCons) * Tri<NBP>::NPH * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -673,15 +711,15 @@ int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* p
   if constexpr (NBP <= 20) {
     const unsigned char* f = reinterpret_cast<const unsigned char*>(alm);
     if (bf16) {
-      const size_t smr = smem_node_rb<NBP, true>();
-      if (prep(k_gram_node_rb<NBP, true>, smr)) return ZETA_ECUDA;
-      k_gram_node_rb<NBP, true><<<gram_ctas(c, GK_NODE), kRbThreads, smr, s>>>(delta, f, c->ng, c->p.nbins, partials,
-                                                                              c->d_status);
+      const size_t smr = smem_node_rb<NBP, 1>();
+      if (prep(k_gram_node_rb<NBP, 1>, smr)) return ZETA_ECUDA;
+      k_gram_node_rb<NBP, 1><<<gram_ctas(c, GK_NODE), kRbThreads, smr, s>>>(delta, f, c->ng, c->p.nbins, partials,
+                                                                           c->d_status);
     } else {
-      const size_t smr = smem_node_rb<NBP, false>();
-      if (prep(k_gram_node_rb<NBP, false>, smr)) return ZETA_ECUDA;
-      k_gram_node_rb<NBP, false><<<gram_ctas(c, GK_NODE), kRbThreads, smr, s>>>(delta, f, c->ng, c->p.nbins, partials,
-                                                                               c->d_status);
+      const size_t smr = smem_node_rb<NBP, 0>();
+      if (prep(k_gram_node_rb<NBP, 0>, smr)) return ZETA_ECUDA;
+      k_gram_node_rb<NBP, 0><<<gram_ctas(c, GK_NODE), kRbThreads, smr, s>>>(delta, f, c->ng, c->p.nbins, partials,
+                                                                           c->d_status);
     }
     return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
   }
@@ -714,7 +752,28 @@ int mass_impl(const zeta_ctx* c, const unsigned long long* hist, int l, double* 
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
+template <int NBP>
+int rows_rb_impl(const zeta_ctx* c, const float* pvals, const float4* s_tq, int64_t np, double* partials, int grid,
+                 cudaStream_t s) {
+  if constexpr (NBP <= 20) {
+    const size_t smr = smem_node_rb<NBP, 2>();
+    if (prep(k_gram_node_rb<NBP, 2>, smr)) return ZETA_ECUDA;
+    k_gram_node_rb<NBP, 2><<<grid, kRbThreads, smr, s>>>(reinterpret_cast<const float*>(s_tq),
+                                                         reinterpret_cast<const unsigned char*>(pvals), np,
+                                                         c->p.nbins, partials, c->d_status);
+    return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
+  }
+  return ZETA_ENOTSUP;
+}
+
 }  // namespace
+
+int launch_gram_rows_rb(const zeta_ctx* c, const float* pvals, const float4* s_tq, int64_t np, double* partials,
+                        int grid, cudaStream_t s) {
+#define ZK_CALL(P) rows_rb_impl<P>(c, pvals, s_tq, np, partials, grid, s)
+  ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
+#undef ZK_CALL
+}
 
 int gram_ctas(const zeta_ctx* c, int kind) {
   int per = c->tune[kind];

@@ -101,9 +101,15 @@ struct zeta_ctx {
   // particle Gram: batches with at least this many particles stage their tile's halo in
   // shared memory; sparser ones gather from global memory
   int staged_min = 0;
-  // CUDA graph of the last batch (zeta_batch)
+  // CUDA graph of the last batch (zeta_batch); up to kMaxBatchStreams catalogues in flight, on
+  // cap_stream and the auxiliary streams forked from it inside the capture
+  static constexpr int kMaxBatchStreams = 4;
   bool capturing = false;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_aux[kMaxBatchStreams - 1] = {};
+  cudaEvent_t cap_fork = nullptr;
+  cudaEvent_t cap_join[kMaxBatchStreams - 1] = {};
+  int batch_streams = 1;
   cudaGraphExec_t batch_exec = nullptr;
   std::vector<int64_t> batch_key;
 };
@@ -218,6 +224,10 @@ int launch_reduce_vec(const zeta_ctx* c, const double* partials, int nparts, con
 int launch_particle_xi(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int64_t* tile_start,
                        int64_t np, const float* alm, float* pvals, double* partials, cudaStream_t s);
 int launch_mass(const zeta_ctx* c, const unsigned long long* hist, int l, double* partials, cudaStream_t s);
+// Weighted Gram of the interpolated particle rows ([np][bins padded to 4]) with the weights of the
+// prepared records, register-blocked (<= 20 bins; ZETA_ENOTSUP above): grid CTAs, partials[grid].
+int launch_gram_rows_rb(const zeta_ctx* c, const float* pvals, const float4* s_tq, int64_t np, double* partials,
+                        int grid, cudaStream_t s);
 // Number of per-CTA partial Grams launch_gram_particles writes.
 int gram_particle_parts(const zeta_ctx* c);
 // out[b1][b2] += scale * (1/ *wdiv if wdiv) * sum_cta partials[cta][b1][b2], symmetrised.

@@ -54,6 +54,30 @@ def test_batch_equals_one_by_one_and_replays(Z):
             assert err < 1e-5, (f, l, err)
 
 
+@pytest.mark.parametrize("copies", [2, 3])
+def test_concurrent_batch_equals_one_by_one(Z, copies):
+    """With room for several per-catalogue workspaces the batch graph runs catalogues on forked
+    streams; every catalogue's result is still bit-identical to zeta_ell's."""
+    n, box, lmax, dsup = 32, 200.0, 3, 4
+    edges = np.linspace(10.0, 70.0, 6)
+    sizes = mocks.batch_sizes(7, 800, 9000, 78)
+    cats = _cats(n, box, sizes, 700)
+    allp = torch.from_numpy(np.concatenate(cats)).to("cuda")
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    forms = ("node", "particle")
+    ctx = Z.Context(n, box, dsup, lmax, edges, np_max=int(sizes.max()), forms=forms, ws_copies=copies)
+    out = ctx.batch(allp, offs, forms=forms)
+    replay = ctx.batch(allp, offs, forms=forms, out=out.clone())
+    torch.cuda.synchronize()
+    assert ctx.get_status() == 0
+    for i, p in enumerate(cats):
+        one = ctx.zeta_ell(particles=torch.from_numpy(p).to("cuda"), forms=forms)
+        for k, f in enumerate(forms):
+            np.testing.assert_array_equal(out[i, k].cpu().numpy(), one[f].cpu().numpy())
+            np.testing.assert_array_equal(replay[i, k].cpu().numpy(), one[f].cpu().numpy())
+    ctx.close()
+
+
 def test_autotune_keeps_results(Z):
     n, box, lmax, dsup = 32, 200.0, 2, 4
     edges = np.linspace(10.0, 70.0, 5)
