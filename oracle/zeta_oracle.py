@@ -32,6 +32,12 @@ listed in the design notes):
       by delta = n/n_bar - 1: zeta = (1/W) sum_p w_p sum_m f_b1 f_b2 - U, where
       U = (1/V) int sum_m f_b1 f_b2 dx is the "-1" (uniform) term.
   R8  No self-triplet or shot-noise subtraction (the paper's formulas have none).
+  R9  dsup = 3 selects the Daubechies scaling function of genus 4 (four filter taps,
+      support [0, 3]; Sec. 2.2 and the runtime benchmark of Sec. 3).  It is known only
+      through its two-scale relation phi(x) = sqrt2 sum_k h_k phi(2x - k): its point values
+      are the exact dyadic values of level DAUB_LEVEL = 10 joined linearly (what a cascade
+      table of that level holds), while its mass and connection coefficients and its
+      Fourier transform are those of phi itself, solved from the same relation.
 
 Parity pins of each function live in tests/test_oracle_pins.py; none of the
 functions below is unpinned.
@@ -44,7 +50,8 @@ import numpy as np
 from scipy import special
 
 __all__ = [
-    "bspline", "stencil_base", "assign", "contrast", "fft_integers", "nyquist_mask",
+    "bspline", "daub4_filter", "daub4_dyadic", "daub4_phi", "daub4_power", "daub4_mass", "daub4_gamma",
+    "basis", "stencil_base", "assign", "contrast", "fft_integers", "nyquist_mask",
     "jbar", "real_ylm", "tophat_window", "phi_hat", "radial_window", "primary_filter", "window_kernel", "multipole_fields", "sum_node",
     "gamma_1d", "mass_1d", "sum_gamma", "interpolate", "sum_particles",
     "mass_term", "mass_term_fourier", "zeta_multipoles", "xi_node", "xi_particle", "legendre_sum", "reduced_q",
@@ -71,15 +78,139 @@ def bspline(u, dsup: int):
     raise ValueError("dsup must be 2 or 4")
 
 
+# ---------------------------------------------------------------------------
+# The Daubechies scaling function of genus D_g = 4 (Sec. 2.2: support D_sup = D_g - 1 = 3;
+# the basis of the paper's runs), selected by dsup = 3 (reading R9).
+# ---------------------------------------------------------------------------
+DAUB_LEVEL = 10
+_SQRT2 = math.sqrt(2.0)
+_DYADIC = {}
+
+
+def daub4_filter():
+    """Low-pass taps h_0..h_3 of the genus-4 Daubechies filter: (1+s, 3+s, 3-s, 1-s) / (4 sqrt2), s = sqrt3."""
+    s3 = math.sqrt(3.0)
+    return np.array([1.0 + s3, 3.0 + s3, 3.0 - s3, 1.0 - s3]) / (4.0 * _SQRT2)
+
+
+def daub4_dyadic(level: int = DAUB_LEVEL):
+    """phi(k / 2^level) for k = 0 .. 3 * 2^level, from the two-scale relation.
+
+    Level 0: phi(0) = phi(3) = 0, and (phi(1), phi(2)) is the eigenvector of eigenvalue 1 of the
+    relation restricted to the integers, scaled to sum 1 (partition of unity).  Level j+1: the
+    even points are those of level j; an odd point k / 2^(j+1) takes
+    phi = sqrt2 sum_i h_i phi(k / 2^j - i), whose arguments are points of level j.
+    """
+    if level not in _DYADIC:
+        h = daub4_filter()
+        t = _SQRT2 * np.array([[h[1], h[0]], [h[3], h[2]]])
+        ev, vec = np.linalg.eig(t)
+        v = vec[:, int(np.argmin(np.abs(ev - 1.0)))].real
+        v = v / v.sum()
+        vals = np.array([0.0, v[0], v[1], 0.0])
+        for j in range(level):
+            m = 3 * 2 ** (j + 1)
+            new = np.zeros(m + 1)
+            new[0::2] = vals
+            odd = np.arange(1, m, 2)
+            for i, hi in enumerate(h):
+                src = odd - i * 2 ** j  # level-j index of k / 2^j - i
+                ok = (src >= 0) & (src <= 3 * 2 ** j)
+                new[odd[ok]] += _SQRT2 * hi * vals[src[ok]]
+            vals = new
+        _DYADIC[level] = vals
+    return _DYADIC[level]
+
+
+def daub4_phi(u, level: int = DAUB_LEVEL):
+    """phi(u): the dyadic values of the given level joined linearly, zero outside [0, 3] (R9)."""
+    tab = daub4_dyadic(level)
+    x = np.arange(tab.size, dtype=np.float64) / 2.0 ** level
+    return np.interp(np.asarray(u, np.float64), x, tab, left=0.0, right=0.0)
+
+
+def daub4_power(omega):
+    """|phi-hat(omega)|^2 = prod_{j >= 1} |m0(omega / 2^j)|^2 with m0(w) = (1/sqrt2) sum_k h_k e^{-i k w}
+    (the Fourier transform of the two-scale relation); the factors left once |omega| / 2^j < 1e-6
+    differ from 1 by less than 1e-22 (m0 has two vanishing moments)."""
+    h = daub4_filter()
+    w = np.asarray(omega, np.float64) / 2.0
+    out = np.ones_like(w)
+    while w.size and np.max(np.abs(w)) > 1e-6:
+        m0 = sum(hk * np.exp(-1j * k * w) for k, hk in enumerate(h)) / _SQRT2
+        out = out * np.abs(m0) ** 2
+        w = w / 2.0
+    return out
+
+
+def _two_scale_solve(offsets, rows, norm_rows, norm_rhs):
+    """Least-squares solution of (T - I) x = 0 stacked with the normalisation rows."""
+    idx = {o: i for i, o in enumerate(offsets)}
+    a = np.zeros((len(offsets), len(offsets)))
+    for o in offsets:
+        for o2, c in rows(o):
+            if o2 in idx:
+                a[idx[o], idx[o2]] += c
+        a[idx[o], idx[o]] -= 1.0
+    lhs = np.vstack([a, norm_rows(idx)])
+    rhs = np.concatenate([np.zeros(len(offsets)), norm_rhs])
+    x, *_ = np.linalg.lstsq(lhs, rhs, rcond=None)
+    return {o: float(x[idx[o]]) for o in offsets}
+
+
+def daub4_mass():
+    """M(a) = int phi(x) phi(x - a) dx for |a| <= 2, from M(a) = sum_{i,j} h_i h_j M(2a + j - i)
+    (substitute the two-scale relation twice) and sum_a M(a) = int phi = 1."""
+    h = daub4_filter()
+    offs = list(range(-2, 3))
+
+    def rows(a):
+        return [(2 * a + j - i, h[i] * h[j]) for i in range(4) for j in range(4)]
+
+    return _two_scale_solve(offs, rows, lambda idx: np.ones((1, len(offs))), np.array([1.0]))
+
+
+def daub4_gamma():
+    """Gamma(a, b) = int phi(x) phi(x - a) phi(x - b) dx (Eq. con-coeff in 1-D) for the 23 pairs
+    whose supports overlap, from Gamma(a, b) = sqrt2 sum_{i,j,k} h_i h_j h_k
+    Gamma(2a + j - i, 2b + k - i) and sum_b Gamma(a, b) = M(a) (partition of unity)."""
+    h = daub4_filter()
+    offs = [(a, b) for a in range(-2, 3) for b in range(-2, 3) if abs(a - b) < 3]
+    mass = daub4_mass()
+
+    def rows(ab):
+        a, b = ab
+        return [((2 * a + j - i, 2 * b + k - i), _SQRT2 * h[i] * h[j] * h[k])
+                for i in range(4) for j in range(4) for k in range(4)]
+
+    def norm_rows(idx):
+        out = np.zeros((5, len(offs)))
+        for (a, b), i in idx.items():
+            out[a + 2, i] = 1.0
+        return out
+
+    return _two_scale_solve(offs, rows, norm_rows, np.array([mass[a] for a in range(-2, 3)]))
+
+
+def basis(u, dsup: int):
+    """The scaling function of the basis: beta_D for dsup 2 or 4, the Daubechies phi for dsup 3."""
+    if dsup == 3:
+        return daub4_phi(u)
+    return bspline(u, dsup)
+
+
 def stencil_base(u, dsup: int):
-    """First node of the dsup-point stencil around grid coordinate u."""
+    """First node of the stencil of grid coordinate u: the dsup nodes l with basis(u - l) != 0
+    (centred B-splines: floor(u) - (dsup/2 - 1); Daubechies, support [0, 3]: floor(u) - 2)."""
+    if dsup == 3:
+        return np.floor(u).astype(np.int64) - 2
     return np.floor(u).astype(np.int64) - (dsup // 2 - 1)
 
 
 def assign(pos, w, n: int, box: float, dsup: int):
     """SFCs of the point process, Sec. 2.1 and Fig. 1 step (2) (reading R6).
 
-    eps_l = sum_p w_p prod_d beta(u_pd - l_d), periodic in l; u = x / H.
+    eps_l = sum_p w_p prod_d phi(u_pd - l_d), periodic in l; u = x / H; phi the basis function.
     Returns (eps[z, y, x], W = sum_p w_p).
     """
     pos = np.asarray(pos, np.float64)
@@ -89,13 +220,13 @@ def assign(pos, w, n: int, box: float, dsup: int):
     eps = np.zeros(n ** 3)
     for oz in range(dsup):
         lz = base[:, 2] + oz
-        bz = bspline(u[:, 2] - lz, dsup)
+        bz = basis(u[:, 2] - lz, dsup)
         for oy in range(dsup):
             ly = base[:, 1] + oy
-            by = bspline(u[:, 1] - ly, dsup)
+            by = basis(u[:, 1] - ly, dsup)
             for ox in range(dsup):
                 lx = base[:, 0] + ox
-                bx = bspline(u[:, 0] - lx, dsup)
+                bx = basis(u[:, 0] - lx, dsup)
                 idx = ((lz % n) * n + (ly % n)) * n + (lx % n)
                 eps += np.bincount(idx, weights=w * bx * by * bz, minlength=n ** 3)
     return eps.reshape(n, n, n), float(w.sum())
@@ -195,8 +326,12 @@ def phi_hat(n: int, dsup: int):
     """Phi-hat(n) = prod_d sinc^{2 dsup}(pi n_d / n), the power spectrum |beta-hat|^2 of the
     B-spline basis at the lattice wavevectors, without the aliasing sum (Fig. 1 step (3) and
     Eq. SFC-3PCF-vertex; reading: the aliasing images are dropped as the paper's delta_{m,n}
-    does).  Full DFT grid [z, y, x]."""
-    s1 = np.sinc(fft_integers(n) / n) ** (2 * dsup)
+    does).  Full DFT grid [z, y, x].  dsup = 3: |phi-hat|^2 of the Daubechies function
+    (daub4_power at 2 pi n_d / n)."""
+    if dsup == 3:
+        s1 = daub4_power(2.0 * math.pi * fft_integers(n) / n)
+    else:
+        s1 = np.sinc(fft_integers(n) / n) ** (2 * dsup)
     return s1[:, None, None] * s1[None, :, None] * s1[None, None, :]
 
 
@@ -294,11 +429,14 @@ def _unit_interval_quadrature(func, lo: int, hi: int, nq: int = 8):
 
 
 def gamma_1d(dsup: int):
-    """1-D connection coefficients gamma(a, b) = int beta(u) beta(u-a) beta(u-b) du.
+    """1-D connection coefficients gamma(a, b) = int phi(u) phi(u-a) phi(u-b) du.
 
     Eq. (con-coeff) factorises over axes: Gamma_{l1,l2} = prod_d gamma(l1_d, l2_d).
-    Returns {(a, b): value} for |a|, |b| < dsup with a nonzero value.
+    Returns {(a, b): value} for |a|, |b| < dsup with a nonzero value (B-splines: exact
+    piecewise-polynomial quadrature; Daubechies: the two-scale solution, daub4_gamma).
     """
+    if dsup == 3:
+        return daub4_gamma()
     half = dsup // 2
     out = {}
     for a in range(-(dsup - 1), dsup):
@@ -311,7 +449,9 @@ def gamma_1d(dsup: int):
 
 
 def mass_1d(dsup: int):
-    """M(a) = int beta(u) beta(u - a) du for |a| < dsup."""
+    """M(a) = int phi(u) phi(u - a) du for |a| < dsup (Daubechies: daub4_mass)."""
+    if dsup == 3:
+        return daub4_mass()
     half = dsup // 2
     return {a: _unit_interval_quadrature(lambda u: bspline(u, dsup) * bspline(u - a, dsup), -half, half)
             for a in range(-(dsup - 1), dsup)}
@@ -354,7 +494,7 @@ def sum_gamma(delta, a, dsup: int):
 # per-(L, M) densities n^LM(x, r) = sum_l eps~^LM_l phi_l(x).
 # ---------------------------------------------------------------------------
 def interpolate(a, pos, n: int, box: float, dsup: int):
-    """f_b(x_p) = sum_l beta(u_p - l) a_b(l) (B-spline expansion at each point)."""
+    """f_b(x_p) = sum_l phi(u_p - l) a_b(l) (the basis expansion at each point)."""
     pos = np.asarray(pos, np.float64)
     u = pos / (box / n)
     base = stencil_base(u, dsup)
@@ -363,13 +503,13 @@ def interpolate(a, pos, n: int, box: float, dsup: int):
     f = np.zeros((nb, pos.shape[0]))
     for oz in range(dsup):
         lz = base[:, 2] + oz
-        bz = bspline(u[:, 2] - lz, dsup)
+        bz = basis(u[:, 2] - lz, dsup)
         for oy in range(dsup):
             ly = base[:, 1] + oy
-            by = bspline(u[:, 1] - ly, dsup)
+            by = basis(u[:, 1] - ly, dsup)
             for ox in range(dsup):
                 lx = base[:, 0] + ox
-                bx = bspline(u[:, 0] - lx, dsup)
+                bx = basis(u[:, 0] - lx, dsup)
                 idx = ((lz % n) * n + (ly % n)) * n + (lx % n)
                 f += (bx * by * bz)[None, :] * af[:, idx]
     return f
