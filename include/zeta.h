@@ -104,7 +104,9 @@ enum {
 typedef struct {
   int n;                /* grid side: power of two, 16 <= n <= 512                   */
   double box;           /* periodic box side, same unit as positions and edges       */
-  int dsup;             /* B-spline support D: 2 (linear hat) or 4 (cubic)           */
+  int dsup;             /* basis support D: 2 (linear B-spline hat), 4 (cubic         */
+                        /* B-spline), or 3: the genus-4 Daubechies scaling function   */
+                        /* (Sec. 2.2, D_sup = D_g - 1 = 3; see "Daubechies basis")    */
   int lmax;             /* highest multipole l, 0 <= lmax <= 14                      */
   int nbins;            /* number of radial bins, 1 <= nbins <= 32                   */
   const double* edges;  /* host, nbins+1 strictly increasing, edges[0] > 0,          */
@@ -122,8 +124,22 @@ typedef struct {
                         /* replaced by IDFT[DFT(delta) W_TH(|k| R)] (0: none); the     */
                         /* particle form's primary vertex is the catalogue itself     */
   int phi_hat;          /* 1: secondary vertices times Phi-hat(n) = prod_d            */
-                        /* sinc^{2D}(pi n_d / n), |beta-hat|^2 of the basis (no aliasing) */
+                        /* |phi-hat(2 pi n_d / n)|^2 of the basis (no aliasing):       */
+                        /* sinc^{2D}(pi n_d / n) for the B-splines                    */
 } zeta_params;
+
+/* Daubechies basis (dsup = 3).  phi is the scaling function of the genus-4 Daubechies filter
+ * h = (1 + s, 3 + s, 3 - s, 1 - s) / (4 sqrt2), s = sqrt3, defined by the two-scale relation
+ * phi(x) = sqrt2 sum_k h_k phi(2x - k), support [0, 3].  A particle at grid coordinate u = x / H
+ * enters the three nodes l = floor(u) - 2 .. floor(u) with weight prod_d phi(u_d - l_d), where
+ * phi(t) is read from the float32 table of its exact values at the dyadic points k / 2^10
+ * (zeta_host_daub4_dyadic) joined linearly; the grid is laid out like the B-spline grids (node l
+ * at index l).  The node form, the particle form (its uniform term with M(a) = [a == 0]: the
+ * basis is orthonormal) and the Gamma form use the exact connection coefficients Gamma(a, b) =
+ * int phi(x) phi(x - a) phi(x - b) dx of phi (zeta_host_daub4_gamma), applied per node through
+ * their eigen-split (5 x 5 per axis, 125 terms per node).  The particle gradient
+ * (zeta_backward_particles) and zeta_assign_noalloc take B-splines only (ZETA_ENOTSUP /
+ * ZETA_EINVAL for dsup 3); the node gradient does not depend on the basis. */
 
 /* Library version (major*10000 + minor*100 + patch). Host only. */
 int zeta_version(void);
@@ -389,9 +405,24 @@ int zeta_host_jbar_table(int n, double box, int lmax, int nbins, const double* e
  * p->tophat > 0.  Host only; ZETA_EINVAL on invalid parameters. */
 int zeta_host_window_table(const zeta_params* p, float* out);
 
-/* Phi-hat per axis: out[i] = sinc^{2 dsup}(pi f / n) for DFT index i < n, f its signed frequency
- * (Fig. 1 step (3), the basis power spectrum without aliasing).  Host only. */
+/* Phi-hat per axis: out[i] = |phi-hat(2 pi f / n)|^2 for DFT index i < n, f its signed
+ * frequency (Fig. 1 step (3), the basis power spectrum without aliasing): sinc^{2 dsup}(pi f / n)
+ * for the B-splines (dsup 2, 4); for the Daubechies basis (dsup 3) the product
+ * sinc^4(w/2) prod_{j>=1} (1 + 2 sin^2(w / 2^(j+1))), w = 2 pi f / n (the transform of the
+ * two-scale relation).  Host only. */
 int zeta_host_phi_hat(int n, int dsup, double* out);
+
+/* The Daubechies scaling function's values at the dyadic points k / 2^level, k = 0 .. 3 * 2^level
+ * (from its two-scale relation; the device table is the level-10 one rounded to float32).
+ * out: caller-owned host memory of 3 * 2^level + 1 doubles; 0 <= level <= 20, else ZETA_EINVAL. */
+int zeta_host_daub4_dyadic(int level, double* out);
+
+/* The Daubechies basis's 1-D connection coefficients (Eq. con-coeff per axis):
+ * gamma[(a + 2) * 5 + (b + 2)] = int phi(x) phi(x - a) phi(x - b) dx for |a|, |b| <= 2 (zero where
+ * |a - b| >= 3), solved from the two-scale relation with sum_b Gamma(a, b) = [a == 0].  When lam and
+ * u are not NULL they receive the eigen-split Gamma = U diag(lam) U^T the Gamma form applies:
+ * lam[k] (5 doubles) and u[o * 5 + k] (25 doubles; row o is the offset o - 2).  Host only. */
+int zeta_host_daub4_gamma(double* gamma, double* lam, double* u);
 
 /* The 3PCF in angle from its multipoles, Eq. (triplet-counting): out[i][b1][b2] =
  * sum_{l <= lmax} zeta_l[l][b1][b2] P_l(mu[i]), P_l by the three-term recurrence, float64 host
@@ -405,9 +436,9 @@ int zeta_host_reduced_q(int count, const double* zeta, const double* xi1, const 
 
 /* Mhat(k) = M(0) + 2 sum_{0<a<dsup} M(a) cos(2 pi k a / n) for 0 <= k < n, in float64: the 1-D
  * factor of the B-spline mass matrix's DFT in the uniform term of the particle form (Sec. 2.2,
- * Eq. DDD-sum-privertex); M(a) = int beta_D(u) beta_D(u - a) du.  The context's device table is
- * its float32 rounding.  out: n doubles, caller-owned host memory.  2 <= n <= 2^20, dsup 2 or
- * 4, else ZETA_EINVAL. */
+ * Eq. DDD-sum-privertex); M(a) = int phi(u) phi(u - a) du (1 for every k with the orthonormal
+ * Daubechies basis, dsup 3).  The context's device table is its float32 rounding.  out: n
+ * doubles, caller-owned host memory.  2 <= n <= 2^20, dsup 2, 3 or 4, else ZETA_EINVAL. */
 int zeta_host_mass_hat(int n, int dsup, double* out);
 
 /* The per-cell quadrature of the connection-coefficient (Gamma) form (Eqs. con-coeff,

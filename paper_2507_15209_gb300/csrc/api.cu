@@ -131,7 +131,7 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
   *out = nullptr;
   if (!p || !is_pow2(p->n) || p->n < 16 || p->n > 512) return ZETA_EINVAL;
   if (!(p->box > 0) || !std::isfinite(p->box)) return ZETA_EINVAL;
-  if (p->dsup != 2 && p->dsup != 4) return ZETA_EINVAL;
+  if (p->dsup < 2 || p->dsup > 4) return ZETA_EINVAL;  // 2, 4: B-splines; 3: Daubechies
   if (p->lmax < 0 || p->lmax > kMaxL) return ZETA_EINVAL;
   if (p->nbins < 1 || p->nbins > kMaxBins) return ZETA_EINVAL;
   if (p->gram < ZETA_GRAM_FP32 || p->gram > ZETA_GRAM_BF16_FIELDS) return ZETA_EINVAL;
@@ -191,11 +191,22 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
     for (int i = 0; i < p->n; ++i) phi[i] = static_cast<float>(ph64[i]);
   std::vector<float> wprim;
   if (p->tophat_primary > 0) host_tophat_table(p->n, p->box, p->tophat_primary, wprim);
-  std::vector<double> qt, qw, qb;
-  host_cell_quadrature(c->gamma_q, p->dsup, qt, qw, qb);
-  std::vector<float> gq;
-  for (double v : qw) gq.push_back(static_cast<float>(v));
-  for (double v : qb) gq.push_back(static_cast<float>(v));
+  std::vector<float> gq;  // Gamma form: point weights [q], then stencil taps [q][taps]
+  std::vector<float> daub;
+  if (p->dsup == 3) {
+    std::vector<double> lam, u, dy;
+    host_daub4_gamma_split(lam, u);
+    for (int k = 0; k < 5; ++k) gq.push_back(static_cast<float>(lam[k]));
+    for (int k = 0; k < 5; ++k)
+      for (int o = 0; o < 5; ++o) gq.push_back(static_cast<float>(u[o * 5 + k]));
+    host_daub4_dyadic(kDaubLevel, dy);
+    for (double v : dy) daub.push_back(static_cast<float>(v));
+  } else {
+    std::vector<double> qt, qw, qb;
+    host_cell_quadrature(c->gamma_q, p->dsup, qt, qw, qb);
+    for (double v : qw) gq.push_back(static_cast<float>(v));
+    for (double v : qb) gq.push_back(static_cast<float>(v));
+  }
 
   if (cudaMalloc(&c->d_jtab, jtab.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
   if (cudaMalloc(&c->d_tw, tw.size() * sizeof(float2)) != cudaSuccess) return fail(ZETA_ENOMEM);
@@ -203,6 +214,11 @@ int zeta_create(const zeta_params* p, zeta_ctx** out) {
   if (cudaMalloc(&c->d_gq, gq.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
   if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess) return fail(ZETA_ENOMEM);
   if (cudaMalloc(&c->d_phi, phi.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
+  if (!daub.empty()) {
+    if (cudaMalloc(&c->d_daub, daub.size() * sizeof(float)) != cudaSuccess) return fail(ZETA_ENOMEM);
+    if (cudaMemcpy(c->d_daub, daub.data(), daub.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(ZETA_ECUDA);
+  }
   if (cudaMemcpy(c->d_phi, phi.data(), phi.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(ZETA_ECUDA);
   if (!wprim.empty()) {
@@ -238,6 +254,7 @@ int zeta_destroy(zeta_ctx* c) {
   cudaFree(c->d_status);
   cudaFree(c->d_phi);
   cudaFree(c->d_wprim);
+  cudaFree(c->d_daub);
   delete c;
   return ZETA_OK;
 }
@@ -825,6 +842,7 @@ int zeta_backward_particles(zeta_ctx* c, const float* particles, int64_t np, con
   ZK_TRY(check_ctx(c));
   if (!particles || np < 1 || np > 0x7fffffffLL || !weights || !grad) return ZETA_EINVAL;
   if (c->p.tophat_primary > 0) return ZETA_ENOTSUP;
+  if (c->p.dsup == 3) return ZETA_ENOTSUP;  // the Daubechies function has no derivative to move points with
   ZK_TRY(need_ws(c, np, true));
   const Layout L = layout(c, np, true);
   const int nb = c->p.nbins;

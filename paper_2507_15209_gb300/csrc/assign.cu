@@ -1,8 +1,9 @@
-// B-spline (MRA) assignment of the catalogue and particle tiling, sm_103a.
+// MRA assignment of the catalogue and particle tiling, sm_103a.
 //
 // Assignment (Sec. 2.1 expansion n = sum eps phi; Fig. 1 step (2); contrast of Sec. 3):
-//   eps_l = sum_p w_p beta(u_p - l), u = x / H, periodic in l, beta the centred B-spline of
-//   order D; delta_l = eps_l / eps_bar - 1 with eps_bar = W / N_g.
+//   eps_l = sum_p w_p phi(u_p - l), u = x / H, periodic in l, phi the centred B-spline of
+//   order D or the genus-4 Daubechies function (tabulated); delta_l = eps_l / eps_bar - 1 with
+//   eps_bar = W / N_g.
 // Contributions are scattered as 64-bit fixed point (scale 2^k with k chosen from sum |w|
 // so no cell can overflow), so the result does not depend on the order of the atomics.
 // The cell and in-cell offset of each particle are computed in float64 so that a float32
@@ -23,8 +24,8 @@ __device__ __forceinline__ bool finite4(float4 p) {
   return isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w);
 }
 
-// grid coordinate wrapped into [0, n): returns cell and in-cell offset t in [0, 1)
-__device__ __forceinline__ int cell_of(float x, double inv_h, int n, float& t) {
+// grid coordinate wrapped into [0, n): returns cell (less shift, periodic) and in-cell offset t in [0, 1)
+__device__ __forceinline__ int cell_of(float x, double inv_h, int n, int shift, float& t) {
   double u = static_cast<double>(x) * inv_h;
   u -= floor(u / n) * n;
   int i = static_cast<int>(floor(u));
@@ -35,6 +36,8 @@ __device__ __forceinline__ int cell_of(float x, double inv_h, int n, float& t) {
   if (i < 0) i += n;
   t = static_cast<float>(fr);
   if (t >= 1.0f) t = 0.99999994f;
+  i -= shift;
+  if (i < 0) i += n;
   return i;
 }
 
@@ -50,6 +53,16 @@ __device__ __forceinline__ void bspline_weights(float t, float* w) {
     w[2] = (-3.f * t3 + 3.f * t2 + 3.f * t + 1.f) * (1.f / 6.f);
     w[3] = t3 * (1.f / 6.f);
   }
+}
+
+// Stencil weights of the basis: the B-spline of order D, or with a table (D = 4) the Daubechies
+// function's.
+template <int D>
+__device__ __forceinline__ void stencil_weights(float t, const float* __restrict__ dtab, float* w) {
+  if (D == 4 && dtab != nullptr)
+    daub4_weights(t, dtab, w);
+  else
+    bspline_weights<D>(t, w);
 }
 
 __global__ void k_weight_partials(const float4* __restrict__ p, long long np, double* __restrict__ part,
@@ -105,21 +118,22 @@ __global__ void k_weight_final(const double* __restrict__ part, int nparts, doub
 }
 
 template <int D>
-__global__ void k_assign_scatter(const float4* __restrict__ p, long long np, int n, double inv_h,
-                                 const double* __restrict__ wstat, unsigned long long* __restrict__ acc) {
+__global__ void k_assign_scatter(const float4* __restrict__ p, long long np, int n, double inv_h, int shift,
+                                 const float* __restrict__ dtab, const double* __restrict__ wstat,
+                                 unsigned long long* __restrict__ acc) {
   const double scale = wstat[2];
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np;
        i += static_cast<long long>(blockDim.x) * gridDim.x) {
     const float4 q = p[i];
     if (!finite4(q)) continue;
     float tx, ty, tz;
-    const int cx = cell_of(q.x, inv_h, n, tx);
-    const int cy = cell_of(q.y, inv_h, n, ty);
-    const int cz = cell_of(q.z, inv_h, n, tz);
+    const int cx = cell_of(q.x, inv_h, n, shift, tx);
+    const int cy = cell_of(q.y, inv_h, n, shift, ty);
+    const int cz = cell_of(q.z, inv_h, n, shift, tz);
     float wx[D], wy[D], wz[D];
-    bspline_weights<D>(tx, wx);
-    bspline_weights<D>(ty, wy);
-    bspline_weights<D>(tz, wz);
+    stencil_weights<D>(tx, dtab, wx);
+    stencil_weights<D>(ty, dtab, wy);
+    stencil_weights<D>(tz, dtab, wz);
     const int off = D / 2 - 1;
     const double ws = static_cast<double>(q.w) * scale;
 #pragma unroll
@@ -152,20 +166,21 @@ __global__ void k_assign_finalize(const unsigned long long* __restrict__ acc, lo
   }
 }
 
-__device__ __forceinline__ long long tile_of(float4 q, double inv_h, int n) {
+__device__ __forceinline__ long long tile_of(float4 q, double inv_h, int n, int shift) {
   float t;
   const int nt = n / kTile;
   if (!finite4(q)) return 0;
-  const int cx = cell_of(q.x, inv_h, n, t) / kTile;
-  const int cy = cell_of(q.y, inv_h, n, t) / kTile;
-  const int cz = cell_of(q.z, inv_h, n, t) / kTile;
+  const int cx = cell_of(q.x, inv_h, n, shift, t) / kTile;
+  const int cy = cell_of(q.y, inv_h, n, shift, t) / kTile;
+  const int cz = cell_of(q.z, inv_h, n, shift, t) / kTile;
   return (static_cast<long long>(cz) * nt + cy) * nt + cx;
 }
 
-__global__ void k_tile_count(const float4* __restrict__ p, long long np, int n, double inv_h, int* __restrict__ cnt) {
+__global__ void k_tile_count(const float4* __restrict__ p, long long np, int n, double inv_h, int shift,
+                             int* __restrict__ cnt) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np;
        i += static_cast<long long>(blockDim.x) * gridDim.x)
-    atomicAdd(cnt + tile_of(p[i], inv_h, n), 1);
+    atomicAdd(cnt + tile_of(p[i], inv_h, n, shift), 1);
 }
 
 // Exclusive prefix sum of cnt[0..m) into start[0..m] (start[m] = total) with one CTA;
@@ -197,12 +212,12 @@ __global__ void k_tile_scan(int* __restrict__ cnt, long long m, long long* __res
   if (threadIdx.x == 0) start[m] = carry;
 }
 
-__global__ void k_tile_scatter(const float4* __restrict__ p, long long np, int n, double inv_h,
+__global__ void k_tile_scatter(const float4* __restrict__ p, long long np, int n, double inv_h, int shift,
                                const long long* __restrict__ start, int* __restrict__ cursor,
                                int* __restrict__ orig) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np;
        i += static_cast<long long>(blockDim.x) * gridDim.x) {
-    const long long t = tile_of(p[i], inv_h, n);
+    const long long t = tile_of(p[i], inv_h, n, shift);
     const int slot = atomicAdd(cursor + t, 1);
     orig[start[t] + slot] = static_cast<int>(i);
   }
@@ -235,7 +250,8 @@ __global__ void k_tile_order(const float4* __restrict__ p, const long long* __re
 // The float64 cell arithmetic of a particle, done once per catalogue: cell (linear index
 // z n^2 + y n + x), in-cell offsets t in [0, 1) and the weight (0 for a non-finite particle,
 // which sits in cell 0 with t = 0 and so contributes nothing anywhere).
-__device__ __forceinline__ void prep_one(float4 q, double inv_h, int n, int& cell, float4& tq, int& tile) {
+__device__ __forceinline__ void prep_one(float4 q, double inv_h, int n, int shift, int& cell, float4& tq,
+                                         int& tile) {
   const int nt = n / kTile;
   if (!finite4(q)) {
     cell = 0;
@@ -244,21 +260,22 @@ __device__ __forceinline__ void prep_one(float4 q, double inv_h, int n, int& cel
     return;
   }
   float tx, ty, tz;
-  const int cx = cell_of(q.x, inv_h, n, tx), cy = cell_of(q.y, inv_h, n, ty), cz = cell_of(q.z, inv_h, n, tz);
+  const int cx = cell_of(q.x, inv_h, n, shift, tx), cy = cell_of(q.y, inv_h, n, shift, ty),
+            cz = cell_of(q.z, inv_h, n, shift, tz);
   cell = (cz * n + cy) * n + cx;
   tile = ((cz / kTile) * nt + cy / kTile) * nt + cx / kTile;
   tq = make_float4(tx, ty, tz, q.w);
 }
 
 // Prepared data in the original order and the particle count of every tile.
-__global__ void k_particle_prep(const float4* __restrict__ p, long long np, int n, double inv_h,
+__global__ void k_particle_prep(const float4* __restrict__ p, long long np, int n, double inv_h, int shift,
                                 int* __restrict__ o_tile, int* __restrict__ o_cell, float4* __restrict__ o_tq,
                                 int* __restrict__ cnt) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np;
        i += static_cast<long long>(blockDim.x) * gridDim.x) {
     int cell, tile;
     float4 tq;
-    prep_one(p[i], inv_h, n, cell, tq, tile);
+    prep_one(p[i], inv_h, n, shift, cell, tq, tile);
     o_tile[i] = tile;
     o_cell[i] = cell;
     o_tq[i] = tq;
@@ -277,13 +294,13 @@ __global__ void k_tile_scatter_pre(const int* __restrict__ o_tile, long long np,
 }
 
 // Prepared data of particles that are already sorted (a caller's sorted array).
-__global__ void k_prep_sorted(const float4* __restrict__ sorted, long long np, int n, double inv_h,
+__global__ void k_prep_sorted(const float4* __restrict__ sorted, long long np, int n, double inv_h, int shift,
                               int* __restrict__ s_cell, float4* __restrict__ s_tq) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < np;
        i += static_cast<long long>(blockDim.x) * gridDim.x) {
     int cell, tile;
     float4 tq;
-    prep_one(sorted[i], inv_h, n, cell, tq, tile);
+    prep_one(sorted[i], inv_h, n, shift, cell, tq, tile);
     s_cell[i] = cell;
     s_tq[i] = tq;
   }
@@ -325,7 +342,8 @@ __device__ __forceinline__ long long fix64(float x, int k) {
 template <int D>
 __global__ void __launch_bounds__(256) k_assign_tiles(const long long* __restrict__ tile_start,
                                                       const int* __restrict__ s_cell, const float4* __restrict__ s_tq,
-                                                      int n, const double* __restrict__ wstat, float* __restrict__ delta) {
+                                                      int n, const float* __restrict__ dtab,
+                                                      const double* __restrict__ wstat, float* __restrict__ delta) {
   constexpr int T3 = kTile * kTile * kTile;
   constexpr int OFF = D / 2 - 1;
   __shared__ unsigned long long acc[kTile * kTile * kAccPitch];  // rows padded against bank conflicts
@@ -387,9 +405,9 @@ __global__ void __launch_bounds__(256) k_assign_tiles(const long long* __restric
     const int lz = r[2] + oz;
     if (!reach || lz < 0 || lz >= kTile) continue;
     float wx[D], wy[D], wz[D];
-    bspline_weights<D>(q.x, wx);
-    bspline_weights<D>(q.y, wy);
-    bspline_weights<D>(q.z, wz);
+    stencil_weights<D>(q.x, dtab, wx);
+    stencil_weights<D>(q.y, dtab, wy);
+    stencil_weights<D>(q.z, dtab, wz);
     float wzo = wz[0];
 #pragma unroll
     for (int o = 1; o < D; ++o) wzo = oz == o ? wz[o] : wzo;
@@ -443,9 +461,9 @@ int launch_assign(const zeta_ctx* c, const float4* parts, int64_t np, float* del
   const double inv_h = c->n / c->p.box;
   const int g = grid_for(np, 256, c->num_sms);
   if (c->p.dsup == 2)
-    k_assign_scatter<2><<<g, 256, 0, s>>>(parts, np, c->n, inv_h, wstat, acc);
+    k_assign_scatter<2><<<g, 256, 0, s>>>(parts, np, c->n, inv_h, 0, nullptr, wstat, acc);
   else
-    k_assign_scatter<4><<<g, 256, 0, s>>>(parts, np, c->n, inv_h, wstat, acc);
+    k_assign_scatter<4><<<g, 256, 0, s>>>(parts, np, c->n, inv_h, cell_shift(c), c->d_daub, wstat, acc);
   k_assign_finalize<<<grid_for(c->ng, 256, c->num_sms), 256, 0, s>>>(acc, c->ng, wstat, delta);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
@@ -466,13 +484,14 @@ int launch_sort(const zeta_ctx* c, const float4* parts, int64_t np, float4* sort
   const int g = grid_for(np, 256, c->num_sms);
   long long* st = reinterpret_cast<long long*>(tile_start);
   if (prep) {
-    k_particle_prep<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, prep->o_tile, prep->o_cell, prep->o_tq, counts);
+    k_particle_prep<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, cell_shift(c), prep->o_tile, prep->o_cell, prep->o_tq,
+                                      counts);
     k_tile_scan<<<1, 1024, 0, s>>>(counts, c->ntiles, st);
     k_tile_scatter_pre<<<g, 256, 0, s>>>(prep->o_tile, np, st, counts, orig);
   } else {
-    k_tile_count<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, counts);
+    k_tile_count<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, cell_shift(c), counts);
     k_tile_scan<<<1, 1024, 0, s>>>(counts, c->ntiles, st);
-    k_tile_scatter<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, st, counts, orig);
+    k_tile_scatter<<<g, 256, 0, s>>>(parts, np, c->n, inv_h, cell_shift(c), st, counts, orig);
   }
   const long long warps = c->ntiles;
   k_tile_order<<<static_cast<unsigned>((warps * 32 + 255) / 256), 256, 0, s>>>(
@@ -500,7 +519,8 @@ int launch_ss_fields(const zeta_ctx* c, float* data_delta, float* rand_delta, cu
 
 int launch_prep_sorted(const zeta_ctx* c, const float4* sorted, int64_t np, int* s_cell, float4* s_tq, cudaStream_t s) {
   StageScope prof(c, ST_SORT, 1, s);
-  k_prep_sorted<<<grid_for(np, 256, c->num_sms), 256, 0, s>>>(sorted, np, c->n, c->n / c->p.box, s_cell, s_tq);
+  k_prep_sorted<<<grid_for(np, 256, c->num_sms), 256, 0, s>>>(sorted, np, c->n, c->n / c->p.box, cell_shift(c),
+                                                              s_cell, s_tq);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
@@ -513,9 +533,10 @@ int launch_assign_tiles(const zeta_ctx* c, const float4* parts, int64_t np, cons
   k_weight_final<<<1, 32, 0, s>>>(scratch, kRedCtas, wstat, wsum);
   const long long* ts = reinterpret_cast<const long long*>(tile_start);
   if (c->p.dsup == 2)
-    k_assign_tiles<2><<<static_cast<unsigned>(c->ntiles), 256, 0, s>>>(ts, s_cell, s_tq, c->n, wstat, delta);
+    k_assign_tiles<2><<<static_cast<unsigned>(c->ntiles), 256, 0, s>>>(ts, s_cell, s_tq, c->n, nullptr, wstat, delta);
   else
-    k_assign_tiles<4><<<static_cast<unsigned>(c->ntiles), 256, 0, s>>>(ts, s_cell, s_tq, c->n, wstat, delta);
+    k_assign_tiles<4><<<static_cast<unsigned>(c->ntiles), 256, 0, s>>>(ts, s_cell, s_tq, c->n, c->d_daub, wstat,
+                                                                        delta);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
@@ -597,9 +618,9 @@ extern "C" int zeta_assign_noalloc(int n, double box, int dsup, const float* par
   const double inv_h = n / box;
   const int g = grid_for(np, 256, sms);
   if (dsup == 2)
-    k_assign_scatter<2><<<g, 256, 0, s>>>(p, np, n, inv_h, wstat, acc);
+    k_assign_scatter<2><<<g, 256, 0, s>>>(p, np, n, inv_h, 0, nullptr, wstat, acc);
   else
-    k_assign_scatter<4><<<g, 256, 0, s>>>(p, np, n, inv_h, wstat, acc);
+    k_assign_scatter<4><<<g, 256, 0, s>>>(p, np, n, inv_h, 0, nullptr, wstat, acc);
   k_assign_finalize<<<grid_for(ng, 256, sms), 256, 0, s>>>(acc, ng, wstat, delta);
   k_poison_if_bad<<<grid_for(ng, 256, sms), 256, 0, s>>>(status, delta, ng, wsum);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;

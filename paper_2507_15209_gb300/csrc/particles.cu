@@ -99,14 +99,20 @@ __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;"
 // arithmetic only.
 template <int D, int PW>
 __device__ __forceinline__ void particle_setup(int cell, float4 tq, int n, int lg, int tx, int ty, int tz,
-                                               bool staged, int4& org, float* pw) {
+                                               bool staged, const float* __restrict__ dtab, int4& org, float* pw) {
   using H = Halo<D>;
   constexpr int OFF = D / 2 - 1;
   float wx[D], wy[D], wz[D];
   const int cix[3] = {cell & (n - 1), (cell >> lg) & (n - 1), cell >> (2 * lg)};
-  bsw<D>(tq.x, wx);
-  bsw<D>(tq.y, wy);
-  bsw<D>(tq.z, wz);
+  if (D == 4 && dtab != nullptr) {  // Daubechies basis (the cell is one below floor(u))
+    daub4_weights(tq.x, dtab, wx);
+    daub4_weights(tq.y, dtab, wy);
+    daub4_weights(tq.z, dtab, wz);
+  } else {
+    bsw<D>(tq.x, wx);
+    bsw<D>(tq.y, wy);
+    bsw<D>(tq.z, wz);
+  }
   const int lx = cix[0] - tx * kTile, ly = cix[1] - ty * kTile, lz = cix[2] - tz * kTile;
   const bool inside = lx >= 0 && lx < kTile && ly >= 0 && ly < kTile && lz >= 0 && lz < kTile;
   org = make_int4(cix[0] - OFF, cix[1] - OFF, cix[2] - OFF, (staged && inside) ? lz * H::PP + ly * H::XP + lx : -1);
@@ -181,7 +187,7 @@ template <int NBP, int D>
 __global__ void __launch_bounds__(kIThreads, 3)
     k_interp_part(const int* __restrict__ s_cell, const float4* __restrict__ s_tq,
                   const long long* __restrict__ tile_start, const float4* __restrict__ f4, long long ng, int n, int nb,
-                  int staged_min, float* __restrict__ pvals, int* __restrict__ status) {
+                  int staged_min, const float* __restrict__ dtab, float* __restrict__ pvals, int* __restrict__ status) {
   using H = Halo<D>;
   using S = InterpSmem<NBP, D>;
   constexpr int PW = S::PW;
@@ -294,7 +300,7 @@ __global__ void __launch_bounds__(kIThreads, 3)
       if (ct < cnt) {
         const bool pre = pf_bs == bs;
         particle_setup<D, PW>(pre ? pf_cell : s_cell[bs + ct], pre ? pf_tq : s_tq[bs + ct], n, lg, tx, ty, tz,
-                              true, org[ct], bw + ct * PW);
+                              true, dtab, org[ct], bw + ct * PW);
       }
       {  // prefetch the next batch (this tile's next one, or the first of the next tile)
         const bool same = bs + kPBP < s1;
@@ -407,7 +413,7 @@ template <int NBP, int D>
 __global__ void __launch_bounds__(kThreadsL1, 1)
     k_interp_part_l1(const int* __restrict__ s_cell, const float4* __restrict__ s_tq,
                      const long long* __restrict__ tile_start, const float4* __restrict__ f4, long long ng, int n,
-                     int nb, int staged_min, float* __restrict__ pvals) {
+                     int nb, int staged_min, const float* __restrict__ dtab, float* __restrict__ pvals) {
   using S = InterpL1Smem<NBP, D>;
   constexpr int PW = S::PW;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -434,7 +440,7 @@ __global__ void __launch_bounds__(kThreadsL1, 1)
       if (cnt >= staged_min) continue;  // the staged kernel takes this batch
       __syncthreads();  // the previous batch's value rows are written out
       if (threadIdx.x < cnt)
-        particle_setup<D, PW>(s_cell[bs + threadIdx.x], s_tq[bs + threadIdx.x], n, lg, tx, ty, tz, false,
+        particle_setup<D, PW>(s_cell[bs + threadIdx.x], s_tq[bs + threadIdx.x], n, lg, tx, ty, tz, false, dtab,
                               org[threadIdx.x], bw + threadIdx.x * PW);
       __syncthreads();
       for (int pb = warp * PPW; pb < cnt; pb += NW * PPW) {  // warp-uniform
@@ -589,13 +595,14 @@ int part_impl(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const in
     const size_t sm = InterpSmem<NBP, D>::BYTES;
     if (prep(k_interp_part<NBP, D>, sm)) return ZETA_ECUDA;
     k_interp_part<NBP, D><<<gram_ctas(c, GK_PART), kIThreads, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n,
-                                                                       c->p.nbins, c->staged_min, pvals, c->d_status);
+                                                                       c->p.nbins, c->staged_min, c->d_daub, pvals,
+                                                                       c->d_status);
   }
   if (part_l1_on(c)) {
     const size_t sm = InterpL1Smem<NBP, D>::BYTES;
     if (prep(k_interp_part_l1<NBP, D>, sm)) return ZETA_ECUDA;
     k_interp_part_l1<NBP, D><<<c->num_sms, kThreadsL1, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n, c->p.nbins,
-                                                                c->staged_min, pvals);
+                                                                c->staged_min, c->d_daub, pvals);
   }
   if constexpr (NBP <= 20) {  // register-blocked Gram of the rows (sums.cu), one CTA per SM
     return launch_gram_rows_rb(c, pvals, s_tq, np, partials, gram_particle_parts(c), s);
@@ -666,13 +673,14 @@ int xi_impl(const zeta_ctx* c, const int* s_cell, const float4* s_tq, const int6
     const size_t sm = InterpSmem<NBP, D>::BYTES;
     if (prep(k_interp_part<NBP, D>, sm)) return ZETA_ECUDA;
     k_interp_part<NBP, D><<<gram_ctas(c, GK_PART), kIThreads, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n,
-                                                                       c->p.nbins, c->staged_min, pvals, c->d_status);
+                                                                       c->p.nbins, c->staged_min, c->d_daub, pvals,
+                                                                       c->d_status);
   }
   if (part_l1_on(c)) {
     const size_t sm = InterpL1Smem<NBP, D>::BYTES;
     if (prep(k_interp_part_l1<NBP, D>, sm)) return ZETA_ECUDA;
     k_interp_part_l1<NBP, D><<<c->num_sms, kThreadsL1, sm, s>>>(s_cell, s_tq, ts, f4, c->ng, c->n, c->p.nbins,
-                                                                c->staged_min, pvals);
+                                                                c->staged_min, c->d_daub, pvals);
   }
   k_row_sums<NBP><<<gram_particle_parts(c), kThreads, 0, s>>>(pvals, s_tq, np, c->p.nbins, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;

@@ -267,7 +267,11 @@ __device__ __forceinline__ bool rb_consume(const unsigned char* ring, unsigned l
           }
         }
       }
-      if (p >= cnt) w = 0.f;  // a ragged last chunk: the slot holds stale (finite) values there
+      if (p >= cnt) {  // a ragged last chunk (particle rows only): the slot's tail was not written by
+        w = 0.f;       // this chunk's copy and may hold anything, NaN included, so zero the values too
+#pragma unroll
+        for (int q = 0; q < NBP; ++q) v[q] = 0.f;
+      }
       rb_accum_seq<NBP, H>(acc, v, w, std::make_integer_sequence<int, T::NPH>{});
       if (++pending == kRbFlush) {
         rb_flush<NBP>(acc, dacc, lane);
@@ -377,6 +381,14 @@ constexpr size_t smem_node_rb() {
 // Phase 1 puts each point's stencil origin, B-spline weights and n_rec weight in shared
 // memory; phase 2 spreads (point, bin group) tasks over the CTA, each gathering its D^3
 // stencil of float4 bin groups from the L1-cached fields; phase 3 contracts the batch.
+// B-splines (D = 2, 4): the points are the q^3 Gauss-Legendre nodes of each cell, so the sum is
+// the exact integral of n_rec f_b1 f_b2 over the cell.  Daubechies (D = 5): the per-axis
+// connection coefficients split as gamma = U diag(lam) U^T (5 x 5), so
+// sum_l delta_l sum_{o1,o2} Gamma(o1, o2) a_b1(l + o1) a_b2(l + o2)
+//   = sum_l sum_k (lam_kx lam_ky lam_kz delta_l) A_k,b1(l) A_k,b2(l),
+// A_k(l) = sum_o U[ox][kx] U[oy][ky] U[oz][kz] a(l + o - 2): the "points" of node l are the 5^3
+// eigen-indices k, the stencil taps U[o][k] (offsets -2..2), and the point weight the product of
+// lam times delta at the node itself.
 template <int NBP, int D>
 __global__ void __launch_bounds__(kThreads)
     k_gram_gamma(const float* __restrict__ delta, const float4* __restrict__ f4, long long ng, int n, int nb,
@@ -396,7 +408,9 @@ __global__ void __launch_bounds__(kThreads)
   const int ngrp = (nb + 3) / 4;
   const int nt = n / kTile;
   const long long ntiles = static_cast<long long>(nt) * nt * nt;
-  constexpr int OFF = D / 2 - 1;
+  constexpr bool DB = D == 5;                 // Daubechies eigen-split form
+  constexpr int OFF = DB ? 2 : D / 2 - 1;
+  constexpr int LW = DB ? 8 : D;              // lanes per gather task (a power of two)
   const int q3 = q * q * q;
   const int mask = n - 1;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -426,18 +440,22 @@ __global__ void __launch_bounds__(kThreads)
             wy[o] = beta[qy * D + o];
             wz[o] = beta[qz * D + o];
           }
-          // n_rec at the node: the B-spline expansion of delta
           float nr = 0.f;
+          if (DB) {  // delta at the node itself
+            nr = __ldg(delta + (static_cast<long long>(cz) * n + cy) * n + cx);
+          } else {  // n_rec at the quadrature point: the B-spline expansion of delta
 #pragma unroll
-          for (int oz = 0; oz < D; ++oz)
+            for (int oz = 0; oz < D; ++oz)
 #pragma unroll
-            for (int oy = 0; oy < D; ++oy) {
-              const long long row = (static_cast<long long>((cz - OFF + oz) & mask) * n + ((cy - OFF + oy) & mask)) * n;
-              float a = 0.f;
+              for (int oy = 0; oy < D; ++oy) {
+                const long long row =
+                    (static_cast<long long>((cz - OFF + oz) & mask) * n + ((cy - OFF + oy) & mask)) * n;
+                float a = 0.f;
 #pragma unroll
-              for (int ox = 0; ox < D; ++ox) a = fmaf(wx[ox], __ldg(delta + row + ((cx - OFF + ox) & mask)), a);
-              nr = fmaf(wz[oz] * wy[oy], a, nr);
-            }
+                for (int ox = 0; ox < D; ++ox) a = fmaf(wx[ox], __ldg(delta + row + ((cx - OFF + ox) & mask)), a);
+                nr = fmaf(wz[oz] * wy[oy], a, nr);
+              }
+          }
           pw = gq[qx] * gq[qy] * gq[qz] * nr;
         }
         org[me] = make_int4(cx - OFF, cy - OFF, cz - OFF, 0);
@@ -452,18 +470,19 @@ __global__ void __launch_bounds__(kThreads)
         for (int b = 4 * ngrp; b < NBP; ++b) vals[me * G::NBS + b] = 0.f;
       }
       __syncthreads();
-      // phase 2: (point, group) gathers, D lanes per task (one per x offset of the stencil) so
-      // that a warp load covers 32/D tasks with D consecutive float4 (one row segment) each
-      // (the loop runs in whole warps so every lane reaches the shuffles; D divides 32)
-      const int total = cnt * ngrp * D;
+      // phase 2: (point, group) gathers, LW lanes per task (one per x offset of the stencil; the
+      // Daubechies form's 5 taps take 8 lanes, 3 idle) so that a warp load covers 32/LW tasks with
+      // D consecutive float4 (one row segment) each (the loop runs in whole warps so every lane
+      // reaches the shuffles; LW divides 32)
+      const int total = cnt * ngrp * LW;
       const int lane = threadIdx.x & 31;
       for (int tb = threadIdx.x - lane; tb < total; tb += blockDim.x) {
         const int task = tb + lane;
         const bool act = task < total;
-        const int ox = task % D, pg = task / D;
+        const int ox = task % LW, pg = task / LW;
         const int p = act ? pg % cnt : 0, q4 = act ? pg / cnt : 0;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (act) {
+        if (act && ox < D) {
           const int4 o = org[p];
           const float* w = bw + p * 3 * D;
           const float4* base = f4 + q4 * ng;
@@ -484,11 +503,11 @@ __global__ void __launch_bounds__(kThreads)
           }
         }
 #pragma unroll
-        for (int off = 1; off < D; off <<= 1) {
-          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off, D);
-          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off, D);
-          acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off, D);
-          acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off, D);
+        for (int off = 1; off < LW; off <<= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off, LW);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off, LW);
+          acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off, LW);
+          acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off, LW);
         }
         if (act && ox == 0) *reinterpret_cast<float4*>(vals + p * G::NBS + 4 * q4) = acc;
       }
@@ -792,6 +811,10 @@ int launch_gram_node(const zeta_ctx* c, const float* delta, const float* alm, do
 int launch_gram_gamma(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
   if (c->p.dsup == 2) {
 #define ZK_CALL(P) gamma_impl<P, 2>(c, delta, alm, partials, s)
+    ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
+#undef ZK_CALL
+  } else if (c->p.dsup == 3) {
+#define ZK_CALL(P) gamma_impl<P, 5>(c, delta, alm, partials, s)
     ZK_NBP_SWITCH(c->p.nbins, ZK_CALL)
 #undef ZK_CALL
   } else {

@@ -18,7 +18,9 @@
 //    step (3)) as a per-axis factor sinc^{2D}(pi n_d / n).
 //  * DFT twiddles.
 #include <cmath>
+#include <cstdlib>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "zeta_internal.h"
@@ -236,7 +238,181 @@ void host_ylm_constants(double* mm, double* a, double* b) {
   }
 }
 
+// ---- the genus-4 Daubechies scaling function (dsup = 3; Sec. 2.2, D_sup = 3) ----
+// Low-pass taps h_k = (1 + s, 3 + s, 3 - s, 1 - s) / (4 sqrt2), s = sqrt3, and the two-scale
+// relation phi(x) = sqrt2 sum_k h_k phi(2x - k), support [0, 3].
+static void daub4_taps(double* h) {
+  const double s = std::sqrt(3.0), d = 4.0 * std::sqrt(2.0);
+  h[0] = (1.0 + s) / d;
+  h[1] = (3.0 + s) / d;
+  h[2] = (3.0 - s) / d;
+  h[3] = (1.0 - s) / d;
+}
+
+void host_daub4_dyadic(int level, std::vector<double>& out) {
+  double h[4];
+  daub4_taps(h);
+  const double r2 = std::sqrt(2.0);
+  // the integers: phi(1) = sqrt2 (h1 phi(1) + h0 phi(2)) with phi(1) + phi(2) = 1
+  const double ratio = r2 * h[0] / (1.0 - r2 * h[1]);  // phi(1) / phi(2)
+  const double p2 = 1.0 / (1.0 + ratio);
+  std::vector<double> cur = {0.0, ratio * p2, p2, 0.0};
+  for (int j = 0; j < level; ++j) {
+    const int64_t unit = int64_t(1) << j;  // points per unit at level j
+    const int64_t m = 6 * unit;            // last index at level j + 1
+    std::vector<double> nxt(static_cast<size_t>(m + 1), 0.0);
+    for (int64_t k = 0; k <= m; ++k) {
+      if ((k & 1) == 0) {
+        nxt[k] = cur[k / 2];
+        continue;
+      }
+      double v = 0.0;  // phi(k / 2^(j+1)) = sqrt2 sum_i h_i phi(k / 2^j - i)
+      for (int i = 0; i < 4; ++i) {
+        const int64_t src = k - i * unit;
+        if (src >= 0 && src <= 3 * unit) v += h[i] * cur[src];
+      }
+      nxt[k] = r2 * v;
+    }
+    cur.swap(nxt);
+  }
+  out.swap(cur);
+}
+
+double host_daub4_power(double omega) {
+  // |phi-hat|^2 = prod_{j>=1} |m0(omega / 2^j)|^2 with |m0(w)|^2 = cos^4(w/2) (1 + 2 sin^2(w/2)) and
+  // prod_{j>=1} cos(omega / 2^(j+1)) = sin(omega/2) / (omega/2)
+  const double x = 0.5 * omega;
+  const double sinc = x == 0.0 ? 1.0 : std::sin(x) / x;
+  double p = sinc * sinc * sinc * sinc;
+  double w = 0.25 * omega;
+  for (int j = 0; j < 64 && w != 0.0; ++j, w *= 0.5) {
+    const double sw = std::sin(w);
+    p *= 1.0 + 2.0 * sw * sw;
+  }
+  return p;
+}
+
+// Solves the square system a x = b (size m, row-major a) by Gaussian elimination with partial
+// pivoting; a and b are overwritten.
+static void solve_dense(int m, std::vector<double>& a, std::vector<double>& b, std::vector<double>& x) {
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(a[r * m + c]) > std::fabs(a[piv * m + c])) piv = r;
+    if (piv != c) {
+      for (int k = 0; k < m; ++k) std::swap(a[c * m + k], a[piv * m + k]);
+      std::swap(b[c], b[piv]);
+    }
+    for (int r = c + 1; r < m; ++r) {
+      const double f = a[r * m + c] / a[c * m + c];
+      if (f == 0.0) continue;
+      for (int k = c; k < m; ++k) a[r * m + k] -= f * a[c * m + k];
+      b[r] -= f * b[c];
+    }
+  }
+  x.assign(m, 0.0);
+  for (int r = m - 1; r >= 0; --r) {
+    double v = b[r];
+    for (int k = r + 1; k < m; ++k) v -= a[r * m + k] * x[k];
+    x[r] = v / a[r * m + r];
+  }
+}
+
+void host_daub4_gamma(double* g) {
+  // Gamma(a, b) = int phi(x) phi(x-a) phi(x-b) dx, |a|, |b| <= 2, index (a+2) * 5 + (b+2):
+  // the two-scale relation gives Gamma(a, b) = sqrt2 sum_{i,j,k} h_i h_j h_k Gamma(2a+j-i, 2b+k-i)
+  // (zero where the supports do not overlap, |a - b| >= 3), and the partition of unity with the
+  // orthonormality of phi gives sum_b Gamma(a, b) = [a == 0].  The stacked (25 + 5) x 25 system
+  // is solved through its normal equations.
+  double h[4];
+  daub4_taps(h);
+  const double r2 = std::sqrt(2.0);
+  const int m = 25, rows = 30;
+  std::vector<double> a(static_cast<size_t>(rows) * m, 0.0), rhs(rows, 0.0);
+  for (int ia = -2; ia <= 2; ++ia)
+    for (int ib = -2; ib <= 2; ++ib) {
+      const int r = (ia + 2) * 5 + (ib + 2);
+      a[r * m + r] -= 1.0;
+      if (std::abs(ia - ib) >= 3) continue;  // the equation reads Gamma = 0 there
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+          for (int k = 0; k < 4; ++k) {
+            const int p = 2 * ia + j - i, q = 2 * ib + k - i;
+            if (p < -2 || p > 2 || q < -2 || q > 2 || std::abs(p - q) >= 3) continue;
+            a[r * m + (p + 2) * 5 + (q + 2)] += r2 * h[i] * h[j] * h[k];
+          }
+    }
+  for (int ia = -2; ia <= 2; ++ia) {
+    const int r = 25 + ia + 2;
+    for (int ib = -2; ib <= 2; ++ib) a[r * m + (ia + 2) * 5 + (ib + 2)] = 1.0;
+    rhs[r] = ia == 0 ? 1.0 : 0.0;
+  }
+  std::vector<double> ata(static_cast<size_t>(m) * m, 0.0), atb(m, 0.0), x;
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) {
+      double v = 0.0;
+      for (int r = 0; r < rows; ++r) v += a[r * m + i] * a[r * m + j];
+      ata[i * m + j] = v;
+    }
+    double v = 0.0;
+    for (int r = 0; r < rows; ++r) v += a[r * m + i] * rhs[r];
+    atb[i] = v;
+  }
+  solve_dense(m, ata, atb, x);
+  for (int i = 0; i < m; ++i) g[i] = x[i];
+}
+
+void host_daub4_gamma_split(std::vector<double>& lam, std::vector<double>& u) {
+  // gamma = U diag(lam) U^T by cyclic Jacobi rotations (gamma is symmetric 5 x 5)
+  double g[25];
+  host_daub4_gamma(g);
+  double a[5][5], v[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      a[i][j] = 0.5 * (g[i * 5 + j] + g[j * 5 + i]);
+      v[i][j] = i == j ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < 5; ++i)
+      for (int j = i + 1; j < 5; ++j) off += a[i][j] * a[i][j];
+    if (off < 1e-34) break;
+    for (int p = 0; p < 5; ++p)
+      for (int q = p + 1; q < 5; ++q) {
+        if (a[p][q] == 0.0) continue;
+        const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < 5; ++k) {  // columns p, q
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = c * akp - s * akq;
+          a[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < 5; ++k) {  // rows p, q
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = c * apk - s * aqk;
+          a[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < 5; ++k) {
+          const double vkp = v[k][p], vkq = v[k][q];
+          v[k][p] = c * vkp - s * vkq;
+          v[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  lam.assign(5, 0.0);
+  u.assign(25, 0.0);
+  for (int k = 0; k < 5; ++k) {
+    lam[k] = a[k][k];
+    for (int o = 0; o < 5; ++o) u[o * 5 + k] = v[o][k];  // u[o][k]: offset o - 2, eigenvector k
+  }
+}
+
 void host_mass_1d(int dsup, double* out) {
+  if (dsup == 3) {  // orthonormal basis: M(a) = [a == 0]
+    for (int a = -2; a <= 2; ++a) out[a + 2] = a == 0 ? 1.0 : 0.0;
+    return;
+  }
   for (int a = -(dsup - 1); a <= dsup - 1; ++a) out[a + dsup - 1] = cardinal_bspline(2 * dsup, a);
 }
 
@@ -262,6 +438,10 @@ void host_phi_hat_1d(int n, int dsup, std::vector<double>& out) {
   out.resize(n);
   for (int i = 0; i < n; ++i) {
     const int f = i < n / 2 ? i : i - n;
+    if (dsup == 3) {
+      out[i] = host_daub4_power(2.0 * kPi * f / n);
+      continue;
+    }
     const double x = kPi * f / n;
     const double sinc = f == 0 ? 1.0 : std::sin(x) / x;
     out[i] = std::pow(sinc, 2 * dsup);
@@ -342,7 +522,7 @@ extern "C" int zeta_host_window_table(const zeta_params* p, float* out) {
 }
 
 extern "C" int zeta_host_phi_hat(int n, int dsup, double* out) {
-  if (n < 2 || n > (1 << 20) || (dsup != 2 && dsup != 4) || !out) return ZETA_EINVAL;
+  if (n < 2 || n > (1 << 20) || dsup < 2 || dsup > 4 || !out) return ZETA_EINVAL;
   std::vector<double> v;
   zk::host_phi_hat_1d(n, dsup, v);
   for (int i = 0; i < n; ++i) out[i] = v[i];
@@ -350,7 +530,7 @@ extern "C" int zeta_host_phi_hat(int n, int dsup, double* out) {
 }
 
 extern "C" int zeta_host_mass_hat(int n, int dsup, double* out) {
-  if (n < 2 || n > (1 << 20) || (dsup != 2 && dsup != 4) || !out) return ZETA_EINVAL;
+  if (n < 2 || n > (1 << 20) || dsup < 2 || dsup > 4 || !out) return ZETA_EINVAL;
   zk::mass_hat_f64(n, dsup, out);
   return ZETA_OK;
 }
@@ -364,6 +544,26 @@ extern "C" int zeta_host_cell_quadrature(int q, int dsup, double* t, double* wq,
     wq[i] = wv[i];
   }
   for (size_t i = 0; i < bv.size(); ++i) beta[i] = bv[i];
+  return ZETA_OK;
+}
+
+extern "C" int zeta_host_daub4_dyadic(int level, double* out) {
+  if (level < 0 || level > 20 || !out) return ZETA_EINVAL;
+  std::vector<double> v;
+  zk::host_daub4_dyadic(level, v);
+  for (size_t i = 0; i < v.size(); ++i) out[i] = v[i];
+  return ZETA_OK;
+}
+
+extern "C" int zeta_host_daub4_gamma(double* gamma, double* lam, double* u) {
+  if (!gamma) return ZETA_EINVAL;
+  zk::host_daub4_gamma(gamma);
+  if (lam && u) {
+    std::vector<double> l, uv;
+    zk::host_daub4_gamma_split(l, uv);
+    for (int k = 0; k < 5; ++k) lam[k] = l[k];
+    for (int k = 0; k < 25; ++k) u[k] = uv[k];
+  }
   return ZETA_OK;
 }
 

@@ -43,8 +43,18 @@ void host_jbar_values(int l, double box, double r_lo, double r_hi, const int64_t
 void host_twiddles(int n, std::vector<float2>& out);
 // Real-spherical-harmonic recurrence constants: mm[m], a[l][m], b[l][m] (l, m <= kMaxL).
 void host_ylm_constants(double* mm, double* a, double* b);
-// B-spline Gram values M(a) for |a| < dsup, index a + dsup - 1.
+// Gram values M(a) = int phi(u) phi(u - a) du for |a| < dsup, index a + dsup - 1 (B-splines;
+// dsup 3, the orthonormal Daubechies function: [a == 0]).
 void host_mass_1d(int dsup, double* out);
+// The genus-4 Daubechies scaling function (dsup 3): its values at k / 2^level, k <= 3 * 2^level
+// (two-scale relation); |phi-hat(omega)|^2; the 1-D connection coefficients Gamma(a, b),
+// |a|, |b| <= 2, at [(a + 2) * 5 + b + 2]; and their eigen-split Gamma = U diag(lam) U^T with
+// u[o * 5 + k] (offset o - 2, eigenvector k).
+constexpr int kDaubLevel = 10;  // dyadic level of the point-value table the kernels interpolate
+void host_daub4_dyadic(int level, std::vector<double>& out);
+double host_daub4_power(double omega);
+void host_daub4_gamma(double* g);
+void host_daub4_gamma_split(std::vector<double>& lam, std::vector<double>& u);
 // 1-D DFT of the mass sequence: Mhat(k) = sum_a M(a) cos(2 pi k a / n), k-index < n; with_phi
 // multiplies by the square of the per-axis Phi-hat (the uniform term of Phi-hat-windowed fields).
 void host_mass_hat(int n, int dsup, std::vector<float>& out, bool with_phi = false);
@@ -90,6 +100,7 @@ struct zeta_ctx {
   float* d_gq = nullptr;      // cell quadrature: weights[q] then beta[q*dsup+o]
   float* d_phi = nullptr;     // Phi-hat per axis by DFT index (all ones without phi_hat)
   float* d_wprim = nullptr;   // primary-vertex tophat W_TH / N_g by |n|^2 (tophat_primary > 0)
+  float* d_daub = nullptr;    // Daubechies basis (dsup 3): phi at k / 2^kDaubLevel, k <= 3 * 2^kDaubLevel
   std::vector<double> radii;
   int* d_status = nullptr;    // latched device status
   // workspace
@@ -115,6 +126,29 @@ struct zeta_ctx {
 };
 
 namespace zk {
+
+// The Daubechies basis (dsup 3) runs on the 4-node stencil of the cubic B-spline: every prepared
+// particle's cell is one below floor(u) (cell_shift), so the stencil's nodes cell - 1 .. cell + 2
+// are floor(u) - 2 .. floor(u) + 1, with weights phi(t + 2), phi(t + 1), phi(t) and 0.
+inline int cell_shift(const zeta_ctx* c) { return c->p.dsup == 3 ? 1 : 0; }
+
+#ifdef __CUDACC__
+// phi(t + 2), phi(t + 1), phi(t), 0 for t in [0, 1), phi read from the table of its values at
+// the dyadic points of level kDaubLevel joined linearly.
+__device__ __forceinline__ void daub4_weights(float t, const float* __restrict__ tab, float* w) {
+  constexpr int unit = 1 << kDaubLevel;
+  const float sc = t * static_cast<float>(unit);  // exact: a power-of-two scale
+  int i = static_cast<int>(sc);
+  i = i < 0 ? 0 : (i > unit - 1 ? unit - 1 : i);
+  const float f = sc - static_cast<float>(i);
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    const float a = __ldg(tab + i + (2 - o) * unit), b = __ldg(tab + i + 1 + (2 - o) * unit);
+    w[o] = fmaf(f, b - a, a);
+  }
+  w[3] = 0.f;
+}
+#endif
 
 // Records an event pair around the kernels issued while it is alive (when profiling).
 class StageScope {

@@ -105,6 +105,8 @@ _SIGS = {
     "zeta_host_legendre_sum": ([_INT, _INT, _VP, _INT, _VP, _VP], _INT),
     "zeta_host_reduced_q": ([_INT, _VP, _VP, _VP, _VP, _VP], _INT),
     "zeta_host_phi_hat": ([_INT, _INT, _VP], _INT),
+    "zeta_host_daub4_dyadic": ([_INT, _VP], _INT),
+    "zeta_host_daub4_gamma": ([_VP, _VP, _VP], _INT),
 }
 
 
@@ -159,6 +161,22 @@ def host_mass_hat(n: int, dsup: int) -> np.ndarray:
     out = np.empty(n, np.float64)
     _check("zeta_host_mass_hat", lib().zeta_host_mass_hat(n, dsup, out.ctypes.data))
     return out
+
+
+def host_daub4_dyadic(level: int) -> np.ndarray:
+    """zeta_host_daub4_dyadic: the Daubechies function at k / 2^level, k = 0 .. 3 * 2^level."""
+    out = np.empty(3 * 2 ** int(level) + 1, np.float64)
+    _check("zeta_host_daub4_dyadic", lib().zeta_host_daub4_dyadic(int(level), out.ctypes.data))
+    return out
+
+
+def host_daub4_gamma():
+    """zeta_host_daub4_gamma: (gamma[5, 5] indexed [a + 2, b + 2], lam[5], u[5, 5] indexed [o, k])."""
+    g = np.empty((5, 5), np.float64)
+    lam = np.empty(5, np.float64)
+    u = np.empty((5, 5), np.float64)
+    _check("zeta_host_daub4_gamma", lib().zeta_host_daub4_gamma(g.ctypes.data, lam.ctypes.data, u.ctypes.data))
+    return g, lam, u
 
 
 def host_cell_quadrature(q: int, dsup: int):

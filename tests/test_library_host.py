@@ -49,7 +49,8 @@ def test_create_rejects_bad_parameters_without_touching_the_device(zmod):
     lib = zmod.lib()
     edges = np.array([5.0, 10.0, 20.0])
     good = dict(n=32, box=100.0, dsup=4, lmax=4, nbins=2, gram=0)
-    bad = [dict(n=48), dict(n=8), dict(n=1024), dict(box=-1.0), dict(dsup=3), dict(lmax=15), dict(nbins=0),
+    bad = [dict(n=48), dict(n=8), dict(n=1024), dict(box=-1.0), dict(dsup=1), dict(dsup=5), dict(lmax=15),
+           dict(nbins=0),
            dict(nbins=40), dict(gram=7), dict(box=30.0)]
     for change in bad:
         kw = {**good, **change}
@@ -94,7 +95,7 @@ def test_host_ylm_matches_oracle(zmod):
     assert zmod.host_ylm(3, 1, 0.0, 0.0, 0.0) == 0.0
 
 
-@pytest.mark.parametrize("n,dsup", [(16, 2), (16, 4), (512, 4)])
+@pytest.mark.parametrize("n,dsup", [(16, 2), (16, 4), (512, 4), (32, 3)])
 def test_host_mass_hat_matches_oracle(zmod, n, dsup):
     got = zmod.host_mass_hat(n, dsup)
     m = O.mass_1d(dsup)
@@ -123,7 +124,10 @@ def test_host_cell_quadrature_matches_oracle(zmod, q, dsup):
 def test_host_table_helpers_reject_bad_arguments(zmod):
     lib = zmod.lib()
     out = np.empty(64, np.float64)
-    assert lib.zeta_host_mass_hat(16, 3, out.ctypes.data) == -1
+    assert lib.zeta_host_mass_hat(16, 5, out.ctypes.data) == -1
+    assert lib.zeta_host_cell_quadrature(5, 3, out.ctypes.data, out.ctypes.data, out.ctypes.data) == -1
+    assert lib.zeta_host_daub4_dyadic(-1, out.ctypes.data) == -1 and lib.zeta_host_daub4_dyadic(21, out.ctypes.data) == -1
+    assert lib.zeta_host_daub4_gamma(None, None, None) == -1
     assert lib.zeta_host_mass_hat(1, 4, out.ctypes.data) == -1
     assert lib.zeta_host_cell_quadrature(0, 4, out.ctypes.data, out.ctypes.data, out.ctypes.data) == -1
     assert lib.zeta_host_cell_quadrature(5, 4, None, out.ctypes.data, out.ctypes.data) == -1
@@ -176,13 +180,14 @@ def test_window_table_with_vertex_windows_matches_oracle(zmod, vertex):
     assert zmod.lib().zeta_host_window_table(ctypes.byref(bad), out.ctypes.data_as(ctypes.c_void_p)) == -1
 
 
-@pytest.mark.parametrize("dsup", [2, 4])
+@pytest.mark.parametrize("dsup", [2, 3, 4])
 def test_phi_hat_per_axis_matches_oracle(zmod, dsup):
     n = 24
     out = np.zeros(n)
     assert zmod.lib().zeta_host_phi_hat(n, dsup, out.ctypes.data_as(ctypes.c_void_p)) == 0
     full = O.phi_hat(n, dsup)
-    np.testing.assert_allclose(out, full[0, 0, :], rtol=1e-14)
+    # the Daubechies product takes about 25 factors, each rounded
+    np.testing.assert_allclose(out, full[0, 0, :], rtol=1e-14 if dsup != 3 else 1e-13)
     np.testing.assert_allclose(np.multiply.outer(np.multiply.outer(out, out), out), full, rtol=1e-13)
 
 
@@ -209,3 +214,19 @@ def test_legendre_sum_and_reduced_q_match_oracle(zmod):
     np.testing.assert_allclose(gl[:, 0, 0], (1 - 2 * mu * t + t * t) ** -0.5, rtol=1e-14)
     with pytest.raises(zmod.ZetaError):
         zmod.legendre_sum(zl, [1.5])
+
+
+@pytest.mark.parametrize("level", [0, 3, 10])
+def test_daub4_dyadic_table_matches_oracle(zmod, level):
+    got = zmod.host_daub4_dyadic(level)
+    np.testing.assert_allclose(got, O.daub4_dyadic(level), rtol=0, atol=2e-15)
+
+
+def test_daub4_connection_coefficients_and_split_match_oracle(zmod):
+    g, lam, u = zmod.host_daub4_gamma()
+    want = O.daub4_gamma()
+    for a in range(-2, 3):
+        for b in range(-2, 3):
+            assert abs(g[a + 2, b + 2] - want.get((a, b), 0.0)) < 1e-14, (a, b)
+    np.testing.assert_allclose(u @ u.T, np.eye(5), atol=1e-14)       # orthonormal eigenvectors
+    np.testing.assert_allclose(u @ np.diag(lam) @ u.T, g, atol=1e-14)  # the split the Gamma form applies
