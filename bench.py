@@ -40,11 +40,14 @@ METRIC = "zeta_l(r1,r2) s/catalog at Ng=512^3"
 UNIT = "s/catalog"
 FALLBACK_HBM_GBS = 6800.0
 
-# dram bytes (read + write) per call of a stage from one ncu capture of its kernels on the
-# 512^3 / 16M-particle / 20-bin workload, and the sha of the source file they were built from
-# (the entry is ignored once that source changes).  gram_particles = k_interp_part
-# (18.081 + 1.279 GB) + k_gram_rows (1.536 + 0.0002 GB).
-NCU_TRAFFIC = {"gram_particles": {"bytes": 20896354816, "sha": "ef13c78e0f09dd54"}}
+# dram bytes (read + write) per call of a stage, from one ncu capture of its kernels on a small
+# case scaled to the 512^3 / 16M-particle / 20-bin workload by the ratio of the algorithmic bytes
+# per call, and the shas of the source files they were built from (the entry is ignored once a
+# source changes).  gram_particles: k_interp_part (1.474160 + 0.125004 GB) + k_gram_node_rb<16, 2>
+# (0.160079 + 0.003164 GB) on the 256^3 / 2M-particle / 15-bin case, 1.762407 GB against
+# 1.038633 GB algorithmic (1.697x), times 10.993418 GB.  The fields' re-read share grows with the
+# grid (L2 holds a smaller part of a field), so at 512^3 this is a lower bound.
+NCU_TRAFFIC = {"gram_particles": {"bytes": 18654209914, "sha": ["50434d7e3b4e428b", "0fe8474692370d7b"]}}
 
 
 def _sha(path):
@@ -579,11 +582,11 @@ def run_ours(args, w, rank, world, local_rank):
         ms_k, launches_k, calls_k = rows[dom]
         bytes_launch = _alg_bytes(dom, w, nb)
         achieved = bytes_launch * calls_k / (ms_k / 1e3) / 1e9
-        src = {"alm_z": "fft.cu", "alm_y": "fft.cu", "alm_x": "fft.cu", "r2c": "fft.cu",
-               "gram_particles": "particles.cu", "gram_node": "sums.cu", "mass": "sums.cu"}[dom]
+        src = {"alm_z": ["fft.cu"], "alm_y": ["fft.cu"], "alm_x": ["fft.cu"], "r2c": ["fft.cu"],
+               "gram_particles": ["particles.cu", "sums.cu"], "gram_node": ["sums.cu"], "mass": ["sums.cu"]}[dom]
         tr = NCU_TRAFFIC.get(dom)
         traffic = None
-        if tr and tr["sha"] == _sha(os.path.join(ROOT, "paper_2507_15209_gb300", "csrc", src)):
+        if tr and tr["sha"] == [_sha(os.path.join(ROOT, "paper_2507_15209_gb300", "csrc", f)) for f in src]:
             traffic = tr["bytes"]
         gpu_launches = sum(v[1] for v in prof.values())
         stages = {k: {"ms": round(v[0] / args.steps, 3), "launches": v[1] // args.steps}
