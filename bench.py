@@ -469,6 +469,58 @@ def _adjoint_ratio(stream):
             "particle_backward_ms": b_part, "particle_backward_over_forward": round(b_part / f_part, 3)}
 
 
+def _extension_rows(stream):
+    """The extension rows on the 256^3 / 2M-particle workload (lmax 10, 15 bins, cubic B-spline
+    unless stated), seconds per catalogue (CUDA events, 2 repetitions after a warm-up) and the
+    ratio to the plain measurement of the same forms:
+      plain      zeta_ell, particle + node forms
+      windows    the same with point radii (the bin centres), a secondary tophat of one cell,
+                 Phi-hat and a primary tophat of one cell (Fig. 1 steps (3)-(4), Sec. 3)
+      daub4      the same forms on the Daubechies basis (dsup 3)
+      ss         the Szapudi-Szalay numerator and denominator (node form) with a uniform random
+                 catalogue of 2M points (Eq. SSestimator); ratio to the plain node form
+      xi         the 2PCF of every bin in both forms (Eq. pair-counting); ratio to the plain
+                 particle + node measurement"""
+    import torch
+    from paper_2507_15209_gb300.zeta import Context
+    w = WORKLOADS["box1000_n256_np2m"]
+    e = wl_edges(w)
+    nb = len(e) - 1
+    parts = torch.from_numpy(mocks.lognormal_catalogue(w["n"], w["n_p"], w["box"], w["field_seed"],
+                                                       w["sample_seed"])).cuda()
+    rand = torch.from_numpy(mocks.uniform_particles(w["n_p"], w["box"], 7001)).cuda()
+    h = w["box"] / w["n"]
+    both = ("particle", "node")
+    res = {"workload": "box1000_n256_np2m", "unit": "s/catalog"}
+
+    def run(key, fn, ctx):
+        ms = _events_ms(fn, 2, stream)
+        assert ctx.get_status() == 0
+        ctx.close()
+        res[key] = round(ms / 1e3, 5)
+
+    ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=w["n_p"], forms=both)
+    run("plain", lambda: ctx.zeta_ell(particles=parts, forms=both), ctx)
+    ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=w["n_p"], forms=("node",))
+    run("plain_node", lambda: ctx.zeta_ell(particles=parts, forms=("node",)), ctx)
+    radii = 0.5 * (e[:-1] + e[1:])
+    ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], None, np_max=w["n_p"], forms=both, radial="point",
+                  radii=radii, tophat=h, phi_hat=True, tophat_primary=h)
+    run("windows", lambda: ctx.zeta_ell(particles=parts, forms=both), ctx)
+    ctx = Context(w["n"], w["box"], 3, w["lmax"], e, np_max=w["n_p"], forms=both)
+    run("daub4", lambda: ctx.zeta_ell(particles=parts, forms=both), ctx)
+    ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=w["n_p"], forms=("node", "ss"))
+    run("ss", lambda: ctx.zeta_ell_ss(parts, rand, forms=("node",)), ctx)
+    ctx = Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=w["n_p"], forms=both)
+    run("xi", lambda: ctx.xi(particles=parts, forms=both), ctx)
+    for k in ("windows", "daub4", "xi"):
+        res[k + "_over_plain"] = round(res[k] / res["plain"], 4)
+    res["ss_over_plain_node"] = round(res["ss"] / res["plain_node"], 4)
+    del parts, rand
+    torch.cuda.empty_cache()
+    return res
+
+
 def _emit(d):
     print(json.dumps(d), flush=True)
 
@@ -626,6 +678,8 @@ def run_ours(args, w, rank, world, local_rank):
             line["adjoint"] = _adjoint_ratio(stream)
         if "cufft" in extras:
             line["cufft_reference"] = _cufft_reference(w, nb, stages, stream)
+        if "rows" in extras:
+            line["extension_rows"] = _extension_rows(stream)
         if world == 1 and not args.no_cpu_baseline:
             vals, sample, cores = _cpu_baseline(w, parts)
             line["cpu_baseline"] = {"value": vals[0], "unit": UNIT, "cores": cores, "kind": "oracle, scaled sample",
@@ -650,7 +704,7 @@ def main():
                          "over (l, m) pairs with an FP64 all-reduce of the per-pair slots (strong scaling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the Gram-variant, batch and adjoint extras")
-    ap.add_argument("--extras", default="variants,batch,adjoint,cufft", help="comma list of extras to measure")
+    ap.add_argument("--extras", default="variants,batch,adjoint,cufft,rows", help="comma list of extras to measure")
     ap.add_argument("--lmax", type=int, default=None, help="override lmax (small profiling runs only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
