@@ -17,6 +17,11 @@ on, and the command.
 
   python tests/golden/make_zeta_golden.py box1000_n256_np2m --forms particle,node --procs 4
   python tests/golden/make_zeta_golden.py box500_n64_np20k --forms node,gamma,particle --null
+  python tests/golden/make_zeta_golden.py batch64_n256 --catalogue 3 --forms particle --procs 6
+
+For the batched workload (uneven catalogue sizes) --catalogue picks catalogue i of the batch
+(its size from the workload's size draw, its seeds from batch_seeds(i)); the output is then
+tests/golden/zeta_<workload>_cat<i>.json.
 """
 from __future__ import annotations
 
@@ -37,12 +42,15 @@ if ROOT not in sys.path:
 
 from oracle import zeta_oracle as O  # noqa: E402
 from paper_2507_15209_gb300 import mocks  # noqa: E402
-from paper_2507_15209_gb300.workloads import WORKLOADS, edges as wl_edges  # noqa: E402
+from paper_2507_15209_gb300.workloads import WORKLOADS, batch_seeds, edges as wl_edges  # noqa: E402
 
 BIN_GROUP = 5  # fields built per oracle call (bounds the memory of one worker)
 
 
-def catalogue(w: dict, null: bool) -> np.ndarray:
+def catalogue(w: dict, null: bool, cat: int = -1) -> np.ndarray:
+    if "n_cat" in w:  # one catalogue of a batched workload
+        sizes = mocks.batch_sizes(w["n_cat"], w["n_p_lo"], w["n_p_hi"], w["size_seed"])
+        return mocks.lognormal_catalogue(w["n"], int(sizes[cat]), w["box"], *batch_seeds(cat))
     if null:
         return mocks.uniform_particles(w["n_p"], w["box"], w["null_seed"])
     return mocks.lognormal_catalogue(w["n"], w["n_p"], w["box"], w["field_seed"], w["sample_seed"])
@@ -88,12 +96,12 @@ def _one_lm(job):
     return out
 
 
-def run(name: str, forms, null: bool, procs: int, cache: str) -> dict:
+def run(name: str, forms, null: bool, procs: int, cache: str, cat: int = -1) -> dict:
     w = dict(WORKLOADS[name])
     n, box, lmax, dsup = w["n"], w["box"], w["lmax"], w["dsup"]
     e = wl_edges(w)
     nb = len(e) - 1
-    parts = catalogue(w, null)
+    parts = catalogue(w, null, cat)
     os.makedirs(cache, exist_ok=True)
     eps, wsum = O.assign(parts[:, :3].astype(np.float64), parts[:, 3].astype(np.float64), n, box, dsup)
     delta = O.contrast(eps, wsum)
@@ -125,6 +133,7 @@ def run(name: str, forms, null: bool, procs: int, cache: str) -> dict:
     sym = lambda x: 0.5 * (x + np.swapaxes(x, -1, -2))  # noqa: E731
     return {
         "workload": name, "catalogue": "uniform null" if null else "log-normal",
+        "batch_index": cat if "n_cat" in w else None,
         "catalogue_sha256": sha(parts), "n": n, "box": box, "lmax": lmax, "dsup": dsup, "edges": e.tolist(),
         "n_p": int(len(parts)), "wsum": wsum,
         "zeta": {f: sym(v).tolist() for f, v in zeta.items()},
@@ -139,8 +148,11 @@ def main():
     ap.add_argument("--null", action="store_true", help="also the uniform null catalogue of the workload")
     ap.add_argument("--procs", type=int, default=max(1, min(8, (os.cpu_count() or 2) // 2)))
     ap.add_argument("--cache", default=None, help="checkpoint directory (default: a temporary one)")
+    ap.add_argument("--catalogue", type=int, default=-1, help="catalogue index of a batched workload")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
+    if ("n_cat" in WORKLOADS[args.workload]) != (args.catalogue >= 0):
+        ap.error("--catalogue is required for a batched workload and only there")
     forms = tuple(args.forms.split(","))
     cache = args.cache or tempfile.mkdtemp(prefix="zeta_golden_")
     argv = []
@@ -152,10 +164,11 @@ def main():
         argv.append(a)
     res = {"command": "python tests/golden/make_zeta_golden.py " + " ".join(argv),
            "oracle": "oracle/zeta_oracle.py (FP64)", "data": run(args.workload, forms, False, args.procs,
-                                                                  os.path.join(cache, "data"))}
+                                                                  os.path.join(cache, "data"), args.catalogue)}
     if args.null:
         res["null"] = run(args.workload, forms, True, args.procs, os.path.join(cache, "null"))
-    out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), f"zeta_{args.workload}.json")
+    tag = f"_cat{args.catalogue}" if args.catalogue >= 0 else ""
+    out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), f"zeta_{args.workload}{tag}.json")
     with open(out, "w") as fh:
         json.dump(res, fh, indent=None, separators=(",", ":"))
         fh.write("\n")

@@ -10,6 +10,10 @@ bit for bit (numpy's PCG64 draws are platform-independent).
                      catalogue of 20,000 points (the paper's plain method, Sec. 2.2)
   box1000_n256_np2m  256^3, 1000 Mpc/h, 2,000,000 log-normal particles, lmax 10, 15 bins
                      5-150, cubic B-spline: particle form (with its uniform term) and node form
+  batch64_n256       the batched workload (256^3, 1000 Mpc/h, lmax 8, 12 bins 10-130, cubic
+                     B-spline, particle form): catalogues 0-3 of its uneven size draw (2.86M,
+                     3.97M, 3.28M and 0.94M particles) in one zeta_batch call, catalogue 3
+                     against the oracle's result (zeta_batch64_n256_cat3.json)
 
 Tolerance (float32 path): per l, ||zeta_gpu - zeta_oracle||_F <= 1e-5 ||zeta_oracle||_F.  Where
 the condition sum C_l (sum of absolute values of the summed terms) is more than 100 times
@@ -25,7 +29,7 @@ import numpy as np
 import pytest
 
 from paper_2507_15209_gb300 import mocks
-from paper_2507_15209_gb300.workloads import WORKLOADS, edges as wl_edges
+from paper_2507_15209_gb300.workloads import WORKLOADS, batch_seeds, edges as wl_edges
 
 pytestmark = pytest.mark.gpu
 
@@ -105,3 +109,30 @@ def test_plain_method_64_uniform_null(Z):
 @pytest.mark.slow
 def test_fp32_path_256_full_multipoles(Z):
     _run(Z, "box1000_n256_np2m", "data", ("particle", "node"))
+
+
+@pytest.mark.slow
+def test_batched_workload_at_full_size(Z):
+    name = "batch64_n256"
+    w = WORKLOADS[name]
+    gold = _golden(name + "_cat3")["data"]
+    sizes = mocks.batch_sizes(w["n_cat"], w["n_p_lo"], w["n_p_hi"], w["size_seed"])[:4]
+    cats = [mocks.lognormal_catalogue(w["n"], int(sizes[i]), w["box"], *batch_seeds(i)) for i in range(4)]
+    assert hashlib.sha256(cats[3].tobytes()).hexdigest() == gold["catalogue_sha256"], \
+        "the seeded catalogue differs from the one the oracle result was computed on"
+    e = wl_edges(w)
+    allp = torch.from_numpy(np.concatenate(cats)).cuda()
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    ctx = Z.Context(w["n"], w["box"], w["dsup"], w["lmax"], e, np_max=int(sizes.max()), forms=("particle",))
+    out = ctx.batch(allp, offs, forms=("particle",))
+    torch.cuda.synchronize()
+    assert ctx.get_status() == 0
+    got = out[3, 0].cpu().numpy()
+    np.testing.assert_array_equal(got, np.swapaxes(got, 1, 2))
+    errs = _check(got, np.array(gold["zeta"]["particle"]), np.array(gold["cond"]["particle"]),
+                  (name, "cat3", "particle"))
+    print(name, "catalogue 3", [f"{v:.1e}" for v in errs])
+    for i in range(3):  # the other catalogues of the batch are finite and symmetric
+        o = out[i, 0].cpu().numpy()
+        assert np.all(np.isfinite(o)) and np.array_equal(o, np.swapaxes(o, 1, 2))
+    ctx.close()
