@@ -86,12 +86,14 @@ enum {
   ZETA_GRAM_TF32 = 1,   /* tensor cores, tf32 inputs, fp32 accumulation             */
   ZETA_GRAM_BF16 = 2,   /* tensor cores, bf16 inputs, fp32 accumulation             */
   ZETA_GRAM_BF16X3 = 3, /* tensor cores, split bf16 (hi*hi + hi*lo + lo*hi)          */
-  ZETA_GRAM_BF16_FIELDS = 4 /* zeta_zeta_ell of the node form alone (nbins <= 20): the last
-                         inverse pass stores the fields as bfloat16 (round to nearest even)
-                         and the float32 Gram reads them, half the field bytes of the
-                         contraction; other forms, or more bins, are refused by zeta_zeta_ell
-                         (ZETA_EINVAL / ZETA_ENOTSUP); zeta_sum_grid on a caller's float32
-                         fields runs the float32 Gram                                   */
+  ZETA_GRAM_BF16_FIELDS = 4 /* zeta_zeta_ell of the node form alone: the last inverse pass
+                         stores the fields as bfloat16 (round to nearest even), half the
+                         field bytes of the contraction; up to 20 bins the register-blocked
+                         float32 Gram reads them, above 20 the tensor cores contract them
+                         (A = the fields, B = delta a as a bf16 hi + lo pair, fp32
+                         accumulation); other
+                         forms are refused by zeta_zeta_ell (ZETA_EINVAL); zeta_sum_grid on
+                         a caller's float32 fields runs the float32 Gram                   */
 };
 
 /* Radial part of the secondary-vertex windows (Sec. 3 binning, Eq. 3PCF-multipole-window). */

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
-SOURCES = ["tables.cpp", "fft.cu", "assign.cu", "sums.cu", "particles.cu", "gram_tc.cu", "adjoint.cu", "api.cu",
+SOURCES = ["tables.cpp", "fft.cu", "assign.cu", "sums.cu", "particles.cu", "gram_tc.cu", "gram_ws.cu", "adjoint.cu", "api.cu",
            "profile.cu"]
 
 

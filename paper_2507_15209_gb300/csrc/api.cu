@@ -380,7 +380,6 @@ int measure(zeta_ctx* c, const float* particles, int64_t np, const float* delta,
   // bfloat16 fields serve the node form alone (the other forms interpolate or integrate them)
   const bool bf16f = c->p.gram == ZETA_GRAM_BF16_FIELDS;
   if (bf16f && forms != ZETA_SUM_NODE) return ZETA_EINVAL;
-  if (bf16f && c->p.nbins > 20) return ZETA_ENOTSUP;
   const bool want_p = forms & ZETA_SUM_PARTICLE;
   if ((want_p || !delta) && (!particles || np < 1 || np > 0x7fffffffLL)) return ZETA_EINVAL;
   const int64_t npl = want_p ? np : 0;

@@ -411,8 +411,8 @@ int launch_gram_node_tc(const zeta_ctx* c, const float* delta, const float* alm,
   StageScope prof(c, ST_GRAM_NODE, 1, s);
   switch (c->p.gram) {
     case ZETA_GRAM_TF32: return tc_impl<ZETA_GRAM_TF32>(c, delta, alm, partials, s);
-    case ZETA_GRAM_BF16: return tc_impl<ZETA_GRAM_BF16>(c, delta, alm, partials, s);
-    case ZETA_GRAM_BF16X3: return tc_impl<ZETA_GRAM_BF16X3>(c, delta, alm, partials, s);
+    case ZETA_GRAM_BF16: return launch_gram_ws(c, delta, alm, partials, gram_ctas(c, GK_TC), 0, false, s);
+    case ZETA_GRAM_BF16X3: return launch_gram_ws(c, delta, alm, partials, gram_ctas(c, GK_TC), 0, true, s);
     default: return ZETA_ENOTSUP;
   }
 }

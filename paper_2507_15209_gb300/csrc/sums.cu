@@ -729,7 +729,9 @@ int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* p
   StageScope prof(c, ST_GRAM_NODE, 1, s);
   if constexpr (NBP <= 20) {
     const unsigned char* f = reinterpret_cast<const unsigned char*>(alm);
-    if (bf16) {
+    // the ring's bulk copies start on 16-byte boundaries
+    if ((reinterpret_cast<uintptr_t>(delta) | reinterpret_cast<uintptr_t>(alm)) & 15) return ZETA_EINVAL;
+    if (bf16) {  // bfloat16 fields, register-blocked float32 Gram (faster here than the tensor cores)
       const size_t smr = smem_node_rb<NBP, 1>();
       if (prep(k_gram_node_rb<NBP, 1>, smr)) return ZETA_ECUDA;
       k_gram_node_rb<NBP, 1><<<gram_ctas(c, GK_NODE), kRbThreads, smr, s>>>(delta, f, c->ng, c->p.nbins, partials,
@@ -742,7 +744,8 @@ int node_impl(const zeta_ctx* c, const float* delta, const float* alm, double* p
     }
     return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
   }
-  if (bf16) return ZETA_ENOTSUP;  // bfloat16 fields only with the register-blocked Gram
+  if (bf16)  // bfloat16 fields with more than 20 bins: the tensor-core Gram (gram_ws.cu)
+    return launch_gram_ws(c, delta, alm, partials, gram_ctas(c, GK_NODE), 1, false, s);
   const size_t sm = smem_node<NBP>();
   if (prep(k_gram_node<NBP>, sm)) return ZETA_ECUDA;
   k_gram_node<NBP><<<gram_ctas(c, GK_NODE), kThreads, sm, s>>>(delta, reinterpret_cast<const float4*>(alm), c->ng,
@@ -797,6 +800,7 @@ int launch_gram_rows_rb(const zeta_ctx* c, const float* pvals, const float4* s_t
 int gram_ctas(const zeta_ctx* c, int kind) {
   int per = c->tune[kind];
   if (per < 1) per = 1;
+  if (kind == GK_TC && c->p.gram == ZETA_GRAM_TF32) per *= 2;  // the TF32 kernel holds two CTAs per SM
   int g = c->num_sms * per;
   return g > kMaxCtas ? kMaxCtas : g;
 }

@@ -108,7 +108,7 @@ struct zeta_ctx {
   size_t ws_bytes = 0;
   mutable zk::Profiler prof;
   // persistent-grid size of each Gram kind, in CTAs per SM (set by zeta_autotune)
-  int tune[5] = {3, 3, 4, 4, 4};
+  int tune[5] = {3, 3, 4, 4, 1};
   // particle Gram: batches with at least this many particles stage their tile's halo in
   // shared memory; sparser ones gather from global memory
   int staged_min = 0;
@@ -241,6 +241,10 @@ int launch_gram_particles(const zeta_ctx* c, const int* s_cell, const float4* s_
 size_t particle_rows_bytes(const zeta_ctx* c, int64_t np);
 // tensor-core node Gram (gram_tc.cu), arithmetic chosen by c->p.gram
 int launch_gram_node_tc(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s);
+// Warp-specialised tensor-core node Gram (gram_ws.cu): ctas persistent CTAs, one partial each;
+// raw 0: float32 fields (split: hi/lo bfloat16 operands), 1: bfloat16 fields.
+int launch_gram_ws(const zeta_ctx* c, const float* delta, const void* fields, double* partials, int ctas, int raw,
+                   bool split, cudaStream_t s);
 int launch_wait_selftest(const zeta_ctx* c, long long spins, cudaStream_t s);
 // Uniform term of the particle form: launch_mass_hist sums the mode weights of dhat per integer
 // |n|^2 into hist (nn2 + 1 words: the sums, then the scale), once per catalogue; launch_mass

@@ -234,7 +234,7 @@ def test_nonfinite_particle_is_reported_and_workspace_checked(Z):
 
 # --- node-form Gram on the tensor cores (tcgen05): per-arithmetic error bounds -------------
 @pytest.mark.parametrize("gram,tol", [("tf32", 5e-3), ("bf16", 3e-2), ("bf16x3", 1e-4)])
-@pytest.mark.parametrize("nb", [5, 20])
+@pytest.mark.parametrize("nb", [5, 20, 32])
 def test_tensor_core_node_gram(Z, gram, tol, nb):
     n = 32
     edges = np.linspace(5.0, 30.0, nb + 1)
@@ -259,3 +259,23 @@ def test_tensor_core_zeta_ell_node_form(Z):
         assert ctx.get_status() == 0
         for l in range(lmax + 1):
             assert _rel(got[l], want["node"][l]) < tol, (gram, l)
+
+
+@pytest.mark.parametrize("nb", [6, 27])
+def test_bfloat16_fields_node_form_on_the_tensor_cores(Z, nb):
+    """Fields stored as bfloat16 by the last inverse pass, contracted on the tensor cores (any bin
+    count up to 32): zeta_l of the node form against the oracle.  Bound: the fields carry a
+    relative rounding of 2^-9 and so does delta a; 5e-3 of |zeta_l| per l (or 5e-4 of the condition
+    sum where that exceeds 100 |zeta_l|)."""
+    n, box, lmax = 32, 240.0, 2
+    edges = np.linspace(8.0, 100.0, nb + 1)
+    parts = mocks.lognormal_catalogue(n, 12000, box, 57, 58)
+    want, cond = O.zeta_multipoles(parts.astype(np.float64), n, box, edges, lmax, 4, forms=("node",))
+    ctx = Z.Context(n, box, 4, lmax, edges, gram="bf16_fields", np_max=len(parts), forms=("node",))
+    got = ctx.zeta_ell(particles=_dev(parts), forms=("node",))["node"].cpu().numpy()
+    assert ctx.get_status() == 0
+    for l in range(lmax + 1):
+        err = float(np.linalg.norm(got[l] - want["node"][l]))
+        zn, cn = float(np.linalg.norm(want["node"][l])), float(np.linalg.norm(cond["node"][l]))
+        print(nb, l, f"{err / zn:.1e}", f"{err / cn:.1e}")
+        assert err <= (5e-4 * cn if cn > 100 * zn else 5e-3 * zn), (nb, l, err / zn)
