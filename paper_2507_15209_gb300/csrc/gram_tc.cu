@@ -1,4 +1,6 @@
-// Node-form Gram contraction on the fifth-generation tensor cores (tcgen05, sm_103a).
+// Node-form Gram contraction on the fifth-generation tensor cores (tcgen05, sm_103a), TF32
+// operands.  (The BF16 and split-BF16 contractions run in the warp-specialised kernel of
+// gram_ws.cu.)
 //
 // G[b1][b2] = sum_x a_b1(x) * (delta(x) a_b2(x)) (the grid sum of Eq. 3PCF-multipole-sum at one
 // (l, m)) is a dense contraction over the grid points: D = A B^T with A[b][x] = a_b(x) and
@@ -12,12 +14,9 @@
 //     128 columns) and tcgen05.commit;
 //   * every kFlushStages stages (and at the end) warps 0-3 read D with tcgen05.ld and add the
 //     diagonal blocks into float64 registers, so long sums do not accumulate in float32.
-// Operand arithmetic: TF32 (kind::tf32), BF16 (kind::f16), or split BF16 with three products
-// hi*hi + hi*lo + lo*hi (the lo*lo term is below float32 resolution of the result).
+// Operand arithmetic: TF32 (kind::tf32).
 // Waits on an mbarrier are bounded: on timeout the CTA latches ZETA_ETIMEOUT in the status
 // word, stops issuing, and still frees its TMEM.
-#include <cuda_bf16.h>
-
 #include <cstdint>
 
 #include "zeta_internal.h"
@@ -34,22 +33,12 @@ constexpr long long kSpinLimit = 1LL << 26;
 
 template <int MODE>
 struct TcT;
-// ES: operand bytes; KI: K of one instruction; KT: points per slot and stage (32 bytes of K per
+// ES: operand bytes; KT: points per slot and stage (32 bytes of K per
 // instruction -> KT * ES / 32 instructions per stage)
 template <>
 struct TcT<ZETA_GRAM_TF32> {
-  static constexpr int ES = 4, KI = 8, SPLIT = 1, KT = 32;
+  static constexpr int ES = 4, KT = 32;
   static constexpr uint32_t FMT = 2;
-};
-template <>
-struct TcT<ZETA_GRAM_BF16> {
-  static constexpr int ES = 2, KI = 16, SPLIT = 1, KT = 64;
-  static constexpr uint32_t FMT = 1;
-};
-template <>
-struct TcT<ZETA_GRAM_BF16X3> {
-  static constexpr int ES = 2, KI = 16, SPLIT = 2, KT = 64;
-  static constexpr uint32_t FMT = 1;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -73,19 +62,11 @@ __device__ __forceinline__ uint32_t make_idesc() {
          (static_cast<uint32_t>(kM >> 4) << 24);
 }
 
-template <int MODE>
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-  if (MODE == ZETA_GRAM_TF32) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(idesc), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(idesc), "r"(acc));
-  }
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -141,28 +122,9 @@ __device__ __forceinline__ uint32_t tile_off(int row, int e) {
   return (row >> 3) * SBO + ((e * ES) >> 4) * 128 + (row & 7) * 16 + ((e * ES) & 15);
 }
 
-// Pack CP = 16 / ES consecutive values into one 16-byte core-matrix row segment (and the
-// low parts for split BF16).
-template <int MODE>
-__device__ __forceinline__ void pack16(const float* x, uint4& hi, uint4& lo) {
-  using T = TcT<MODE>;
-  if (T::ES == 4) {
-    hi = make_uint4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
-  } else {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
-      h[i] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
-      if (T::SPLIT == 2) {
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
-        l[i] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
-      }
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    if (T::SPLIT == 2) lo = make_uint4(l[0], l[1], l[2], l[3]);
-  }
+// Pack four consecutive values (rounded to tf32) into one 16-byte core-matrix row segment.
+__device__ __forceinline__ uint4 pack16(const float* x) {
+  return make_uint4(to_tf32(x[0]), to_tf32(x[1]), to_tf32(x[2]), to_tf32(x[3]));
 }
 
 // Block-diagonal packing: NS = min(128 / nb, 32 / groups) slots, each a different run of KT points.  Row
@@ -177,7 +139,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_gram_node_tc(const float* __r
   constexpr int KT = T::KT;
   constexpr uint32_t TILE = kM * KT * T::ES;  // one operand tile (A and B have 128 rows each)
   constexpr uint32_t SBO = KT * T::ES * 8;
-  constexpr uint32_t STAGE = T::SPLIT * 2 * TILE;
+  constexpr uint32_t STAGE = 2 * TILE;
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tmem_slot;
@@ -283,8 +245,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_gram_node_tc(const float* __r
     unsigned char* base = smraw + b * STAGE;
     unsigned char* Ahi = base;
     unsigned char* Bhi = base + TILE;
-    unsigned char* Alo = base + 2 * TILE;
-    unsigned char* Blo = base + 3 * TILE;
     if (stage >= 2 && ok) {
       if (!mbar_wait(&bar[b], ((stage - 2) >> 1) & 1)) ok = false;
     }
@@ -304,13 +264,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_gram_node_tc(const float* __r
           bv[i] = pd[i] * x;
         }
         const uint32_t off = tile_off<T::ES, KT>(sl * nb + bin, k0);
-        uint4 hi, lo;
-        pack16<MODE>(av, hi, lo);
-        *reinterpret_cast<uint4*>(Ahi + off) = hi;
-        if (T::SPLIT == 2) *reinterpret_cast<uint4*>(Alo + off) = lo;
-        pack16<MODE>(bv, hi, lo);
-        *reinterpret_cast<uint4*>(Bhi + off) = hi;
-        if (T::SPLIT == 2) *reinterpret_cast<uint4*>(Blo + off) = lo;
+        *reinterpret_cast<uint4*>(Ahi + off) = pack16(av);
+        *reinterpret_cast<uint4*>(Bhi + off) = pack16(bv);
       }
     }
     if (it + 1 < nmine) {  // next stage's loads are in flight while this one is contracted
@@ -325,16 +280,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_gram_node_tc(const float* __r
     if (abort_flag) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t aa = smem_u32(Ahi), ab = smem_u32(Bhi), la = smem_u32(Alo), lb = smem_u32(Blo);
+      const uint32_t aa = smem_u32(Ahi), ab = smem_u32(Bhi);
 #pragma unroll
       for (int k = 0; k < KT * T::ES / 32; ++k) {
         const uint32_t koff = k * 2 * 128;  // two core matrices along K per instruction
         const uint64_t dA = make_desc(aa + koff, 128, SBO), dB = make_desc(ab + koff, 128, SBO);
-        mma<MODE>(tmem, dA, dB, idesc, (started || k > 0) ? 1u : 0u);
-        if (T::SPLIT == 2) {
-          mma<MODE>(tmem, dA, make_desc(lb + koff, 128, SBO), idesc, 1u);
-          mma<MODE>(tmem, make_desc(la + koff, 128, SBO), dB, idesc, 1u);
-        }
+        mma(tmem, dA, dB, idesc, (started || k > 0) ? 1u : 0u);
       }
       commit(&bar[b]);
     }
@@ -391,7 +342,7 @@ template <int MODE>
 int tc_impl(const zeta_ctx* c, const float* delta, const float* alm, double* partials, cudaStream_t s) {
   using T = TcT<MODE>;
   // two stages of operands; the flush also stages the 128 x 129 float D tile in the same bytes
-  const size_t ops = 2 * T::SPLIT * 2 * static_cast<size_t>(kM) * T::KT * T::ES;
+  const size_t ops = 2 * 2 * static_cast<size_t>(kM) * T::KT * T::ES;
   const size_t dtile = static_cast<size_t>(kM) * (kN + 1) * sizeof(float);
   const size_t sm = ops > dtile ? ops : dtile;
   if (ensure_smem(reinterpret_cast<const void*>(k_gram_node_tc<MODE>), sm) != ZETA_OK) return ZETA_ECUDA;
