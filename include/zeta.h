@@ -317,7 +317,8 @@ int zeta_batch(zeta_ctx* ctx, const float* particles, const int64_t* offsets, in
 /* Autotuner: on this catalogue, times the Gram kernels that `forms` uses at persistent grid
  * sizes of 1, 2, 3, 4, 6 and 8 CTAs per SM and keeps the fastest for each kernel (used by all
  * later calls); with the particle form it then picks the staging threshold of
- * zeta_set_staging the same way.  Synchronises the stream; overwrites the workspace. */
+ * zeta_set_staging the same way; last it picks the tile shape of each field-reconstruction
+ * pass (zeta_set_shapes).  Synchronises the stream; overwrites the workspace. */
 int zeta_autotune(zeta_ctx* ctx, const float* particles, int64_t np, int forms, zeta_stream stream);
 
 /* The tuned persistent grid sizes in CTAs per SM: [node fp32, particle, Gamma, mass,
@@ -328,6 +329,15 @@ int zeta_get_tuning(const zeta_ctx* ctx, int* ctas_per_sm, int n);
  * restore a tuning saved from an earlier run.  Each value must be in [1, 16], else
  * ZETA_EINVAL and nothing changes.  Drops a cached batch graph. */
 int zeta_set_tuning(zeta_ctx* ctx, const int* ctas_per_sm, int n);
+
+/* Tile shapes of the three passes of the field reconstruction (zeta_reconstruct_alm and every
+ * measurement): shape[0] z-pass (0: 8 columns per CTA, 1: 4), shape[1] y-pass (0: 16 columns,
+ * 1: 8), shape[2] x-pass (0: 4 rows per CTA, 1: 2).  The shapes change only which threads
+ * transform which columns, not the arithmetic of a transform.  zeta_autotune picks them by
+ * timing each pass's two shapes on the caller's data.  Values other than 0 or 1, or n > 3:
+ * ZETA_EINVAL and nothing changes.  Drops a cached batch graph.  zeta_get_shapes returns 3. */
+int zeta_set_shapes(zeta_ctx* ctx, const int* shape, int n);
+int zeta_get_shapes(const zeta_ctx* ctx, int* shape, int n);
 
 /* Particle form: a batch of up to 128 particles of one 8x8x8-cell tile copies the tile's
  * halo of the fields into shared memory when it holds at least `min_particles` particles

@@ -750,6 +750,40 @@ int zeta_autotune(zeta_ctx* c, const float* particles, int64_t np, int forms, ze
       if (rc != ZETA_OK) break;
     }
   }
+  // tile shapes of the three field-reconstruction passes, one pass at a time (the other two
+  // passes cost the same under either shape of the pass being chosen)
+  float2* spec = at<float2>(c, L.spectra);
+  auto time_alm = [&]() -> float {
+    if ((rc = launch_alm(c, dhat, l, 0, 0, c->p.nbins, spec, fields, stream)) != ZETA_OK) return -1.f;
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, stream);
+      for (int r = 0; r < 2 && rc == ZETA_OK; ++r) rc = launch_alm(c, dhat, l, 0, 0, c->p.nbins, spec, fields, stream);
+      cudaEventRecord(e1, stream);
+      if (rc != ZETA_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = rc ? rc : ZETA_ECUDA;
+        return -1.f;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) best_ms = ms;
+    }
+    return best_ms;
+  };
+  for (int pass = 0; pass < 3 && rc == ZETA_OK; ++pass) {
+    float best = 1e30f;
+    int best_s = 0;
+    for (int sh = 0; sh < 2; ++sh) {
+      c->alm_shape[pass] = sh;
+      const float ms = time_alm();
+      if (ms < 0.f) break;
+      if (ms < best) {
+        best = ms;
+        best_s = sh;
+      }
+    }
+    c->alm_shape[pass] = best_s;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   drop_batch_graph(c);
@@ -783,6 +817,22 @@ int zeta_get_tuning(const zeta_ctx* c, int* ctas_per_sm, int n) {
   if (!c || !ctas_per_sm || n < 0) return ZETA_EINVAL;
   for (int i = 0; i < n && i < 5; ++i) ctas_per_sm[i] = c->tune[i];
   return 5;
+}
+
+int zeta_set_shapes(zeta_ctx* c, const int* shape, int n) {
+  ZK_TRY(check_ctx(c));
+  if (!shape || n < 0 || n > 3) return ZETA_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (shape[i] != 0 && shape[i] != 1) return ZETA_EINVAL;
+  for (int i = 0; i < n; ++i) c->alm_shape[i] = shape[i];
+  drop_batch_graph(c);
+  return ZETA_OK;
+}
+
+int zeta_get_shapes(const zeta_ctx* c, int* shape, int n) {
+  if (!c || !shape || n < 0) return ZETA_EINVAL;
+  for (int i = 0; i < n && i < 3; ++i) shape[i] = c->alm_shape[i];
+  return 3;
 }
 
 }  // extern "C"

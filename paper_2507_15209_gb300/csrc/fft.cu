@@ -514,33 +514,40 @@ int c2r_impl(const zeta_ctx* c, float2* data, int nf, cudaStream_t s, bool do_y)
   return check_launch();
 }
 
-template <int N>
-int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
-             cudaStream_t s, bool bf16) {
+// The three passes of the field reconstruction, each on one of two tile shapes (the context's
+// alm_shape, chosen by zeta_autotune; 0 is the default): z-pass columns T (8 or 4), y-pass
+// columns TY (16 or 8), x-pass rows RB (4 or 2).
+template <int N, int T>
+int alm_z_pass(const zeta_ctx* c, const float2* dhat, int l, int b0, int m, int nf, float2* spec, cudaStream_t s) {
   constexpr int NC = N / 2;
-  constexpr int T = kTz < NC ? kTz : NC;
-  constexpr int TY = kTy < NC ? kTy : NC;
   const long long fstride = static_cast<long long>(N) * N * NC;
-  {
-    StageScope prof(c, ST_ALM_Z, 1, s);
-    const size_t smz = AlmZ<N, T>::smem();
-    if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
-    const int nbp4 = (c->p.nbins + 3) / 4;
-    const float4* jt4 = reinterpret_cast<const float4*>(c->d_jtab) + static_cast<long long>(l) * c->nn2 * nbp4 + b0 / 4;
-    k_alm_z<N, T><<<dim3(NC / T, N), AlmZ<N, T>::NT, smz, s>>>(dhat, spec, fstride, nf, jt4, nbp4, l, m, c->d_tw,
-                                                                c->d_phi);
-    if (check_launch()) return ZETA_ECUDA;
-  }
-  {
-    StageScope prof(c, ST_ALM_Y, 1, s);
-    size_t sma = axis_smem<N, TY>();
-    if (set_smem(k_fft_axis<N, TY, true, 1>, sma)) return ZETA_ECUDA;
-    k_fft_axis<N, TY, true, 1><<<dim3(NC / TY, N, nf), RegThreads<N, TY, 512>::NT, sma, s>>>(spec, fstride, c->d_tw);
-    if (check_launch()) return ZETA_ECUDA;
-  }
+  StageScope prof(c, ST_ALM_Z, 1, s);
+  const size_t smz = AlmZ<N, T>::smem();
+  if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
+  const int nbp4 = (c->p.nbins + 3) / 4;
+  const float4* jt4 = reinterpret_cast<const float4*>(c->d_jtab) + static_cast<long long>(l) * c->nn2 * nbp4 + b0 / 4;
+  k_alm_z<N, T><<<dim3(NC / T, N), AlmZ<N, T>::NT, smz, s>>>(dhat, spec, fstride, nf, jt4, nbp4, l, m, c->d_tw,
+                                                              c->d_phi);
+  return check_launch();
+}
+
+template <int N, int TY>
+int alm_y_pass(const zeta_ctx* c, int nf, float2* spec, cudaStream_t s) {
+  constexpr int NC = N / 2;
+  const long long fstride = static_cast<long long>(N) * N * NC;
+  StageScope prof(c, ST_ALM_Y, 1, s);
+  const size_t sma = axis_smem<N, TY>();
+  if (set_smem(k_fft_axis<N, TY, true, 1>, sma)) return ZETA_ECUDA;
+  k_fft_axis<N, TY, true, 1><<<dim3(NC / TY, N, nf), RegThreads<N, TY, 512>::NT, sma, s>>>(spec, fstride, c->d_tw);
+  return check_launch();
+}
+
+template <int N, int RB>
+int alm_x_pass(const zeta_ctx* c, int nf, const float2* spec, float* out, cudaStream_t s, bool bf16) {
+  constexpr int NC = N / 2;
+  const long long fstride = static_cast<long long>(N) * N * NC;
   StageScope prof(c, ST_ALM_X, 1, s);
-  constexpr int RB = kRB4;
-  size_t smx = x4_smem<N, RB>();
+  const size_t smx = x4_smem<N, RB>();
   const int ng4 = (nf + 3) / 4;
   if (bf16) {
     if (set_smem(k_c2r_x4<N, RB, true>, smx)) return ZETA_ECUDA;
@@ -552,6 +559,20 @@ int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf
         spec, fstride, nf, reinterpret_cast<float4*>(out), c->d_tw);
   }
   return check_launch();
+}
+
+template <int N>
+int alm_impl(const zeta_ctx* c, const float2* dhat, int l, int m, int b0, int nf, float2* spec, float* out,
+             cudaStream_t s, bool bf16) {
+  constexpr int NC = N / 2;
+  constexpr int T0 = kTz < NC ? kTz : NC, T1 = 4 < NC ? 4 : NC;
+  constexpr int Y0 = kTy < NC ? kTy : NC, Y1 = 8 < NC ? 8 : NC;
+  int rc = c->alm_shape[0] ? alm_z_pass<N, T1>(c, dhat, l, b0, m, nf, spec, s)
+                           : alm_z_pass<N, T0>(c, dhat, l, b0, m, nf, spec, s);
+  if (rc != ZETA_OK) return rc;
+  rc = c->alm_shape[1] ? alm_y_pass<N, Y1>(c, nf, spec, s) : alm_y_pass<N, Y0>(c, nf, spec, s);
+  if (rc != ZETA_OK) return rc;
+  return c->alm_shape[2] ? alm_x_pass<N, 2>(c, nf, spec, out, s, bf16) : alm_x_pass<N, kRB4>(c, nf, spec, out, s, bf16);
 }
 
 // Full inverse of nf half spectra in place: z-, y- and x-passes.

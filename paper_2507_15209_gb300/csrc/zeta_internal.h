@@ -109,6 +109,8 @@ struct zeta_ctx {
   mutable zk::Profiler prof;
   // persistent-grid size of each Gram kind, in CTAs per SM (set by zeta_autotune)
   int tune[5] = {3, 3, 4, 4, 1};
+  // tile shape of each field-reconstruction pass (z, y, x), 0 = default (set by zeta_autotune)
+  int alm_shape[3] = {0, 0, 0};
   // particle Gram: batches with at least this many particles stage their tile's halo in
   // shared memory; sparser ones gather from global memory
   int staged_min = 0;

@@ -106,6 +106,8 @@ _SIGS = {
     "zeta_host_reduced_q": ([_INT, _VP, _VP, _VP, _VP, _VP], _INT),
     "zeta_host_phi_hat": ([_INT, _INT, _VP], _INT),
     "zeta_host_daub4_dyadic": ([_INT, _VP], _INT),
+    "zeta_set_shapes": ([_VP, _VP, _INT], _INT),
+    "zeta_get_shapes": ([_VP, _VP, _INT], _INT),
     "zeta_host_daub4_gamma": ([_VP, _VP, _VP], _INT),
 }
 
@@ -597,6 +599,17 @@ class Context:
         """zeta_set_tuning: persistent grid sizes [node, particle, Gamma, mass, node-tc]."""
         t = np.ascontiguousarray(ctas_per_sm, dtype=np.int32)
         _check("zeta_set_tuning", lib().zeta_set_tuning(self._h, t.ctypes.data, len(t)))
+
+    def shapes(self) -> list:
+        """zeta_get_shapes: tile shape of the z-, y- and x-pass (0 default, 1 the narrower tile)."""
+        t = np.zeros(3, np.int32)
+        lib().zeta_get_shapes(self._h, t.ctypes.data, 3)
+        return [int(x) for x in t]
+
+    def set_shapes(self, shape):
+        """zeta_set_shapes: tile shapes [z, y, x] of the field-reconstruction passes (0 or 1)."""
+        t = np.ascontiguousarray(shape, dtype=np.int32)
+        _check("zeta_set_shapes", lib().zeta_set_shapes(self._h, t.ctypes.data, len(t)))
 
     def selftest_wait(self, spins: int = 1000):
         _check("zeta_selftest_wait", lib().zeta_selftest_wait(self._h, int(spins), _stream()))

@@ -107,3 +107,40 @@ def test_tuning_roundtrip_and_validation(Z):
     assert lib.zeta_set_staging(ctx._h, -1) == -1
     ctx.set_staging(40)
     assert ctx.staging() == 40
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_every_tile_shape_gives_the_fields_and_zeta(Z, n):
+    """The tile shapes of the three reconstruction passes (zeta_set_shapes) only move columns
+    between threads: every combination gives the oracle's fields of one (l, m) and zeta_l within
+    the float32 bound, and the same zeta_l as the default shapes to float32 rounding."""
+    box, lmax, dsup = 4.0 * n, 2, 4
+    edges = np.linspace(2.5 * box / n, 0.4 * box, 5)
+    parts = mocks.lognormal_catalogue(n, 3 * n ** 3 // 16, box, 90 + n, 91 + n)
+    ctx = Z.Context(n, box, dsup, lmax, edges, np_max=len(parts), forms=("node", "particle"))
+    pd = torch.from_numpy(parts).cuda()
+    d, _ = ctx.assign(pd)
+    dh = ctx.fft_r2c(d)
+    dh64 = np.fft.fftn(d.cpu().numpy().astype(np.float64))
+    ref = O.multipole_fields(dh64, 2, -1, n, box, edges)
+    base = None
+    for sz in (0, 1):
+        for sy in (0, 1):
+            for sx in (0, 1):
+                ctx.set_shapes([sz, sy, sx])
+                assert ctx.shapes() == [sz, sy, sx]
+                got = Z.deinterleave(ctx.reconstruct_alm(dh, 2, -1).cpu().numpy(), ctx.nbins)
+                for b in range(ctx.nbins):
+                    assert np.abs(got[b] - ref[b]).max() <= 1e-5 * np.abs(ref[b]).max(), (sz, sy, sx, b)
+                z = ctx.zeta_ell(particles=pd, forms=("node", "particle"))
+                zz = {f: z[f].cpu().numpy() for f in z}
+                if base is None:
+                    base = zz
+                for f in zz:
+                    rel = np.abs(zz[f] - base[f]).max() / np.abs(base[f]).max()
+                    assert rel < 1e-5, (sz, sy, sx, f, rel)
+    with pytest.raises(Z.ZetaError):
+        ctx.set_shapes([2, 0, 0])
+    tuned = ctx.autotune(pd, forms=("node", "particle"))
+    assert len(tuned) == 5 and all(s in (0, 1) for s in ctx.shapes())
+    ctx.close()
