@@ -147,10 +147,13 @@ __global__ void __launch_bounds__(kAT)
   const int nt = n / kTile;
   const long long ntiles = static_cast<long long>(nt) * nt * nt;
   const int mask = n - 1;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const long long s0 = tile_start[t], s1 = tile_start[t + 1];
-    for (long long bs = s0; bs < s1; bs += kAPB) {
-      const int cnt = static_cast<int>((s1 - bs) < kAPB ? (s1 - bs) : kAPB);
+  // full batches of kAPB consecutive particles of the tile-sorted catalogue (a tile holds few
+  // particles at survey densities; consecutive tiles keep the batch's stencils close together)
+  const long long ptot = tile_start[ntiles];
+  {
+    for (long long bs = static_cast<long long>(blockIdx.x) * kAPB; bs < ptot;
+         bs += static_cast<long long>(gridDim.x) * kAPB) {
+      const int cnt = static_cast<int>((ptot - bs) < kAPB ? (ptot - bs) : kAPB);
       __syncthreads();
       if (threadIdx.x < cnt) {
         const int me = threadIdx.x;

@@ -158,7 +158,8 @@ struct WsPlan {
   static constexpr uint32_t RAWSLOT = kWsPts * 4 + G * GST;  // delta, then the groups
   static constexpr uint32_t OPSLOT = (NA + NB) * kWsTile;
   // operand slots: 4 of 32 KB, 3 of 48 KB, 2 of 64 KB (the converters run that many stages ahead)
-  static constexpr int OR = static_cast<int>((144u * 1024u) / OPSLOT) < 2 ? 2 : static_cast<int>((144u * 1024u) / OPSLOT);
+  static constexpr int ORF = static_cast<int>((144u * 1024u) / OPSLOT);
+  static constexpr int OR = ORF < 2 ? 2 : ORF;
   // as many raw slots as fit (the bulk copies of several stages in flight cover the DRAM latency)
   static constexpr int RRF = static_cast<int>((200u * 1024u - OR * OPSLOT) / RAWSLOT);
   static constexpr int RR = RRF > 12 ? 12 : (RRF < 2 ? 2 : RRF);
