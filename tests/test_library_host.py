@@ -128,6 +128,9 @@ def test_host_table_helpers_reject_bad_arguments(zmod):
     assert lib.zeta_host_cell_quadrature(5, 3, out.ctypes.data, out.ctypes.data, out.ctypes.data) == -1
     assert lib.zeta_host_daub4_dyadic(-1, out.ctypes.data) == -1 and lib.zeta_host_daub4_dyadic(21, out.ctypes.data) == -1
     assert lib.zeta_host_daub4_gamma(None, None, None) == -1
+    shape = np.zeros(3, np.int32)
+    assert lib.zeta_set_shapes(None, shape.ctypes.data, 3) == -1
+    assert lib.zeta_get_shapes(None, shape.ctypes.data, 3) == -1
     assert lib.zeta_host_mass_hat(1, 4, out.ctypes.data) == -1
     assert lib.zeta_host_cell_quadrature(0, 4, out.ctypes.data, out.ctypes.data, out.ctypes.data) == -1
     assert lib.zeta_host_cell_quadrature(5, 4, None, out.ctypes.data, out.ctypes.data) == -1
