@@ -263,12 +263,15 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
 }
 
 // z-pass of the field reconstruction with the multipole window fused in.
-// grid (nc/T, n).  For its own stage-0 points each thread keeps delta_hat * R_lm(n-hat) (with
-// the real sign of i^l) and the window-table row of |n|^2 in shared memory.  Bins are taken
-// four at a time: one float4 gather of the window table [n2][nbp] per point gives the
-// values of four fields, and the gather of the next four is issued before the current four
-// are transformed, so its latency hides behind them.  Field f (bin b0 + f) is
-// delta_hat * R * J_f(|n|^2) (* i for odd l); its z-transformed tile goes to out + f * fstride.
+// grid (nc/T, n/2 + 1): CTA (x-tile, iy) transforms the rows iy and n - iy together (one row for
+// iy = 0; the y-Nyquist row iy = n/2 is zero).  The two rows share |n|^2 at every (x, z), so
+// one gather of the window table serves both.  For its own stage-0 points each thread keeps
+// delta_hat * R_lm(n-hat) of both rows (with the real sign of i^l) and the window-table row of
+// |n|^2 in shared memory.  Bins are taken four at a time: one float4 gather of the window
+// table [n2][nbp] per point gives the values of four fields, and the gather of the next four is
+// issued before the current four are transformed, so its latency hides behind them.  Field f
+// (bin b0 + f) is delta_hat * R * J_f(|n|^2) (* i for odd l); its z-transformed tile goes to
+// out + f * fstride.
 template <int N, int T>
 struct AlmZ {
   static constexpr int NT = RegThreads<N, T, 512>::NT;
@@ -276,7 +279,7 @@ struct AlmZ {
   static constexpr int PADR = 2;  // exchange padding, 2 elements per 2 points (conflict-free for T = 8)
   static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;  // at least 16 warps per SM
   static constexpr size_t smem() {
-    return (StageTw<N>::SIZE + static_cast<size_t>(PPT) * NT + static_cast<size_t>(N) * T + N) *
+    return (StageTw<N>::SIZE + 2 * static_cast<size_t>(PPT) * NT + static_cast<size_t>(N) * T + N) *
                sizeof(float2) +
            static_cast<size_t>(PPT) * NT * sizeof(int);
   }
@@ -293,19 +296,21 @@ __global__ void __launch_bounds__(AlmZ<N, T>::NT, AlmZ<N, T>::MINB)
   constexpr int PADR = AlmZ<N, T>::PADR;
   extern __shared__ float2 sm[];
   float2* tw = sm;                      // per-stage twiddles
-  float2* pd = tw + StageTw<N>::SIZE;   // [PPT][NT] delta_hat * angular factor
-  float2* ex = pd + PPT * NT;           // [N][T] exchange (+ padding)
+  float2* pd = tw + StageTw<N>::SIZE;   // [2][PPT][NT] delta_hat * angular factor of the two rows
+  float2* ex = pd + 2 * PPT * NT;       // [N][T] exchange (+ padding)
   int* pn = reinterpret_cast<int*>(ex + N * T + N);  // [PPT][NT] window-table rows
   const int x0 = blockIdx.x * T;
   const int iy = blockIdx.y;
+  const int iy2 = (N - iy) & (N - 1);        // the mirror row (iy itself for iy = 0)
+  const int nrow = (iy == 0) ? 1 : 2;
   // offsets within one field (n^3 / 2 < 2^31)
-  const int colbase = iy * NC + x0;
+  const int colbase[2] = {iy * NC + x0, iy2 * NC + x0};
   constexpr int zstride = N * NC;
   if (iy == N / 2) {  // y-Nyquist row: the window is zero
     for (int f = 0; f < nf; ++f)
       for (int idx = threadIdx.x; idx < N * T; idx += blockDim.x) {
         const int z = idx / T, c = idx % T;
-        out[f * fstride + colbase + z * zstride + c] = make_float2(0.f, 0.f);
+        out[f * fstride + colbase[0] + z * zstride + c] = make_float2(0.f, 0.f);
       }
     return;
   }
@@ -321,10 +326,18 @@ __global__ void __launch_bounds__(AlmZ<N, T>::NT, AlmZ<N, T>::MINB)
     const bool nyq = (z == N / 2);
     const int row = nyq ? 0 : (nx * nx + ny * ny + nz * nz) * nbp4;
     pn[s * NT + threadIdx.x] = row;
+    const float pxz = __ldg(phi + nx) * __ldg(phi + z);
     const float a = nyq ? 0.f
                         : sgn * ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(ny), static_cast<float>(nz)) *
-                              (__ldg(phi + nx) * __ldg(phi + iy) * __ldg(phi + z));
-    pd[s * NT + threadIdx.x] = cscale(dhat[colbase + z * zstride + c], a);
+                              (pxz * __ldg(phi + iy));
+    pd[s * NT + threadIdx.x] = cscale(dhat[colbase[0] + z * zstride + c], a);
+    if (nrow == 2) {
+      const float a2 = nyq ? 0.f
+                           : sgn *
+                                 ylm_dev(l, m, static_cast<float>(nx), static_cast<float>(-ny), static_cast<float>(nz)) *
+                                 (pxz * __ldg(phi + iy2));
+      pd[(PPT + s) * NT + threadIdx.x] = cscale(dhat[colbase[1] + z * zstride + c], a2);
+    }
     jn[s] = __ldg(jt4 + row);
   }
   __syncthreads();
@@ -339,16 +352,18 @@ __global__ void __launch_bounds__(AlmZ<N, T>::NT, AlmZ<N, T>::MINB)
     const int nj = (nf - 4 * g) < 4 ? (nf - 4 * g) : 4;
     for (int j = 0; j < nj; ++j) {
       const int f = 4 * g + j;
-      float2 v[PPT];
+      for (int r = 0; r < nrow; ++r) {
+        float2 v[PPT];
 #pragma unroll
-      for (int s = 0; s < PPT; ++s) {
-        const float jj = j == 0 ? jv[s].x : j == 1 ? jv[s].y : j == 2 ? jv[s].z : jv[s].w;
-        v[s] = cscale(pd[s * NT + threadIdx.x], jj);
-        if (l & 1) v[s] = mul_i(v[s]);
+        for (int s = 0; s < PPT; ++s) {
+          const float jj = j == 0 ? jv[s].x : j == 1 ? jv[s].y : j == 2 ? jv[s].z : jv[s].w;
+          v[s] = cscale(pd[(r * PPT + s) * NT + threadIdx.x], jj);
+          if (l & 1) v[s] = mul_i(v[s]);
+        }
+        float2* of = out + f * fstride + colbase[r];
+        auto store = [&](int c, int z, float2 val) { of[z * zstride + c] = val; };
+        fft_reg_v<N, T, NT, true, false, PADR>(v, ex, T, tw, store);
       }
-      float2* of = out + f * fstride;
-      auto store = [&](int c, int z, float2 val) { of[colbase + z * zstride + c] = val; };
-      fft_reg_v<N, T, NT, true, false, PADR>(v, ex, T, tw, store);
     }
   }
 }
@@ -526,8 +541,8 @@ int alm_z_pass(const zeta_ctx* c, const float2* dhat, int l, int b0, int m, int 
   if (set_smem(k_alm_z<N, T>, smz)) return ZETA_ECUDA;
   const int nbp4 = (c->p.nbins + 3) / 4;
   const float4* jt4 = reinterpret_cast<const float4*>(c->d_jtab) + static_cast<long long>(l) * c->nn2 * nbp4 + b0 / 4;
-  k_alm_z<N, T><<<dim3(NC / T, N), AlmZ<N, T>::NT, smz, s>>>(dhat, spec, fstride, nf, jt4, nbp4, l, m, c->d_tw,
-                                                              c->d_phi);
+  k_alm_z<N, T><<<dim3(NC / T, N / 2 + 1), AlmZ<N, T>::NT, smz, s>>>(dhat, spec, fstride, nf, jt4, nbp4, l, m,
+                                                                      c->d_tw, c->d_phi);
   return check_launch();
 }
 
