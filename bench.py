@@ -43,11 +43,11 @@ FALLBACK_HBM_GBS = 6800.0
 # dram bytes (read + write) per call of a stage, from one ncu capture of its kernels on a small
 # case scaled to the 512^3 / 16M-particle / 20-bin workload by the ratio of the algorithmic bytes
 # per call, and the shas of the source files they were built from (the entry is ignored once a
-# source changes).  gram_particles: k_interp_part (1.474160 + 0.125004 GB) + k_gram_node_rb<16, 2>
-# (0.160079 + 0.003164 GB) on the 256^3 / 2M-particle / 15-bin case, 1.762407 GB against
-# 1.038633 GB algorithmic (1.697x), times 10.993418 GB.  The fields' re-read share grows with the
+# source changes).  gram_particles: k_interp_part (1.467544 + 0.124839 GB) + k_gram_node_rb<16, 2>
+# (0.160077 + 0.003190 GB) on the 256^3 / 2M-particle / 15-bin case, 1.755650 GB against
+# 1.038633 GB algorithmic (1.690x), times 10.993418 GB.  The fields' re-read share grows with the
 # grid (L2 holds a smaller part of a field), so at 512^3 this is a lower bound.
-NCU_TRAFFIC = {"gram_particles": {"bytes": 18654209914, "sha": ["50434d7e3b4e428b", "0fe8474692370d7b"]}}
+NCU_TRAFFIC = {"gram_particles": {"bytes": 18582692345, "sha": ["50434d7e3b4e428b", "1bbab9f8391053c4"]}}
 
 
 def _sha(path):
