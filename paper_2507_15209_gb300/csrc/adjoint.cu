@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kAT)
   const long long ntiles = static_cast<long long>(nt) * nt * nt;
   const int mask = n - 1;
   // full batches of kAPB consecutive particles of the tile-sorted catalogue (a tile holds few
-  // particles at survey densities; consecutive tiles keep the batch's stencils close together)
+  // particles at galaxy-catalogue densities; consecutive tiles keep the batch's stencils close together)
   const long long ptot = tile_start[ntiles];
   {
     for (long long bs = static_cast<long long>(blockIdx.x) * kAPB; bs < ptot;
