@@ -310,9 +310,10 @@ class Context:
     def __init__(self, n: int, box: float, dsup: int, lmax: int, edges, gram: str = "fp32", np_max: int = 0,
                  forms=("node",), radial: str = "shell", radii=None, tophat: float = 0.0,
                  tophat_primary: float = 0.0, phi_hat: bool = False, ws_copies: int = 1):
-        """edges: bin edges (radial "shell"); radial "point" with radii instead (edges may be None);
-        tophat / tophat_primary / phi_hat: the vertex windows of zeta_params; ws_copies: whole
-        per-catalogue workspaces to allocate (zeta_batch runs that many catalogues at once)."""
+        """dsup: the basis, 2 or 4 (linear or cubic B-spline) or 3 (the genus-4 Daubechies scaling
+        function); edges: bin edges (radial "shell"); radial "point" with radii instead (edges may
+        be None); tophat / tophat_primary / phi_hat: the vertex windows of zeta_params; ws_copies:
+        whole per-catalogue workspaces to allocate (zeta_batch runs that many catalogues at once)."""
         import torch
         self.n, self.box, self.dsup, self.lmax = int(n), float(box), int(dsup), int(lmax)
         self.edges = None if edges is None else np.ascontiguousarray(edges, dtype=np.float64)
