@@ -51,7 +51,8 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
 }
 
-constexpr long long kSpin = 1LL << 26;  // polls of a bounded mbarrier wait
+constexpr long long kSpin = 1LL << 22;      // polls of a bounded mbarrier wait (about 4 s in all)
+constexpr uint32_t kSuspendNs = 1000;         // a waiting thread sleeps in the poll up to this long
 
 // ---- mbarriers --------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -69,10 +70,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
   for (long long it = 0; it < kSpin; ++it) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
         "selp.b32 %0, 1, 0, P;\n\t}\n"
         : "=r"(ok)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (ok) return true;
   }
