@@ -43,11 +43,12 @@ FALLBACK_HBM_GBS = 6800.0
 # dram bytes (read + write) per call of a stage, from one ncu capture of its kernels on a small
 # case scaled to the 512^3 / 16M-particle / 20-bin workload by the ratio of the algorithmic bytes
 # per call, and the shas of the source files they were built from (the entry is ignored once a
-# source changes).  gram_particles: k_interp_part (1.467544 + 0.124839 GB) + k_gram_node_rb<16, 2>
-# (0.160077 + 0.003190 GB) on the 256^3 / 2M-particle / 15-bin case, 1.755650 GB against
-# 1.038633 GB algorithmic (1.690x), times 10.993418 GB.  The fields' re-read share grows with the
+# source changes).  gram_particles: k_interp_part (1.469452 + 0.124972 GB) + k_gram_node_rb<16, 2>
+# (0.160094 + 0.003012 GB) on the 256^3 / 2M-particle / 15-bin case, 1.757530 GB against
+# 1.038633 GB algorithmic (1.692x), times 10.993418 GB.  The fields' re-read share grows with the
 # grid (L2 holds a smaller part of a field), so at 512^3 this is a lower bound.
-NCU_TRAFFIC = {"gram_particles": {"bytes": 18582692345, "sha": ["50434d7e3b4e428b", "1bbab9f8391053c4"]}}
+NCU_TRAFFIC = {"gram_particles": {"bytes": 18602590626,
+                                  "sha": ["50434d7e3b4e428b", "1bbab9f8391053c4", "4de64bc1cb299339"]}}
 
 
 def _sha(path):
@@ -635,7 +636,8 @@ def run_ours(args, w, rank, world, local_rank):
         bytes_launch = _alg_bytes(dom, w, nb)
         achieved = bytes_launch * calls_k / (ms_k / 1e3) / 1e9
         src = {"alm_z": ["fft.cu"], "alm_y": ["fft.cu"], "alm_x": ["fft.cu"], "r2c": ["fft.cu"],
-               "gram_particles": ["particles.cu", "sums.cu"], "gram_node": ["sums.cu"], "mass": ["sums.cu"]}[dom]
+               "gram_particles": ["particles.cu", "sums.cu", "gram.cuh"], "gram_node": ["sums.cu"],
+               "mass": ["sums.cu"]}[dom]
         tr = NCU_TRAFFIC.get(dom)
         traffic = None
         if tr and tr["sha"] == [_sha(os.path.join(ROOT, "paper_2507_15209_gb300", "csrc", f)) for f in src]:
