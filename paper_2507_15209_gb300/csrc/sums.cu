@@ -377,142 +377,168 @@ constexpr size_t smem_node_rb() {
 }
 
 // ---------------------------------------------------------------------------------------
-// Gamma form: persistent CTAs over 8x8x8-cell tiles, kPB quadrature points per batch.
-// Phase 1 puts each point's stencil origin, B-spline weights and n_rec weight in shared
-// memory; phase 2 spreads (point, bin group) tasks over the CTA, each gathering its D^3
-// stencil of float4 bin groups from the L1-cached fields; phase 3 contracts the batch.
-// B-splines (D = 2, 4): the points are the q^3 Gauss-Legendre nodes of each cell, so the sum is
-// the exact integral of n_rec f_b1 f_b2 over the cell.  Daubechies (D = 5): the per-axis
-// connection coefficients split as gamma = U diag(lam) U^T (5 x 5), so
+// Gamma form: persistent CTAs over 8x8x8-cell tiles, NC cells of K^3 points each per batch.
+// B-splines (D = 2, 4): the points are the K^3 Gauss-Legendre nodes of each cell (K = 2, 5), so
+// the sum is the exact integral of n_rec f_b1 f_b2 over the cell.  Daubechies (D = 5): the
+// per-axis connection coefficients split as gamma = U diag(lam) U^T (5 x 5), so
 // sum_l delta_l sum_{o1,o2} Gamma(o1, o2) a_b1(l + o1) a_b2(l + o2)
 //   = sum_l sum_k (lam_kx lam_ky lam_kz delta_l) A_k,b1(l) A_k,b2(l),
 // A_k(l) = sum_o U[ox][kx] U[oy][ky] U[oz][kz] a(l + o - 2): the "points" of node l are the 5^3
-// eigen-indices k, the stencil taps U[o][k] (offsets -2..2), and the point weight the product of
-// lam times delta at the node itself.
+// eigen-indices k and the point weight is the product of lam times delta at the node itself.
+// Either way a point's value is a tensor-product filter of the cell's D^3 stencil with the
+// per-axis D x K matrix F(o, k) = gq[K + k D + o], and the kernel applies it one axis at a time:
+// x (D^2 rows -> D^2 K values), y (-> D K^2), z (-> K^3), D taps each, per cell and channel
+// (the bin groups as float4, and for the B-splines delta as a fourth, whose filtered value is
+// n_rec at the point).  That is D^2 K + D K^2 + K^3 outputs of D taps instead of K^3 outputs
+// of D^3 taps, and D^3 loads per cell and channel instead of K^3 D^3.  The x pass reads the
+// L1-cached fields and writes into the space of the value table (dead until the z pass), the y
+// pass into its own buffer, the z pass into the value table and the point weights; phase 4
+// contracts the batch.
+template <int NBP, int D>
+struct GammaShape {
+  static constexpr bool DB = D == 5;
+  static constexpr int K = D == 2 ? 2 : 5;   // points per axis
+  static constexpr int K3 = K * K * K;
+  static constexpr int NC = kPB / K3;        // cells per batch (2 or 32)
+  static constexpr int OFF = DB ? 2 : D / 2 - 1;
+  static constexpr int NCH = NBP / 4 + (DB ? 0 : 1);
+  static constexpr int XF = NCH * NC * D * D * K * 4;   // floats of the x-pass output
+  static constexpr int VF = kPB * Gram<NBP>::NBS + kPB;  // floats of the value table and weights
+  static constexpr int AF = XF > VF ? XF : VF;
+  static constexpr int YF = NCH * NC * D * K * K * 4;   // floats of the y-pass output
+  static_assert((kTile * kTile * kTile) % NC == 0, "a tile holds whole batches");
+  static_assert(AF % 4 == 0, "the y buffer starts on a 16-byte boundary");
+};
+
 template <int NBP, int D>
 __global__ void __launch_bounds__(kThreads)
     k_gram_gamma(const float* __restrict__ delta, const float4* __restrict__ f4, long long ng, int n, int nb,
-                  double inv_h, const float* __restrict__ gq, int q, double* __restrict__ partials) {
+                 const float* __restrict__ gq, double* __restrict__ partials) {
   using G = Gram<NBP>;
+  using S = GammaShape<NBP, D>;
+  constexpr int K = S::K, NC = S::NC, OFF = S::OFF;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float* vals = reinterpret_cast<float*>(smraw);    // [kPB][NBS]
-  float* wts = vals + kPB * G::NBS;                  // [kPB]
-  int4* org = reinterpret_cast<int4*>(wts + kPB);    // [kPB] stencil origin (unwrapped cells)
-  float* bw = reinterpret_cast<float*>(org + kPB);   // [kPB][3*D] weights x, y, z
-  double* red = reinterpret_cast<double*>(smraw);    // reused after the main loop
+  float* vals = reinterpret_cast<float*>(smraw);             // [kPB][NBS]
+  float* wts = vals + kPB * G::NBS;                           // [kPB]
+  float4* xbuf = reinterpret_cast<float4*>(smraw);           // [ch][cell][oz][oy][kx], aliases vals
+  float4* ybuf = reinterpret_cast<float4*>(vals + S::AF);    // [ch][cell][oz][ky][kx]
+  double* red = reinterpret_cast<double*>(smraw);            // reused after the main loop
   const int pr = threadIdx.x % G::NPAIR, grp = threadIdx.x / G::NPAIR;
   int b1 = 0, b2 = 0;
   pair_blocks(pr, G::NBLK, b1, b2);
   GramAcc<NBP> g;
   g.init();
+  float fm[D][K], qw[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    qw[k] = __ldg(gq + k);
+#pragma unroll
+    for (int o = 0; o < D; ++o) fm[o][k] = __ldg(gq + K + k * D + o);
+  }
   const int ngrp = (nb + 3) / 4;
+  const int nch = ngrp + (S::DB ? 0 : 1);
   const int nt = n / kTile;
   const long long ntiles = static_cast<long long>(nt) * nt * nt;
-  constexpr bool DB = D == 5;                 // Daubechies eigen-split form
-  constexpr int OFF = DB ? 2 : D / 2 - 1;
-  constexpr int LW = DB ? 8 : D;              // lanes per gather task (a power of two)
-  const int q3 = q * q * q;
   const int mask = n - 1;
+  constexpr int NBATCH = kTile * kTile * kTile / NC;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int tx = static_cast<int>(t % nt), ty = static_cast<int>((t / nt) % nt),
               tz = static_cast<int>(t / (static_cast<long long>(nt) * nt));
-    const long long s0 = 0, s1 = static_cast<long long>(kTile * kTile * kTile) * q3;
-    for (long long bs = s0; bs < s1; bs += kPB) {
-      const int cnt = static_cast<int>((s1 - bs) < kPB ? (s1 - bs) : kPB);
-      __syncthreads();
-      // phase 1: per point
-      const int me = threadIdx.x;
-      if (me < cnt) {
-        float wx[D], wy[D], wz[D];
+    for (int bt = 0; bt < NBATCH; ++bt) {
+      auto cell = [&](int j, int& cx, int& cy, int& cz) {
+        const int ci = bt * NC + j;
+        cx = tx * kTile + ci % kTile;
+        cy = ty * kTile + (ci / kTile) % kTile;
+        cz = tz * kTile + ci / (kTile * kTile);
+      };
+      __syncthreads();  // the previous batch's contraction is done with the value table
+      // x pass: task (channel, cell, oz, oy) filters one stencil row into K values
+      for (int i = threadIdx.x; i < nch * NC * D * D; i += kThreads) {
+        const int oy = i % D, oz = (i / D) % D, j = (i / (D * D)) % NC, ch = i / (D * D * NC);
         int cx, cy, cz;
-        float pw;
-        {
-          const long long id = bs + me;
-          const int cell = static_cast<int>(id / q3), qq = static_cast<int>(id % q3);
-          cx = tx * kTile + cell % kTile;
-          cy = ty * kTile + (cell / kTile) % kTile;
-          cz = tz * kTile + cell / (kTile * kTile);
-          const int qx = qq % q, qy = (qq / q) % q, qz = qq / (q * q);
-          const float* beta = gq + q;
+        cell(j, cx, cy, cz);
+        const long long row = (static_cast<long long>((cz - OFF + oz) & mask) * n + ((cy - OFF + oy) & mask)) * n;
+        float4 in[D];
+        if (ch < ngrp) {
+          const float4* base = f4 + ch * ng + row;
+#pragma unroll
+          for (int o = 0; o < D; ++o) in[o] = __ldg(base + ((cx - OFF + o) & mask));
+        } else {
+#pragma unroll
+          for (int o = 0; o < D; ++o) in[o] = make_float4(__ldg(delta + row + ((cx - OFF + o) & mask)), 0.f, 0.f, 0.f);
+        }
+        float4* out = xbuf + i * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
           for (int o = 0; o < D; ++o) {
-            wx[o] = beta[qx * D + o];
-            wy[o] = beta[qy * D + o];
-            wz[o] = beta[qz * D + o];
+            v.x = fmaf(fm[o][k], in[o].x, v.x);
+            v.y = fmaf(fm[o][k], in[o].y, v.y);
+            v.z = fmaf(fm[o][k], in[o].z, v.z);
+            v.w = fmaf(fm[o][k], in[o].w, v.w);
           }
-          float nr = 0.f;
-          if (DB) {  // delta at the node itself
-            nr = __ldg(delta + (static_cast<long long>(cz) * n + cy) * n + cx);
-          } else {  // n_rec at the quadrature point: the B-spline expansion of delta
-#pragma unroll
-            for (int oz = 0; oz < D; ++oz)
-#pragma unroll
-              for (int oy = 0; oy < D; ++oy) {
-                const long long row =
-                    (static_cast<long long>((cz - OFF + oz) & mask) * n + ((cy - OFF + oy) & mask)) * n;
-                float a = 0.f;
-#pragma unroll
-                for (int ox = 0; ox < D; ++ox) a = fmaf(wx[ox], __ldg(delta + row + ((cx - OFF + ox) & mask)), a);
-                nr = fmaf(wz[oz] * wy[oy], a, nr);
-              }
-          }
-          pw = gq[qx] * gq[qy] * gq[qz] * nr;
+          out[k] = v;
         }
-        org[me] = make_int4(cx - OFF, cy - OFF, cz - OFF, 0);
-#pragma unroll
-        for (int o = 0; o < D; ++o) {
-          bw[me * 3 * D + o] = wx[o];
-          bw[me * 3 * D + D + o] = wy[o];
-          bw[me * 3 * D + 2 * D + o] = wz[o];
-        }
-        wts[me] = pw;
-#pragma unroll
-        for (int b = 4 * ngrp; b < NBP; ++b) vals[me * G::NBS + b] = 0.f;
       }
       __syncthreads();
-      // phase 2: (point, group) gathers, LW lanes per task (one per x offset of the stencil; the
-      // Daubechies form's 5 taps take 8 lanes, 3 idle) so that a warp load covers 32/LW tasks with
-      // D consecutive float4 (one row segment) each (the loop runs in whole warps so every lane
-      // reaches the shuffles; LW divides 32)
-      const int total = cnt * ngrp * LW;
-      const int lane = threadIdx.x & 31;
-      for (int tb = threadIdx.x - lane; tb < total; tb += blockDim.x) {
-        const int task = tb + lane;
-        const bool act = task < total;
-        const int ox = task % LW, pg = task / LW;
-        const int p = act ? pg % cnt : 0, q4 = act ? pg / cnt : 0;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (act && ox < D) {
-          const int4 o = org[p];
-          const float* w = bw + p * 3 * D;
-          const float4* base = f4 + q4 * ng;
-          const int xo = (o.x + ox) & mask;
-          const float wx = w[ox];
+      // y pass: task (channel, cell, oz, kx) filters D x-pass values into K
+      for (int i = threadIdx.x; i < nch * NC * D * K; i += kThreads) {
+        const int kx = i % K, r = i / K;
+        const float4* src = xbuf + r * D * K + kx;
+        float4 in[D];
 #pragma unroll
-          for (int oz = 0; oz < D; ++oz) {
-            const long long zrow = static_cast<long long>((o.z + oz) & mask) * n;
+        for (int o = 0; o < D; ++o) in[o] = src[o * K];
+        float4* out = ybuf + r * K * K + kx;
 #pragma unroll
-            for (int oy = 0; oy < D; ++oy) {
-              const float ww = w[2 * D + oz] * w[D + oy] * wx;
-              const float4 v = __ldg(base + (zrow + ((o.y + oy) & mask)) * n + xo);
-              acc.x = fmaf(ww, v.x, acc.x);
-              acc.y = fmaf(ww, v.y, acc.y);
-              acc.z = fmaf(ww, v.z, acc.z);
-              acc.w = fmaf(ww, v.w, acc.w);
-            }
+        for (int k = 0; k < K; ++k) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int o = 0; o < D; ++o) {
+            v.x = fmaf(fm[o][k], in[o].x, v.x);
+            v.y = fmaf(fm[o][k], in[o].y, v.y);
+            v.z = fmaf(fm[o][k], in[o].z, v.z);
+            v.w = fmaf(fm[o][k], in[o].w, v.w);
           }
+          out[k * K] = v;
         }
-#pragma unroll
-        for (int off = 1; off < LW; off <<= 1) {
-          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off, LW);
-          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off, LW);
-          acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off, LW);
-          acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off, LW);
-        }
-        if (act && ox == 0) *reinterpret_cast<float4*>(vals + p * G::NBS + 4 * q4) = acc;
       }
       __syncthreads();
-      if (grp < G::NGRP) g.add(vals, wts, cnt, b1, b2, grp);
+      // z pass: task (channel, cell, ky, kx) filters D y-pass values into the K points along z
+      for (int i = threadIdx.x; i < nch * NC * K * K; i += kThreads) {
+        const int kk = i % (K * K), r = i / (K * K);
+        const int j = r % NC, ch = r / NC;
+        const int kx = kk % K, ky = kk / K;
+        const float4* src = ybuf + r * D * K * K + kk;
+        float4 in[D];
+#pragma unroll
+        for (int o = 0; o < D; ++o) in[o] = src[o * K * K];
+        const float wxy = __ldg(gq + kx) * __ldg(gq + ky);
+        float dn = 0.f;
+        if (S::DB && ch == 0) {  // delta at the node itself
+          int cx, cy, cz;
+          cell(j, cx, cy, cz);
+          dn = __ldg(delta + (static_cast<long long>(cz) * n + cy) * n + cx);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int o = 0; o < D; ++o) {
+            v.x = fmaf(fm[o][k], in[o].x, v.x);
+            v.y = fmaf(fm[o][k], in[o].y, v.y);
+            v.z = fmaf(fm[o][k], in[o].z, v.z);
+            v.w = fmaf(fm[o][k], in[o].w, v.w);
+          }
+          const int p = j * S::K3 + k * K * K + kk;
+          const float w = wxy * qw[k];
+          if (ch < ngrp) *reinterpret_cast<float4*>(vals + p * G::NBS + 4 * ch) = v;
+          else wts[p] = w * v.x;  // n_rec at the point
+          if (S::DB && ch == 0) wts[p] = w * dn;
+        }
+      }
+      __syncthreads();
+      if (grp < G::NGRP) g.add(vals, wts, NC * S::K3, b1, b2, grp);
     }
   }
   __syncthreads();
@@ -718,8 +744,8 @@ size_t smem_mass() {
 }
 template <int NBP, int D>
 size_t smem_gamma() {
-  using G = Gram<NBP>;
-  const size_t main = (kPB * G::NBS + kPB) * sizeof(float) + kPB * sizeof(int4) + kPB * 3 * D * sizeof(float);
+  using S = GammaShape<NBP, D>;
+  const size_t main = static_cast<size_t>(S::AF + S::YF) * sizeof(float);
   return main > red_bytes<NBP>() ? main : red_bytes<NBP>();
 }
 
@@ -758,9 +784,9 @@ int gamma_impl(const zeta_ctx* c, const float* delta, const float* alm, double* 
   StageScope prof(c, ST_GRAM_GAMMA, 1, s);
   const size_t sm = smem_gamma<NBP, D>();
   if (prep(k_gram_gamma<NBP, D>, sm)) return ZETA_ECUDA;
+  if (c->gamma_q != GammaShape<NBP, D>::K) return ZETA_EINVAL;
   k_gram_gamma<NBP, D><<<gram_ctas(c, GK_GAMMA), kThreads, sm, s>>>(
-      delta, reinterpret_cast<const float4*>(alm), c->ng, c->n, c->p.nbins, c->n / c->p.box, c->d_gq, c->gamma_q,
-      partials);
+      delta, reinterpret_cast<const float4*>(alm), c->ng, c->n, c->p.nbins, c->d_gq, partials);
   return cudaGetLastError() == cudaSuccess ? ZETA_OK : ZETA_ECUDA;
 }
 
