@@ -481,7 +481,9 @@ def _extension_rows(stream):
       ss         the Szapudi-Szalay numerator and denominator (node form) with a uniform random
                  catalogue of 2M points (Eq. SSestimator); ratio to the plain node form
       xi         the 2PCF of every bin in both forms (Eq. pair-counting); ratio to the plain
-                 particle + node measurement"""
+                 particle + node measurement
+      gamma      the connection-coefficient form of the grid sum (Eqs. con-coeff, SFC-3PCF) with
+                 each basis, ms per (l, m) beside the node form's Gram on the same fields"""
     import torch
     from paper_2507_15209_gb300.zeta import Context
     w = WORKLOADS["box1000_n256_np2m"]
@@ -517,6 +519,25 @@ def _extension_rows(stream):
     for k in ("windows", "daub4", "xi"):
         res[k + "_over_plain"] = round(res[k] / res["plain"], 4)
     res["ss_over_plain_node"] = round(res["ss"] / res["plain_node"], 4)
+    # the connection-coefficient (Gamma) form of the grid sum, per (l, m) of lmax 1 on the same grid
+    # (its cost grows as the cube of the cell's quadrature points times the stencil: D^6)
+    delta = None  # the catalogue's contrast (linear assignment) serves every basis as input data
+    gam = {}
+    for dsup, name in ((2, "linear"), (4, "cubic"), (3, "daub4")):
+        ctx = Context(w["n"], w["box"], dsup, 1, e, np_max=w["n_p"], forms=("gamma", "node"))
+        if delta is None:
+            delta, _ = ctx.assign(parts)
+        ctx.zeta_ell(delta=delta, forms=("gamma", "node"))
+        torch.cuda.synchronize()
+        ctx.profile_enable(True)
+        ctx.zeta_ell(delta=delta, forms=("gamma", "node"))
+        torch.cuda.synchronize()
+        p = ctx.profile_read()
+        ctx.profile_enable(False)
+        ctx.close()
+        gam[name] = {"gamma_ms_per_lm": round(p["gram_gamma"][0] / p["gram_gamma"][2], 3),
+                     "node_ms_per_lm": round(p["gram_node"][0] / p["gram_node"][2], 3)}
+    res["gamma_form_per_lm"] = gam
     del parts, rand
     torch.cuda.empty_cache()
     return res

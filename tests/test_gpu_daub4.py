@@ -4,7 +4,8 @@ the C ABI against the FP64 oracle on the same seeded catalogues (GPU).
 Checked: the assignment on every node (64^3, and the 256^3 grid with the 2M-particle
 catalogue); zeta_l of the node and particle forms on the 64^3 / 20k-particle catalogue
 (lmax 4, 8 bins 10-90) and on its uniform null catalogue; the Gamma form (the exact connection
-coefficients applied through their eigen-split) on a 16^3 grid; the 2PCF in both forms; the
+coefficients applied through their eigen-split) on a 16^3 grid, inside zeta_ell and as the
+grid sum alone at 3 and 29 bins; the 2PCF in both forms; the
 fields of one (l, m) with the basis's own Phi-hat window; the node gradient; and that the
 particle gradient refuses this basis.
 
@@ -105,6 +106,24 @@ def test_gamma_form_16(Z):
     want, cond = O.zeta_multipoles(parts.astype(np.float64), n, box, edges, lmax, 3, forms=forms)
     _check(z["node"].cpu().numpy(), want["node"], cond["node"], "node 16")
     _check(z["gamma"].cpu().numpy(), want["gamma"], cond["node"], "gamma 16")
+    ctx.close()
+
+
+@pytest.mark.parametrize("nb", [3, 29])
+def test_gamma_grid_sum_with_the_eigen_split(Z, nb):
+    """The Gamma form's grid sum alone on random fields: 3 bins (one padded group) and 29 (the
+    largest padded bin count, 32, whose per-batch buffers are the largest)."""
+    n = 16
+    edges = np.linspace(5.0, 40.0, nb + 1)
+    rng = np.random.default_rng(700 + nb)
+    d = rng.standard_normal((n, n, n)).astype(np.float32)
+    a = rng.standard_normal((nb, n, n, n)).astype(np.float32)
+    ctx = Z.Context(n, 100.0, 3, 1, edges)
+    got = ctx.sum_grid(torch.from_numpy(d).cuda(), torch.from_numpy(Z.interleave(a)).cuda(), "gamma").cpu().numpy()
+    want = O.sum_gamma(d.astype(np.float64), a.astype(np.float64), 3)
+    err = float(np.linalg.norm(got - want)) / float(np.linalg.norm(want))
+    print(f"gamma grid sum, {nb} bins: relative error {err:.1e}")
+    assert err < 1e-5
     ctx.close()
 
 
