@@ -390,8 +390,9 @@ constexpr size_t smem_node_rb() {
 // x (D^2 rows -> D^2 K values), y (-> D K^2), z (-> K^3), D taps each, per cell and channel
 // (the bin groups as float4, and for the B-splines delta as a fourth, whose filtered value is
 // n_rec at the point).  That is D^2 K + D K^2 + K^3 outputs of D taps instead of K^3 outputs
-// of D^3 taps, and D^3 loads per cell and channel instead of K^3 D^3.  The x pass reads the
-// L1-cached fields and writes into the space of the value table (dead until the z pass), the y
+// of D^3 taps.  The x pass reads the L1-cached fields, each stencil row once for a run of CX
+// cells along x ((CX + D - 1) D^2 loads per run and channel instead of K^3 D^3 per cell), and
+// writes into the space of the value table (dead until the z pass), the y
 // pass into its own buffer, the z pass into the value table and the point weights; phase 4
 // contracts the batch.
 template <int NBP, int D>
@@ -400,13 +401,21 @@ struct GammaShape {
   static constexpr int K = D == 2 ? 2 : 5;   // points per axis
   static constexpr int K3 = K * K * K;
   static constexpr int NC = kPB / K3;        // cells per batch (2 or 32)
+  static constexpr int CX = NC < kTile ? NC : kTile;  // cells per run along x (2 or 8)
+  static constexpr int CR = NC / CX;                  // runs per batch
   static constexpr int OFF = DB ? 2 : D / 2 - 1;
   static constexpr int NCH = NBP / 4 + (DB ? 0 : 1);
-  static constexpr int XF = NCH * NC * D * D * K * 4;   // floats of the x-pass output
+  // row pitches (float4) of the x- and y-pass outputs per (channel, cell, oz): padded for K = 5
+  // to 5 mod 8, so that the y and z passes (lanes along kx, then the next row) hit distinct
+  // banks
+  static constexpr int XR = K == 5 ? (D * K + 7 - 5) / 8 * 8 + 5 : D * K;
+  static constexpr int YR = K == 5 ? (K * K + 7 - 5) / 8 * 8 + 5 : K * K;
+  static constexpr int XF = NCH * NC * D * XR * 4;      // floats of the x-pass output
   static constexpr int VF = kPB * Gram<NBP>::NBS + kPB;  // floats of the value table and weights
   static constexpr int AF = XF > VF ? XF : VF;
-  static constexpr int YF = NCH * NC * D * K * K * 4;   // floats of the y-pass output
-  static_assert((kTile * kTile * kTile) % NC == 0, "a tile holds whole batches");
+  static constexpr int YF = NCH * NC * D * YR * 4;      // floats of the y-pass output
+  static_assert((kTile * kTile * kTile) % NC == 0 && kTile % CX == 0, "a tile holds whole batches and runs");
+  static_assert(XR >= D * K && YR >= K * K, "pitches hold a row");
   static_assert(AF % 4 == 0, "the y buffer starts on a 16-byte boundary");
 };
 
@@ -452,44 +461,49 @@ __global__ void __launch_bounds__(kThreads)
         cz = tz * kTile + ci / (kTile * kTile);
       };
       __syncthreads();  // the previous batch's contraction is done with the value table
-      // x pass: task (channel, cell, oz, oy) filters one stencil row into K values
-      for (int i = threadIdx.x; i < nch * NC * D * D; i += kThreads) {
-        const int oy = i % D, oz = (i / D) % D, j = (i / (D * D)) % NC, ch = i / (D * D * NC);
+      // x pass: task (channel, run, oz, oy) loads the CX + D - 1 nodes of one stencil row that
+      // the run's CX cells share and filters them into K values per cell
+      for (int i = threadIdx.x; i < nch * S::CR * D * D; i += kThreads) {
+        constexpr int CX = S::CX, NE = CX + D - 1;
+        const int oy = i % D, oz = (i / D) % D, cr = (i / (D * D)) % S::CR, ch = i / (D * D * S::CR);
         int cx, cy, cz;
-        cell(j, cx, cy, cz);
+        cell(cr * CX, cx, cy, cz);
         const long long row = (static_cast<long long>((cz - OFF + oz) & mask) * n + ((cy - OFF + oy) & mask)) * n;
-        float4 in[D];
+        float4 in[NE];
         if (ch < ngrp) {
           const float4* base = f4 + ch * ng + row;
 #pragma unroll
-          for (int o = 0; o < D; ++o) in[o] = __ldg(base + ((cx - OFF + o) & mask));
+          for (int e = 0; e < NE; ++e) in[e] = __ldg(base + ((cx - OFF + e) & mask));
         } else {
 #pragma unroll
-          for (int o = 0; o < D; ++o) in[o] = make_float4(__ldg(delta + row + ((cx - OFF + o) & mask)), 0.f, 0.f, 0.f);
+          for (int e = 0; e < NE; ++e) in[e] = make_float4(__ldg(delta + row + ((cx - OFF + e) & mask)), 0.f, 0.f, 0.f);
         }
-        float4* out = xbuf + i * K;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < CX; ++c) {
+          float4* out = xbuf + ((ch * NC + cr * CX + c) * D + oz) * S::XR + oy * K;
 #pragma unroll
-          for (int o = 0; o < D; ++o) {
-            v.x = fmaf(fm[o][k], in[o].x, v.x);
-            v.y = fmaf(fm[o][k], in[o].y, v.y);
-            v.z = fmaf(fm[o][k], in[o].z, v.z);
-            v.w = fmaf(fm[o][k], in[o].w, v.w);
+          for (int k = 0; k < K; ++k) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int o = 0; o < D; ++o) {
+              v.x = fmaf(fm[o][k], in[c + o].x, v.x);
+              v.y = fmaf(fm[o][k], in[c + o].y, v.y);
+              v.z = fmaf(fm[o][k], in[c + o].z, v.z);
+              v.w = fmaf(fm[o][k], in[c + o].w, v.w);
+            }
+            out[k] = v;
           }
-          out[k] = v;
         }
       }
       __syncthreads();
       // y pass: task (channel, cell, oz, kx) filters D x-pass values into K
       for (int i = threadIdx.x; i < nch * NC * D * K; i += kThreads) {
         const int kx = i % K, r = i / K;
-        const float4* src = xbuf + r * D * K + kx;
+        const float4* src = xbuf + r * S::XR + kx;
         float4 in[D];
 #pragma unroll
         for (int o = 0; o < D; ++o) in[o] = src[o * K];
-        float4* out = ybuf + r * K * K + kx;
+        float4* out = ybuf + r * S::YR + kx;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -509,10 +523,10 @@ __global__ void __launch_bounds__(kThreads)
         const int kk = i % (K * K), r = i / (K * K);
         const int j = r % NC, ch = r / NC;
         const int kx = kk % K, ky = kk / K;
-        const float4* src = ybuf + r * D * K * K + kk;
+        const float4* src = ybuf + r * D * S::YR + kk;
         float4 in[D];
 #pragma unroll
-        for (int o = 0; o < D; ++o) in[o] = src[o * K * K];
+        for (int o = 0; o < D; ++o) in[o] = src[o * S::YR];
         const float wxy = __ldg(gq + kx) * __ldg(gq + ky);
         float dn = 0.f;
         if (S::DB && ch == 0) {  // delta at the node itself
