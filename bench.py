@@ -140,11 +140,12 @@ def _make_inputs(w, rank):
 
 def _alg_bytes(stage, w, nb):
     """Algorithmic HBM bytes of one launch of a stage (minimum traffic of what it computes);
-    for the uniform term, of one catalogue."""
+    for the assignment and the uniform term, of one catalogue."""
     ng = w["n"] ** 3
     g = 4.0 * ng  # one float grid == one half spectrum without the x-Nyquist column
     n_p = w["n_p"]
     return {
+        "assign": 16.0 * n_p + g,       # per catalogue: read the particles once, write delta
         "alm_z": g * (1 + nb),          # read delta_hat once, write nb z-transformed spectra
         "alm_y": 2 * g * nb,            # read + write nb spectra
         "alm_x": 2 * g * nb,            # read nb half spectra, write nb real fields
@@ -656,7 +657,7 @@ def run_ours(args, w, rank, world, local_rank):
         ms_k, launches_k, calls_k = rows[dom]
         bytes_launch = _alg_bytes(dom, w, nb)
         achieved = bytes_launch * calls_k / (ms_k / 1e3) / 1e9
-        src = {"alm_z": ["fft.cu"], "alm_y": ["fft.cu"], "alm_x": ["fft.cu"], "r2c": ["fft.cu"],
+        src = {"assign": ["assign.cu"], "alm_z": ["fft.cu"], "alm_y": ["fft.cu"], "alm_x": ["fft.cu"], "r2c": ["fft.cu"],
                "gram_particles": ["particles.cu", "sums.cu", "gram.cuh"], "gram_node": ["sums.cu"],
                "mass": ["sums.cu"]}[dom]
         tr = NCU_TRAFFIC.get(dom)
