@@ -171,6 +171,22 @@ __global__ void __launch_bounds__(256) k_c2r_x(float2* __restrict__ data, long l
   }
 }
 
+// e^{i pi j / 16} (j mod 16), from cos(a pi / 16), a = 0..8, written out; with j a compile-time
+// constant the factors become instruction operands.
+__device__ __forceinline__ float2 root32(int j) {
+  constexpr float c[9] = {1.0f,
+                          0.980785280403230449f,
+                          0.923879532511286756f,
+                          0.831469612302545237f,
+                          0.707106781186547524f,
+                          0.555570233019602225f,
+                          0.382683432365089772f,
+                          0.195090322016128268f,
+                          0.0f};
+  const int a = j & 15;
+  return make_float2(a <= 8 ? c[a] : -c[16 - a], a <= 8 ? c[8 - a] : c[a - 8]);
+}
+
 // x-pass of the field reconstruction: C2R of the rows of four fields at once, written as
 // one bin-interleaved group [z][y][x][4] (lane j = field 4g + j; missing fields give 0).
 // The half-length complex transform takes Z[k] = (X[k] + conj X[NC-k]) + i e^{2 pi i k/N}
@@ -195,10 +211,10 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
   __syncthreads();
   auto store = [&](int c, int j, float2 v) { res[j * PS + c] = v; };
   // z_k = (X_k + conj X_{NC-k}) + i conj(W_N^k) (X_k - conj X_{NC-k}), X_{NC} = 0
-  auto pack = [&](int k, float2 xk, float2 xp) -> float2 {
-    const float2 wk = cconj(tw[k]);
+  auto packw = [](float2 wk, float2 xk, float2 xp) -> float2 {  // wk = conj(W_N^k)
     return cadd(cadd(xk, cconj(xp)), mul_i(cmul(wk, csub(xk, cconj(xp)))));
   };
+  auto pack = [&](int k, float2 xk, float2 xp) -> float2 { return packw(cconj(tw[k]), xk, xp); };
   constexpr int R0 = plan_radix<NC>(0);
   constexpr int PPT = NC * C / NT;
   constexpr int NTASK0 = PPT / R0;
@@ -218,8 +234,12 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
     }
     const bool u0 = (threadIdx.x % H) == 0;
     float2 v[PPT];
+    static_assert(16 % R0 == 0, "stage-0 radix divides 16");
 #pragma unroll
-    for (int i = 0; i < NTASK0; ++i)
+    for (int i = 0; i < NTASK0; ++i) {
+      // the task's points are k + q NC / R0, and conj(W_N^{k + q NC/R0}) = conj(W_N^k) e^{i pi q / R0}:
+      // one table read per task instead of R0
+      const float2 w0 = cconj(tw[pts[i * R0]]);
 #pragma unroll
       for (int q = 0; q < R0; ++q) {
         const int sl = i * R0 + q;
@@ -229,8 +249,10 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
           self_pair = (q == 0) ? make_float2(0.f, 0.f) : xv[i * R0 + (R0 - q)];
         else
           self_pair = xv[i * R0 + (R0 - 1 - q)];
-        v[sl] = pack(pts[sl], xv[sl], u0 ? self_pair : other);
+        const float2 wq = q == 0 ? w0 : cmul(w0, root32(q * (16 / R0)));
+        v[sl] = packw(wq, xv[sl], u0 ? self_pair : other);
       }
+    }
     fft_reg_v<NC, C, NT, true, 2, 0, true>(v, ex, PS, tw2, store);
   } else {
     auto load = [&](int c, int k) -> float2 {
