@@ -43,12 +43,12 @@ FALLBACK_HBM_GBS = 6800.0
 # dram bytes (read + write) per call of a stage, from one ncu capture of its kernels on a small
 # case scaled to the 512^3 / 16M-particle / 20-bin workload by the ratio of the algorithmic bytes
 # per call, and the shas of the source files they were built from (the entry is ignored once a
-# source changes).  gram_particles: k_interp_part (1.469452 + 0.124972 GB) + k_gram_node_rb<16, 2>
-# (0.160094 + 0.003012 GB) on the 256^3 / 2M-particle / 15-bin case, 1.757530 GB against
-# 1.038633 GB algorithmic (1.692x), times 10.993418 GB.  The fields' re-read share grows with the
+# source changes).  gram_particles: k_interp_part (1.446297 + 0.121082 GB) + k_gram_node_rb<16, 2>
+# (0.160077 + 0.000138 GB) on the 256^3 / 2M-particle / 15-bin case, 1.727594 GB against
+# 1.038633 GB algorithmic (1.663x), times 10.993418 GB.  The fields' re-read share grows with the
 # grid (L2 holds a smaller part of a field), so at 512^3 this is a lower bound.
-NCU_TRAFFIC = {"gram_particles": {"bytes": 18602590626,
-                                  "sha": ["50434d7e3b4e428b", "1bbab9f8391053c4", "4de64bc1cb299339"]}}
+NCU_TRAFFIC = {"gram_particles": {"bytes": 18285736709,
+                                  "sha": ["50434d7e3b4e428b", "c0ee103de8e92020", "4de64bc1cb299339"]}}
 
 
 def _sha(path):
