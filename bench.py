@@ -51,6 +51,13 @@ NCU_TRAFFIC = {"gram_particles": {"bytes": 18285736709,
                                   "sha": ["50434d7e3b4e428b", "c0ee103de8e92020", "4de64bc1cb299339"]}}
 
 
+# the source files (under paper_2507_15209_gb300/csrc) of every stage that has algorithmic bytes,
+# for matching a stored counter capture against the current sources
+STAGE_SOURCES = {"assign": ["assign.cu"], "alm_z": ["fft.cu"], "alm_y": ["fft.cu"], "alm_x": ["fft.cu"],
+                 "r2c": ["fft.cu"], "gram_particles": ["particles.cu", "sums.cu", "gram.cuh"],
+                 "gram_node": ["sums.cu"], "mass": ["sums.cu"]}
+
+
 def _sha(path):
     with open(path, "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
@@ -657,9 +664,7 @@ def run_ours(args, w, rank, world, local_rank):
         ms_k, launches_k, calls_k = rows[dom]
         bytes_launch = _alg_bytes(dom, w, nb)
         achieved = bytes_launch * calls_k / (ms_k / 1e3) / 1e9
-        src = {"assign": ["assign.cu"], "alm_z": ["fft.cu"], "alm_y": ["fft.cu"], "alm_x": ["fft.cu"], "r2c": ["fft.cu"],
-               "gram_particles": ["particles.cu", "sums.cu", "gram.cuh"], "gram_node": ["sums.cu"],
-               "mass": ["sums.cu"]}[dom]
+        src = STAGE_SOURCES[dom]
         tr = NCU_TRAFFIC.get(dom)
         traffic = None
         if tr and tr["sha"] == [_sha(os.path.join(ROOT, "paper_2507_15209_gb300", "csrc", f)) for f in src]:
