@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(RegThreads<N / 2, 4 * RB, 256>::NT)
   constexpr int PPT = NC * C / NT;
   constexpr int NTASK0 = PPT / R0;
   constexpr int H = NC / R0 / 2;
-  constexpr bool MIRROR = (NTASK0 % 2 == 0) && H >= 1 && (NT % H == 0) && (NTASK0 / 2) * (NT / H) == C;
+  constexpr int HS = H >= 1 ? H : 1;  // H = 0 (tiny rows) rules the pairing out below
+  constexpr bool MIRROR = (NTASK0 % 2 == 0) && H >= 1 && (NT % HS == 0) && (NTASK0 / 2) * (NT / HS) == C;
   if constexpr (MIRROR) {
     // each thread holds both points of every (k, NC - k) pair: one load per point
     float2 xv[PPT];
